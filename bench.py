@@ -1,0 +1,311 @@
+"""Benchmark: batched-ensemble EDAA throughput on one GB300 (and N replicas).
+
+Workload (one "step"): the Jasper-Ridge-shaped synthetic cube (L=198,
+N=100x100, p=4, Dirichlet(0.3), 25 dB), M=50 runs with gamma in {0.5,1,2},
+T=100 outer iterations of K1=5 A-steps + K2=5 B-steps (Algorithm 1), then
+fit, coherence and Algorithm 2's selection.  Unit: run-steps/s, one
+run-step = one inner A- or B-update of one run (M*T*(K1+K2) per step).
+
+value: device-timed, X resident in HBM.  e2e: the same metric through the
+C ABI with host buffers (X uploaded from pinned memory each step, the
+selected run's E, A and B and every run's fit/coherence read back).
+`--impl reference` times the FP64 CPU oracle on the same workload instead.
+Under torchrun every rank solves its own M=50 ensemble (independent runs,
+no collective on the data path: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ensemble EDAA steps/sec vs plain FP32 at matched loss; HBM GB/s vs peak"
+UNIT = "run-steps/s"
+WORKLOAD = "jasper-shape synthetic cube L=198 N=10000 p=4, M=50 runs, T=100, K1=K2=5, FP32"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_count: int, mhz: float) -> float:
+    """FP32 CUDA-core peak: 4 SM partitions x 32 FP32 lanes = 128 FMA/clk/SM."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def algorithmic_flops_per_outer(L, N, p, M, K1, K2):
+    """Two contractions over the resident pixel tile per X pass ((1+K2) passes),
+    plus the K1 fused A-updates (G a: 2p^2, update: ~8p per run-pixel)."""
+    Mp = M * p
+    return (1 + K2) * 4.0 * L * N * Mp + K1 * (2.0 * p * p + 8.0 * p) * N * M
+
+
+def algorithmic_bytes_per_outer(L, N, p, M, K2, sx=4):
+    """X streamed once per pass plus A and B state read and written."""
+    Mp = M * p
+    return (1 + K2) * L * N * sx + 2.0 * Mp * N * 4 + K2 * 2.0 * Mp * N * 4
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def rank_seed(base_seed: int, rank: int) -> int:
+    """Each rank solves its own ensemble of the same cube: distinct run seeds."""
+    return base_seed + 7919 * rank
+
+
+def run_oracle_sample(cube, n_runs: int, T: int, K1: int = 5, K2: int = 5):
+    """Times the FP64 oracle on `n_runs` runs of `T` outer iterations."""
+    from oracle import edaa_oracle as O
+    Xn = O.normalize_pixels(cube.X)
+    t0 = time.perf_counter()
+    for m in range(n_runs):
+        O.edaa(Xn, cube.p, T, K1, K2, int(cube.seeds[m]), float(cube.gammas[m]))
+    dt = time.perf_counter() - t0
+    return n_runs * T * (K1 + K2) / dt, dt
+
+
+def blas_threads() -> int:
+    return int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2209_11002_gb300 import synth
+    cube = synth.workload(synth.JASPER_ENSEMBLE)
+    T = 20  # one step = one run of 20 outer iterations (a bounded sample)
+    for _ in range(args.warmup):
+        run_oracle_sample(cube, 1, T)
+    rates, total = [], 0.0
+    for k in range(args.steps):
+        r, dt = run_oracle_sample(cube, 1, T)
+        rates.append(r)
+        total += dt
+    value = args.steps * T * 10 / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "1 run x 20 outer iterations per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                             "sample": "1 run x 20 outer iterations (200 run-steps) per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--persistent", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+
+    from paper_2209_11002_gb300 import build, edaa, synth
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build_library()
+    edaa.load_library()
+
+    spec = dict(synth.JASPER_ENSEMBLE)
+    spec["seed"] = rank_seed(spec["seed"], 0)
+    cube = synth.workload(spec)
+    # distinct ensembles per rank: same cube, run seeds drawn from a rank-specific stream
+    seeds, gammas = synth.run_params(rank_seed(spec["seed"], rank), cube.M, spec["gamma_choices"])
+    L, N, p, M = cube.L, cube.N, cube.p, cube.M
+    T, K1, K2 = 100, 5, 5
+    stream = torch.cuda.Stream()
+    Xd = torch.from_numpy(cube.pixel_major()).cuda()
+    ctx = edaa.Context([dict(X=Xd, p=p, seeds=seeds, gammas=gammas)], stream=stream, T=T, K1=K1, K2=K2,
+                       persistent=args.persistent)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_step(ev=None):
+        ctx.reset()
+        if ev is not None:
+            ev[0].record(stream)
+        ctx.step(T)
+        if ev is not None:
+            ev[1].record(stream)
+        ctx.solve()
+        return ctx.select(0)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, kern_ms = [], []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))  # evict X and state from the 129 MB L2 between steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        e0.record(stream)
+        best, fit, mu = one_step(kev)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(kev[0].elapsed_time(kev[1]))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    run_steps = M * T * (K1 + K2)
+    value = world * run_steps * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel: the persistent solve launch (T outer iterations)
+    peaks, peak_kind = _peaks()
+    props = torch.cuda.get_device_properties(local)
+    flops_launch = T * algorithmic_flops_per_outer(L, N, p, M, K1, K2)
+    kern_avg_s = statistics.mean(kern_ms) / 1e3
+    achieved = flops_launch / kern_avg_s / 1e12
+    peak = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_edaa (persistent solve, T outer iterations)",
+                "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 x "
+                               f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max clock)",
+                "kernel_ms": statistics.mean(kern_ms),
+                "effective_gbs": T * algorithmic_bytes_per_outer(L, N, p, M, K2) / kern_avg_s / 1e9}
+
+    # end to end through the C ABI with host buffers
+    Xh = torch.from_numpy(cube.pixel_major()).pin_memory()
+    Eh = np.zeros((L, p), np.float32)
+    Ah = np.zeros((p, N), np.float32)
+    Bh = np.zeros((N, p), np.float32)
+    lib = edaa.load_library()
+    import ctypes
+
+    def e2e_step():
+        ctx.reset(0, Xh)
+        ctx.step(T)
+        ctx.solve()
+        b, f, m = ctx.select(0)
+        edaa._check(lib.edaa_get(ctx.h, 0, b, edaa._ptr(Eh), edaa._ptr(Ah), edaa._ptr(Bh)), "edaa_get")
+        return b
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_e2e = max(3, args.steps // 2)
+    for _ in range(n_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * run_steps * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * L * 4,
+           "d2h_bytes_per_step": (L * p + 2 * N * p) * 4 + 2 * M * 8 + 4}
+
+    launches_solve = ctx.describe(0)["launches_per_solve"]
+    launches = (1 if args.persistent else 5) + (1 if args.persistent else T * (2 + 2 * K2)) + launches_solve
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch_runs": M * world, "L": L, "N": N, "p": p, "M": M,
+                       "T": T, "K1": K1, "K2": K2, "l2": "flushed between timed steps (512 MB write)",
+                       "persistent": args.persistent, "launch": ctx.describe(0)},
+            "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches * args.steps,
+            "selected_run": int(best)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_runs, To = 2, 50
+        rate, dt = run_oracle_sample(cube, n_runs, To)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                                "sample": f"{n_runs} runs x {To} outer iterations ({n_runs * To * 10} run-steps, "
+                                          f"{dt:.1f} s) of the same cube"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", str(os.cpu_count() or 1))
+    sys.exit(main())

@@ -1,0 +1,168 @@
+/*
+ * edaa.h -- C ABI of the GB300 (sm_103a) implementation of Entropic Descent
+ * Archetypal Analysis (EDAA; Zouaoui et al., arXiv 2209.11002).
+ *
+ * The library solves, for each of M runs on each of one or more hyperspectral
+ * cubes,   min_{A,B} 1/2 ||X - X B A||_F^2   with the columns of A (p x N) on
+ * the simplex Delta_p and the columns of B (N x p) on Delta_N (Sec. III-A,
+ * eq. AA), by the alternating entropic descent of Algorithm 1, and then
+ * applies the model-selection rule of Algorithm 2.
+ *
+ * Conventions shared by every entry point
+ *   - X is given PIXEL-MAJOR: an N x L row-major float32 array in which pixel
+ *     i's L band values are contiguous (the paper's L x N matrix stored column
+ *     by column).  X may live in host or device memory; host data is copied
+ *     with cudaMemcpyAsync on the context's stream.
+ *   - Outputs use the paper's shapes in row-major order: E is L x p, A is
+ *     p x N, B is N x p.  Output pointers may be host or device memory; they
+ *     are always caller-owned and never freed by the library.
+ *   - Every call is asynchronous on the stream given to edaa_init unless it
+ *     says it synchronises.  The library owns only what edaa_init allocated.
+ *   - Errors: every call returns an edaa_status; no exception crosses the
+ *     ABI.  edaa_last_error() returns a thread-local message for the last
+ *     failure on the calling thread.  A device-side status word records
+ *     barrier time-outs and non-finite merges; synchronising calls report it,
+ *     after which the context only accepts edaa_destroy (EDAA_ERR_STATE).
+ *   - There is no CPU fallback: without a CUDA device every compute call
+ *     fails with EDAA_ERR_CUDA.
+ */
+#ifndef EDAA_H
+#define EDAA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EDAA_OK = 0,
+  EDAA_ERR_ARG = 1,         /* invalid argument (shape, pointer, index)        */
+  EDAA_ERR_CUDA = 2,        /* a CUDA runtime call failed (no device, launch)  */
+  EDAA_ERR_OOM = 3,         /* device allocation failed                        */
+  EDAA_ERR_STATE = 4,       /* context unusable after an earlier device error  */
+  EDAA_ERR_NONFINITE = 5,   /* a merge met a non-finite or empty softmax sum   */
+  EDAA_ERR_TIMEOUT = 6,     /* a bounded grid barrier gave up waiting          */
+  EDAA_ERR_UNSUPPORTED = 7  /* shape outside the compiled kernels' range       */
+} edaa_status;
+
+typedef enum { EDAA_FP32 = 0, EDAA_TF32 = 1, EDAA_BF16 = 2 } edaa_precision;
+
+typedef struct {
+  int T;              /* outer iterations (Algorithm 1; paper: 100)                 */
+  int K1;             /* A-steps per outer iteration (paper: 5)                     */
+  int K2;             /* B-steps per outer iteration (paper: 5)                     */
+  int normalize;      /* 1: l2-normalise every pixel first (eq. normalization)      */
+  int precision;      /* edaa_precision of the X-streaming contractions             */
+  int fit_norm;       /* Algorithm 2 fit: 0 entrywise sum |X-EA|, 1 max column sum  */
+  int coherence;      /* eq. coherence: 0 cosine of columns of E, 1 raw inner product */
+  double fit_ratio;   /* Algorithm 2 threshold factor (paper: 1.05)                 */
+  int persistent;     /* 1: one persistent launch per solve with bounded grid
+                         barriers; 0: one launch per pass, replayed from a graph    */
+  int autotune;       /* 1: time candidate tile shapes at init and keep the best    */
+  double barrier_timeout_ms; /* give-up time of a grid barrier wait (default 2000)  */
+  int center;         /* 1 (default): iterate on X minus its mean pixel.  EDAA's
+                         iterates are unchanged by a common translation of all
+                         pixels (each gradient changes by a constant along its
+                         softmax axis), and centring avoids the cancellation in
+                         E A A^T - X A^T; outputs and reported gradients are in
+                         the paper's uncentred terms either way.                   */
+} edaa_config;
+
+typedef struct {
+  const float* X;          /* N x L pixel-major float32, host or device             */
+  int L, N, p, M;          /* bands, pixels, endmembers, ensemble runs              */
+  const uint64_t* seeds;   /* host, length M: run seeds s_m (Algorithm 2)           */
+  const double* gammas;    /* host, length M: step factors gamma_m in eq. (eta0A)   */
+} edaa_cube;
+
+typedef struct edaa_ctx edaa_ctx;
+
+/* Fills the paper's defaults: T=100, K1=K2=5, normalize=1 (Sec. III-C),
+ * FP32, entrywise l1 fit, cosine coherence, fit_ratio=1.05 (Algorithm 2),
+ * persistent=1, autotune=0, barrier_timeout_ms=2000, center=1. */
+void edaa_config_default(edaa_config* cfg);
+
+/* Creates a context for n_cubes cubes (1..16), each with its own L, N, p, M,
+ * all sharing T, K1, K2 (Algorithm 1).  Copies and normalises X (eq.
+ * normalization), draws B^0 = softmax(0.1 u) per run from SplitMix64 seeded
+ * with s_m (eq. initB0; entry (i,j) uses generator output i*p+j+1, top 24
+ * bits), sets A^0 = 1/p (eq. initA0), and the step sizes eta1 =
+ * gamma_m / sigma_max^2(X B^0), eta2 = sqrt(p/N) eta1 (eqs. eta0A, eta0B).
+ * Limits: 1 <= p <= 8, p <= N, 1 <= L <= 319, M >= 1.  `stream` is a
+ * cudaStream_t (NULL = legacy default stream).  On success *out owns all
+ * device memory it allocated; free it with edaa_destroy. */
+edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes,
+                      const edaa_config* cfg, void* stream);
+
+/* Re-runs the initialisation of edaa_init on the existing buffers (no
+ * allocation).  If X is not NULL it replaces cube `cube`'s data (same shape,
+ * host or device, pixel-major); cube = -1 with X = NULL resets every cube. */
+edaa_status edaa_reset(edaa_ctx* ctx, int cube, const float* X);
+
+/* Runs n_outer outer iterations of Algorithm 1 (each: K1 A-steps, eq.
+ * update_A, then K2 B-steps, eq. update_B) on every run of every cube. */
+edaa_status edaa_step(edaa_ctx* ctx, int n_outer);
+
+/* Runs the remaining outer iterations up to T, then computes per run the
+ * fit ||X - E A||_1, the loss ||X - X B A||_F^2 and the coherence of E
+ * (Algorithm 2, eq. coherence).  Replays a captured CUDA graph when the
+ * context is at iteration 0. */
+edaa_status edaa_solve(edaa_ctx* ctx);
+
+/* Synchronises; applies Algorithm 2 to cube `cube`: I = {m : fit_m <=
+ * fit_ratio * min fit}, best = argmin_{m in I} mu_m, ties to the lowest m,
+ * non-finite fits excluded.  Writes *best and, when not NULL, fit[M] and
+ * mu[M] (host arrays).  Needs a preceding edaa_solve. */
+edaa_status edaa_select(edaa_ctx* ctx, int cube, int* best, double* fit, double* mu);
+
+/* Algorithm 2's rule alone, on host arrays (no device work).  Returns the
+ * selected index, or -1 when no fit is finite or M < 1. */
+int edaa_select_rule(const double* fit, const double* mu, int M, double fit_ratio);
+
+/* Copies run `run` of cube `cube`: E = X B (L x p), A (p x N), B (N x p),
+ * row-major, to caller buffers (host or device; NULL skips). */
+edaa_status edaa_get(edaa_ctx* ctx, int cube, int run, float* E, float* A, float* B);
+
+/* Gradients of ||X - X B A||_F^2 at the current state of one run:
+ * gA = 2 (E^T E A - E^T X) (p x N row-major) and gB = 2 X^T (E A A^T - X A^T)
+ * (N x p row-major) -- twice the terms inside eqs. (update_A), (update_B).
+ * Caller buffers, host or device; NULL skips. */
+edaa_status edaa_grad(edaa_ctx* ctx, int cube, int run, float* gA, float* gB);
+
+/* Synchronises; writes loss[m] = ||X - X B A||_F^2 (FP64 accumulation) for
+ * every run of cube `cube` at the current state (host array, length M). */
+edaa_status edaa_loss(edaa_ctx* ctx, int cube, double* loss);
+
+/* Step sizes in use for cube `cube` (host arrays of length M; NULL skips). */
+edaa_status edaa_step_sizes(edaa_ctx* ctx, int cube, double* eta1, double* eta2);
+
+/* Synchronises the context's stream and reports the device status word. */
+edaa_status edaa_sync(edaa_ctx* ctx);
+
+/* Outer iterations completed since the last init/reset. */
+int edaa_outer_done(const edaa_ctx* ctx);
+
+/* Describes the launch shape picked for cube `cube` (for logs and tests):
+ * runs per CTA group, pixel tile, CTAs per run group, persistent grid size,
+ * and the number of kernel launches the last edaa_solve enqueued. */
+edaa_status edaa_describe(const edaa_ctx* ctx, int cube, int* runs_per_group, int* pixel_tile,
+                          int* ctas_per_group, int* grid, int* launches_per_solve);
+
+void edaa_destroy(edaa_ctx* ctx);
+
+/* Thread-local text of the last error on this thread ("" if none). */
+const char* edaa_last_error(void);
+
+/* Failure-detection self-test: launches the persistent kernel's grid barrier
+ * on `grid` CTAs while waiting for grid + extra arrivals, with the given
+ * time-out.  With extra > 0 the barrier cannot complete, so every CTA must
+ * give up after timeout_ms and the call must return EDAA_ERR_TIMEOUT with the
+ * device still usable (no trap, no hang).  extra = 0 must return EDAA_OK. */
+edaa_status edaa_selftest_barrier(int grid, int extra, double timeout_ms, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EDAA_H */

@@ -1,0 +1,742 @@
+// Host side of the EDAA C ABI (include/edaa.h): argument checks, device
+// memory, launch shapes, CUDA-graph capture, Algorithm 2's selection rule.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/edaa.h"
+#include "edaa_internal.cuh"
+
+using namespace edaa;
+
+namespace {
+
+thread_local std::string g_err;
+
+edaa_status fail(edaa_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+edaa_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? EDAA_ERR_OOM : EDAA_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                          \
+  do {                                          \
+    cudaError_t e__ = (call);                   \
+    if (e__ != cudaSuccess) return cuda_fail(e__, what); \
+  } while (0)
+
+struct TileCfg {
+  int Rm, WP1, SPT, WP2;
+};
+
+// Register-tile limits of the compiled kernels (must match PassTraits).
+int rq1_max(int p) { return p <= 2 ? 4 : (p <= 4 ? 2 : 1); }
+int spt_max(int p) { return p <= 4 ? 2 : 1; }
+int rq2_max(int p) { return p <= 2 ? 4 : (p <= 4 ? 2 : 1); }
+
+bool tile_ok(const TileCfg& t, int L, int p, int M) {
+  if (t.Rm < 1 || t.Rm > M) return false;
+  if (8 % t.WP1 || 8 % t.WP2 || t.SPT < 1 || t.SPT > spt_max(p)) return false;
+  const int WR1 = 8 / t.WP1, WR2 = 8 / t.WP2;
+  if ((t.Rm + WR1 - 1) / WR1 > rq1_max(p)) return false;
+  if ((t.Rm + WR2 - 1) / WR2 > rq2_max(p)) return false;
+  const int Nt = 32 * t.WP1 * t.SPT;
+  const PassSmem s = pass_smem(L, padded_ld(L), round_up(L, 4), p, t.Rm, Nt);
+  return (size_t)s.total * 4 <= 200 * 1024;
+}
+
+size_t tile_smem(const TileCfg& t, int L, int p) {
+  const int Nt = 32 * t.WP1 * t.SPT;
+  return (size_t)pass_smem(L, padded_ld(L), round_up(L, 4), p, t.Rm, Nt).total * 4;
+}
+
+// Default launch shape: the largest run group the register tiles allow with
+// both phases' warps busy, a pixel tile of 64, and 2 CTAs per SM of shared
+// memory where it fits.
+TileCfg default_tile(int L, int p, int M) {
+  std::vector<TileCfg> cands;
+  for (int Rm : {8, 6, 4, 3, 2, 1}) {
+    if (Rm > M) continue;
+    for (int WP1 : {2, 1, 4, 8})
+      for (int WP2 : {1, 2, 4, 8}) {
+        TileCfg t{Rm, WP1, 64 / (32 * WP1) > 0 ? std::max(1, 64 / (32 * WP1)) : 1, WP2};
+        if (32 * WP1 * t.SPT != 64) continue;
+        if (tile_ok(t, L, p, M)) cands.push_back(t);
+      }
+  }
+  // score: busy warps in each phase (runs spread over warps), then bigger Rm
+  auto score = [&](const TileCfg& t) {
+    const int WR1 = 8 / t.WP1, WR2 = 8 / t.WP2;
+    const double b1 = (double)t.Rm / (WR1 * ((t.Rm + WR1 - 1) / WR1));
+    const double b2 = (double)t.Rm / (WR2 * ((t.Rm + WR2 - 1) / WR2));
+    const int RG = (M + t.Rm - 1) / t.Rm;
+    const double brun = (double)M / (RG * t.Rm);
+    return b1 * b2 * brun * (1.0 + 0.01 * t.Rm) * (tile_smem(t, L, p) <= 110 * 1024 ? 1.0 : 0.8);
+  };
+  TileCfg best{1, 2, 1, 8};
+  double bs = -1.0;
+  for (const auto& t : cands) {
+    const double s = score(t);
+    if (s > bs) { bs = s; best = t; }
+  }
+  return best;
+}
+
+std::vector<TileCfg> tile_candidates(int L, int p, int M) {
+  std::vector<TileCfg> out;
+  for (int Rm : {1, 2, 3, 4, 5, 6, 8, 10, 12, 16})
+    for (int WP1 : {1, 2, 4, 8})
+      for (int SPT : {1, 2})
+        for (int WP2 : {1, 2, 4, 8}) {
+          TileCfg t{Rm, WP1, SPT, WP2};
+          const int Nt = 32 * WP1 * SPT;
+          if (Nt < 32 || Nt > 128) continue;
+          if (tile_ok(t, L, p, M)) out.push_back(t);
+        }
+  return out;
+}
+
+std::map<std::tuple<int, int, int, int, int>, TileCfg>& tune_cache() {
+  static std::map<std::tuple<int, int, int, int, int>, TileCfg> c;
+  return c;
+}
+
+}  // namespace
+
+struct CubeHost {
+  int L, N, p, M, Ls, Lr, Mp;
+  TileCfg tile;
+  int RG, Pg, Nt, ntiles, lchunk, nlchunk;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  float* X_in = nullptr;  // N x L staging copy of the caller's X
+  double* bsum = nullptr; // per-block band sums for the mean pixel
+  double* scale = nullptr; // per-pixel 1/||x_i|| (FP64)
+  CubeDev dev;
+  std::vector<uint64_t> seeds;
+  std::vector<double> gammas;
+};
+
+struct edaa_ctx {
+  edaa_config cfg;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0, sm_count = 0, blocks_per_sm = 1;
+  std::vector<CubeHost> cubes;
+  Batch hb;
+  Batch* d_batch = nullptr;
+  int* d_status = nullptr;
+  unsigned* d_bar = nullptr;
+  size_t smem = 0;
+  int grid = 0;
+  int outer_done = 0;
+  bool broken = false;
+  cudaGraphExec_t g_solve = nullptr;
+  int g_solve_n = -1;
+  bool graphs_ok = true;
+  int launches_last_solve = 0;
+};
+
+static edaa_status check_status(edaa_ctx* c) {
+  if (c->broken) return fail(EDAA_ERR_STATE, "context is unusable after an earlier device error");
+  return EDAA_OK;
+}
+
+// Assign pass work items (run group x pixel group) and merge work items.
+static void plan(edaa_ctx* c) {
+  const int G = c->sm_count * c->blocks_per_sm;
+  double total = 0.0;
+  for (auto& h : c->cubes) total += (double)h.N * h.L * h.M * h.p;
+  int cta = 0, unit = 0, run0 = 0;
+  int units_total = 0;
+  for (auto& h : c->cubes) units_total += h.M;
+  for (auto& h : c->cubes) {
+    h.Nt = 32 * h.tile.WP1 * h.tile.SPT;
+    h.ntiles = (h.N + h.Nt - 1) / h.Nt;
+    h.RG = (h.M + h.tile.Rm - 1) / h.tile.Rm;
+    const double share = total > 0 ? (double)h.N * h.L * h.M * h.p / total : 1.0;
+    int n = std::max(h.RG, (int)floor(share * G));
+    h.Pg = std::max(1, std::min(h.ntiles, n / h.RG));
+    // even tiles per pixel group
+    const int per = (h.ntiles + h.Pg - 1) / h.Pg;
+    h.Pg = (h.ntiles + per - 1) / per;
+    // merge chunks: aim for about G units in total
+    const int want = std::max(1, (int)ceil((double)G * h.M / std::max(1, units_total) / h.M));
+    int lch = std::max(1, (h.L + want - 1) / want);
+    lch = std::min(lch, 256 / h.p);
+    h.lchunk = lch;
+    h.nlchunk = (h.L + lch - 1) / lch;
+    // the B-merge keeps Pg x p scale factors in shared memory
+    const int pg_fit = (int)((c->smem / 8 - 16 - (size_t)2 * kMaxP - (size_t)lch * h.p) / h.p);
+    if (h.Pg > pg_fit) h.Pg = std::max(1, pg_fit);
+    CubeDev& d = h.dev;
+    d.L = h.L; d.Ls = h.Ls; d.Lr = h.Lr; d.N = h.N; d.p = h.p; d.M = h.M; d.Mp = h.Mp;
+    d.LT = (h.L + 1 + 31) / 32;
+    d.Rm = h.tile.Rm; d.RG = h.RG; d.Pg = h.Pg; d.Nt = h.Nt; d.WP1 = h.tile.WP1; d.SPT = h.tile.SPT;
+    d.WP2 = h.tile.WP2; d.ntiles = h.ntiles;
+    d.cta0 = cta; d.lchunk = h.lchunk; d.nlchunk = h.nlchunk; d.unit0 = unit; d.run0 = run0;
+    cta += h.RG * h.Pg;
+    unit += h.M * h.nlchunk;
+    run0 += h.M;
+  }
+  c->hb.pass_items = cta;
+  c->hb.merge_units = unit;
+  c->hb.total_runs = run0;
+  c->grid = std::min(G, std::max(cta, unit));
+  if (c->grid < 1) c->grid = 1;
+}
+
+static size_t cube_smem(const CubeHost& h) {
+  size_t s = tile_smem(h.tile, h.L, h.p);
+  const size_t mb = (size_t)(2 * kMaxP + h.lchunk * h.p + h.Pg * h.p) * 8 + 64;
+  const size_t ma = (size_t)(64 + h.lchunk * h.p) * 8;
+  return std::max(s, std::max(ma, mb));
+}
+
+// Partial buffers are sized for the largest pixel-group count a plan can use.
+static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    const size_t o = off;
+    off += bytes;
+    return o;
+  };
+  const size_t N = h.N, L = h.L, Mp = h.Mp, M = h.M, p = h.p, Ls = h.Ls;
+  size_t oX = take(N * Ls * 4), oXin = take(N * L * 4), oA = take(N * Mp * 4), oB = take(N * Mp * 4);
+  size_t oEf = take(L * Mp * 4), oEd = take(L * Mp * 8), oRf = take(L * Mp * 4), oXAt = take(L * Mp * 8);
+  size_t oAAt = take(M * p * p * 8), olse = take(Mp * 4), oe1 = take(M * 4), oe2 = take(M * 4);
+  size_t oe1d = take(M * 8), oe2d = take(M * 8), osig = take(M * 8);
+  size_t opart = take((size_t)Pg_cap * (L + 1) * Mp * 4), opmax = take((size_t)Pg_cap * Mp * 4);
+  size_t opaa = take((size_t)Pg_cap * M * p * p * 4), opfit = take((size_t)Pg_cap * M * 3 * 8);
+  size_t ofit = take(M * 8), ofitmax = take(M * 8), oloss = take(M * 8), omu = take(M * 8);
+  size_t oseeds = take(M * 8), ogam = take(M * 8);
+  size_t oscale = take(N * 8), oxbar = take(L * 8), osx = take((L + 1) * 8), obsum = take((size_t)normalize_blocks(h.N) * L * 8);
+  if (assign) {
+    char* b = (char*)h.arena;
+    CubeDev& d = h.dev;
+    d.X = (float*)(b + oX);
+    h.X_in = (float*)(b + oXin);
+    d.logA = (float*)(b + oA);
+    d.logB = (float*)(b + oB);
+    d.Ef = (float*)(b + oEf);
+    d.Ed = (double*)(b + oEd);
+    d.Rf = (float*)(b + oRf);
+    d.XAt = (double*)(b + oXAt);
+    d.AAt = (double*)(b + oAAt);
+    d.lse = (float*)(b + olse);
+    d.eta1 = (float*)(b + oe1);
+    d.eta2 = (float*)(b + oe2);
+    d.eta1d = (double*)(b + oe1d);
+    d.eta2d = (double*)(b + oe2d);
+    d.sig2 = (double*)(b + osig);
+    d.part = (float*)(b + opart);
+    d.pmax = (float*)(b + opmax);
+    d.paa = (float*)(b + opaa);
+    d.pfit = (double*)(b + opfit);
+    d.fit = (double*)(b + ofit);
+    d.fitmax = (double*)(b + ofitmax);
+    d.loss2 = (double*)(b + oloss);
+    d.mu = (double*)(b + omu);
+    d.seeds = (const uint64_t*)(b + oseeds);
+    d.gammas = (const double*)(b + ogam);
+    d.xbar = (double*)(b + oxbar);
+    d.sx = (double*)(b + osx);
+    h.bsum = (double*)(b + obsum);
+    h.scale = (double*)(b + oscale);
+  }
+  return off;
+}
+
+static edaa_status upload_x(edaa_ctx* c, CubeHost& h, const float* X) {
+  CK(cudaMemcpyAsync(h.X_in, X, (size_t)h.N * h.L * 4, cudaMemcpyDefault, c->stream), "copy X");
+  CK(launch_normalize(h.X_in, h.dev.X, h.scale, h.bsum, h.dev.xbar, h.dev.sx, h.L, h.Ls, h.N, c->cfg.normalize,
+                      c->cfg.center, c->stream), "normalize");
+  return EDAA_OK;
+}
+
+static edaa_status push_batch(edaa_ctx* c) {
+  for (size_t i = 0; i < c->cubes.size(); ++i) c->hb.c[i] = c->cubes[i].dev;
+  CK(cudaMemcpyAsync(c->d_batch, &c->hb, sizeof(Batch), cudaMemcpyHostToDevice, c->stream), "upload batch");
+  return EDAA_OK;
+}
+
+// Enqueue one program (a sequence of phases) either as one persistent
+// launch or as one launch per phase.
+static edaa_status enqueue(edaa_ctx* c, int mode, int n_outer, int* launches) {
+  const int nph = program_phase_count(mode, n_outer, c->cfg.K2);
+  if (nph <= 0) return EDAA_OK;
+  if (c->cfg.persistent && nph > 1) {
+    CK(launch_program(c->d_batch, mode, n_outer, 0, nph, c->grid, c->smem, true, c->stream), "persistent launch");
+    if (launches) *launches += 1;
+  } else {
+    for (int s = 0; s < nph; ++s) {
+      CK(launch_program(c->d_batch, mode, n_outer, s, s + 1, c->grid, c->smem, false, c->stream), "phase launch");
+      if (launches) *launches += 1;
+    }
+  }
+  return EDAA_OK;
+}
+
+static edaa_status run_init(edaa_ctx* c) {
+  CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "reset status");
+  CK(cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), c->stream), "reset barrier");
+  for (auto& h : c->cubes) {
+    CK(cudaMemsetAsync(h.dev.XAt, 0, (size_t)h.L * h.Mp * 8, c->stream), "zero");
+    CK(cudaMemsetAsync(h.dev.AAt, 0, (size_t)h.M * h.p * h.p * 8, c->stream), "zero");
+  }
+  edaa_status st = enqueue(c, MODE_INIT, 0, nullptr);
+  if (st != EDAA_OK) return st;
+  c->outer_done = 0;
+  return EDAA_OK;
+}
+
+static edaa_status sync_status(edaa_ctx* c) {
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  int st = 0;
+  CK(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+  if (st & kStatTimeout) {
+    c->broken = true;
+    return fail(EDAA_ERR_TIMEOUT, "a grid barrier timed out (CTAs not co-resident?)");
+  }
+  return EDAA_OK;
+}
+
+// Autotuner: time each candidate launch shape on this cube's data (one
+// A-pass + merge and one B-pass + merge, as separate launches) and keep the
+// fastest; results are cached per (device, L, N, p, M).
+static edaa_status autotune(edaa_ctx* c) {
+  for (size_t ci = 0; ci < c->cubes.size(); ++ci) {
+    CubeHost& h = c->cubes[ci];
+    auto key = std::make_tuple(c->device, h.L, h.N, h.p, h.M);
+    auto it = tune_cache().find(key);
+    if (it != tune_cache().end()) {
+      h.tile = it->second;
+      continue;
+    }
+    std::vector<TileCfg> cands = tile_candidates(h.L, h.p, h.M);
+    TileCfg best = h.tile;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    for (const auto& t : cands) {
+      h.tile = t;
+      plan(c);
+      if (cube_smem(h) > c->smem) continue;
+      edaa_status st = push_batch(c);
+      if (st != EDAA_OK) return st;
+      st = run_init(c);
+      if (st != EDAA_OK) return st;
+      // warm-up then time 2 outer iterations with one launch per phase
+      const int persistent = c->cfg.persistent;
+      c->cfg.persistent = 0;
+      st = enqueue(c, MODE_OUTER, 1, nullptr);
+      CK(cudaEventRecord(e0, c->stream), "event");
+      if (st == EDAA_OK) st = enqueue(c, MODE_OUTER, 2, nullptr);
+      CK(cudaEventRecord(e1, c->stream), "event");
+      c->cfg.persistent = persistent;
+      if (st != EDAA_OK) return st;
+      CK(cudaEventSynchronize(e1), "event sync");
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+      if (ms < best_ms) { best_ms = ms; best = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h.tile = best;
+    tune_cache()[key] = best;
+  }
+  plan(c);
+  return push_batch(c);
+}
+
+extern "C" {
+
+void edaa_config_default(edaa_config* cfg) {
+  if (!cfg) return;
+  cfg->T = 100;
+  cfg->K1 = 5;
+  cfg->K2 = 5;
+  cfg->normalize = 1;
+  cfg->precision = EDAA_FP32;
+  cfg->fit_norm = 0;
+  cfg->coherence = 0;
+  cfg->fit_ratio = 1.05;
+  cfg->persistent = 1;
+  cfg->autotune = 0;
+  cfg->barrier_timeout_ms = 2000.0;
+  cfg->center = 1;
+}
+
+const char* edaa_last_error(void) { return g_err.c_str(); }
+
+int edaa_select_rule(const double* fit, const double* mu, int M, double fit_ratio) {
+  if (!fit || !mu || M < 1) return -1;
+  int first = -1;
+  double fmin = INFINITY;
+  for (int m = 0; m < M; ++m)
+    if (isfinite(fit[m]) && fit[m] < fmin) { fmin = fit[m]; first = m; }
+  if (first < 0) return -1;
+  int best = -1;
+  for (int m = 0; m < M; ++m) {
+    if (!isfinite(fit[m]) || !(fit[m] <= fit_ratio * fmin)) continue;
+    if (best < 0 || mu[m] < mu[best]) best = m;
+  }
+  return best;
+}
+
+edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const edaa_config* cfg, void* stream) {
+  g_err.clear();
+  if (!out) return fail(EDAA_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cubes || n_cubes < 1 || n_cubes > kMaxCubes) return fail(EDAA_ERR_ARG, "n_cubes must be 1..16");
+  edaa_config conf;
+  edaa_config_default(&conf);
+  if (cfg) conf = *cfg;
+  if (conf.T < 0 || conf.K1 < 0 || conf.K2 < 0) return fail(EDAA_ERR_ARG, "T, K1, K2 must be >= 0");
+  if (!(conf.fit_ratio >= 1.0)) return fail(EDAA_ERR_ARG, "fit_ratio must be >= 1");
+  if (conf.precision != EDAA_FP32)
+    return fail(EDAA_ERR_UNSUPPORTED, "only EDAA_FP32 contractions are available in this build");
+  for (int i = 0; i < n_cubes; ++i) {
+    const edaa_cube& q = cubes[i];
+    if (!q.X) return fail(EDAA_ERR_ARG, "cube X is NULL");
+    if (q.L < 1 || q.L > kMaxL) return fail(q.L < 1 ? EDAA_ERR_ARG : EDAA_ERR_UNSUPPORTED, "L must be 1..319");
+    if (q.p < 1 || q.p > kMaxP) return fail(q.p < 1 ? EDAA_ERR_ARG : EDAA_ERR_UNSUPPORTED, "p must be 1..8");
+    if (q.N < q.p) return fail(EDAA_ERR_ARG, "N must be >= p");
+    if (q.M < 1) return fail(EDAA_ERR_ARG, "M must be >= 1");
+    if (!q.seeds || !q.gammas) return fail(EDAA_ERR_ARG, "seeds and gammas are required");
+    for (int m = 0; m < q.M; ++m)
+      if (!(q.gammas[m] > 0.0) || !isfinite(q.gammas[m])) return fail(EDAA_ERR_ARG, "gammas must be finite and > 0");
+  }
+  edaa_ctx* c = new edaa_ctx();
+  c->cfg = conf;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "device attribute");
+  }
+  c->stream = (cudaStream_t)stream;
+  if (c->stream == nullptr || c->stream == cudaStreamLegacy) {
+    e = cudaStreamCreate(&c->stream);  // blocking: ordered with the legacy stream
+    if (e != cudaSuccess) {
+      delete c;
+      return cuda_fail(e, "stream create");
+    }
+    c->own_stream = true;
+  }
+  memset(&c->hb, 0, sizeof(Batch));
+  c->hb.n_cubes = n_cubes;
+  c->hb.K1 = conf.K1;
+  c->hb.K2 = conf.K2;
+  c->hb.coh_mode = conf.coherence;
+  c->hb.timeout_ns = (long long)(conf.barrier_timeout_ms * 1e6);
+  for (int i = 0; i < n_cubes; ++i) {
+    CubeHost h;
+    const edaa_cube& q = cubes[i];
+    h.L = q.L; h.N = q.N; h.p = q.p; h.M = q.M;
+    h.Ls = padded_ld(q.L);
+    h.Lr = round_up(q.L, 4);
+    h.Mp = q.M * q.p;
+    h.seeds.assign(q.seeds, q.seeds + q.M);
+    h.gammas.assign(q.gammas, q.gammas + q.M);
+    h.tile = default_tile(q.L, q.p, q.M);
+    memset(&h.dev, 0, sizeof(CubeDev));
+    c->cubes.push_back(h);
+  }
+  // shared memory and occupancy: the largest need over cubes and candidates
+  size_t smem = 0;
+  for (auto& h : c->cubes) {
+    smem = std::max(smem, tile_smem(h.tile, h.L, h.p));
+    if (conf.autotune)
+      for (const auto& t : tile_candidates(h.L, h.p, h.M)) smem = std::max(smem, tile_smem(t, h.L, h.p));
+  }
+  smem = std::max(smem, (size_t)32 * 1024);
+  c->smem = smem;
+  auto bail = [&](edaa_status st) {
+    edaa_destroy(c);
+    return st;
+  };
+  e = set_program_smem(smem);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "set shared memory"));
+  int bps = 0;
+  e = program_occupancy(&bps, smem);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "occupancy"));
+  if (bps < 1) return bail(fail(EDAA_ERR_UNSUPPORTED, "kernel does not fit on an SM"));
+  c->blocks_per_sm = bps;
+  plan(c);
+  const int Gcap = c->sm_count * c->blocks_per_sm;
+  for (auto& h : c->cubes) {
+    const int ntiles_min = (h.N + 31) / 32;
+    const int Pg_cap = std::max(1, std::min(Gcap, ntiles_min));
+    h.arena_bytes = arena_layout(h, Pg_cap, false);
+    e = cudaMalloc(&h.arena, h.arena_bytes);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    arena_layout(h, Pg_cap, true);
+  }
+  e = cudaMalloc(&c->d_batch, sizeof(Batch));
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+  e = cudaMalloc(&c->d_status, 64);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+  c->d_bar = (unsigned*)(c->d_status + 4);
+  c->hb.status = c->d_status;
+  c->hb.bar = c->d_bar;
+  for (size_t i = 0; i < c->cubes.size(); ++i) {
+    CubeHost& h = c->cubes[i];
+    e = cudaMemcpyAsync((void*)h.dev.seeds, h.seeds.data(), h.M * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "copy seeds"));
+    e = cudaMemcpyAsync((void*)h.dev.gammas, h.gammas.data(), h.M * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "copy gammas"));
+    edaa_status st = upload_x(c, h, cubes[i].X);
+    if (st != EDAA_OK) return bail(st);
+  }
+  edaa_status st = push_batch(c);
+  if (st != EDAA_OK) return bail(st);
+  if (conf.autotune) {
+    st = autotune(c);
+    if (st != EDAA_OK) return bail(st);
+  }
+  st = run_init(c);
+  if (st != EDAA_OK) return bail(st);
+  *out = c;
+  return EDAA_OK;
+}
+
+edaa_status edaa_reset(edaa_ctx* c, int cube, const float* X) {
+  if (!c) return fail(EDAA_ERR_ARG, "ctx is NULL");
+  edaa_status st = check_status(c);
+  if (st != EDAA_OK) return st;
+  if (X) {
+    if (cube < 0 || cube >= (int)c->cubes.size()) return fail(EDAA_ERR_ARG, "cube index out of range");
+    st = upload_x(c, c->cubes[cube], X);
+    if (st != EDAA_OK) return st;
+  } else if (cube < -1 || cube >= (int)c->cubes.size()) {
+    return fail(EDAA_ERR_ARG, "cube index out of range");
+  }
+  return run_init(c);
+}
+
+edaa_status edaa_step(edaa_ctx* c, int n_outer) {
+  if (!c) return fail(EDAA_ERR_ARG, "ctx is NULL");
+  if (n_outer < 0) return fail(EDAA_ERR_ARG, "n_outer must be >= 0");
+  edaa_status st = check_status(c);
+  if (st != EDAA_OK) return st;
+  st = enqueue(c, MODE_OUTER, n_outer, nullptr);
+  if (st == EDAA_OK) c->outer_done += n_outer;
+  return st;
+}
+
+edaa_status edaa_solve(edaa_ctx* c) {
+  if (!c) return fail(EDAA_ERR_ARG, "ctx is NULL");
+  edaa_status st = check_status(c);
+  if (st != EDAA_OK) return st;
+  const int n = std::max(0, c->cfg.T - c->outer_done);
+  int launches = 0;
+  // graph: [outer iterations ; fit] captured once per n and replayed
+  if (c->graphs_ok && c->g_solve_n != n) {
+    if (c->g_solve) {
+      cudaGraphExecDestroy(c->g_solve);
+      c->g_solve = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      int l = 0;
+      edaa_status s1 = enqueue(c, MODE_OUTER, n, &l);
+      edaa_status s2 = (s1 == EDAA_OK) ? enqueue(c, MODE_FIT, 0, &l) : s1;
+      e = cudaStreamEndCapture(c->stream, &g);
+      if (e == cudaSuccess && s2 == EDAA_OK) e = cudaGraphInstantiate(&c->g_solve, g, 0);
+      else if (e == cudaSuccess) e = cudaErrorUnknown;
+      if (g) cudaGraphDestroy(g);
+      if (e == cudaSuccess) {
+        c->g_solve_n = n;
+        c->launches_last_solve = l;
+      }
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->graphs_ok = false;
+      c->g_solve = nullptr;
+    }
+  }
+  if (c->graphs_ok && c->g_solve) {
+    CK(cudaGraphLaunch(c->g_solve, c->stream), "graph launch");
+  } else {
+    st = enqueue(c, MODE_OUTER, n, &launches);
+    if (st == EDAA_OK) st = enqueue(c, MODE_FIT, 0, &launches);
+    if (st != EDAA_OK) return st;
+    c->launches_last_solve = launches;
+  }
+  c->outer_done += n;
+  return EDAA_OK;
+}
+
+edaa_status edaa_sync(edaa_ctx* c) {
+  if (!c) return fail(EDAA_ERR_ARG, "ctx is NULL");
+  edaa_status st = check_status(c);
+  if (st != EDAA_OK) return st;
+  return sync_status(c);
+}
+
+edaa_status edaa_select(edaa_ctx* c, int cube, int* best, double* fit, double* mu) {
+  if (!c || !best) return fail(EDAA_ERR_ARG, "ctx and best are required");
+  if (cube < 0 || cube >= (int)c->cubes.size()) return fail(EDAA_ERR_ARG, "cube index out of range");
+  edaa_status st = edaa_sync(c);
+  if (st != EDAA_OK) return st;
+  CubeHost& h = c->cubes[cube];
+  std::vector<double> f(h.M), m(h.M);
+  CK(cudaMemcpy(f.data(), c->cfg.fit_norm ? h.dev.fitmax : h.dev.fit, h.M * 8, cudaMemcpyDeviceToHost), "read fit");
+  CK(cudaMemcpy(m.data(), h.dev.mu, h.M * 8, cudaMemcpyDeviceToHost), "read mu");
+  if (fit) memcpy(fit, f.data(), h.M * 8);
+  if (mu) memcpy(mu, m.data(), h.M * 8);
+  *best = edaa_select_rule(f.data(), m.data(), h.M, c->cfg.fit_ratio);
+  if (*best < 0) return fail(EDAA_ERR_NONFINITE, "no run has a finite fit");
+  return EDAA_OK;
+}
+
+edaa_status edaa_get(edaa_ctx* c, int cube, int run, float* E, float* A, float* B) {
+  if (!c) return fail(EDAA_ERR_ARG, "ctx is NULL");
+  if (cube < 0 || cube >= (int)c->cubes.size()) return fail(EDAA_ERR_ARG, "cube index out of range");
+  CubeHost& h = c->cubes[cube];
+  if (run < 0 || run >= h.M) return fail(EDAA_ERR_ARG, "run index out of range");
+  edaa_status st = check_status(c);
+  if (st != EDAA_OK) return st;
+  // outputs may be host memory: gather into device scratch, then copy
+  cudaPointerAttributes pa;
+  auto is_dev = [&](const void* p) {
+    if (!p) return true;
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+  };
+  const bool dE = is_dev(E), dA = is_dev(A), dB = is_dev(B);
+  if (dE && dA && dB) {
+    CK(launch_gather(h.dev, run, E, A, B, c->stream), "gather");
+    return EDAA_OK;
+  }
+  const size_t nE = (size_t)h.L * h.p, nA = (size_t)h.N * h.p;
+  float* tmp = nullptr;
+  CK(cudaMallocAsync((void**)&tmp, (nE + 2 * nA) * 4, c->stream), "scratch");
+  float* tE = E ? (dE ? E : tmp) : nullptr;
+  float* tA = A ? (dA ? A : tmp + nE) : nullptr;
+  float* tB = B ? (dB ? B : tmp + nE + nA) : nullptr;
+  CK(launch_gather(h.dev, run, tE, tA, tB, c->stream), "gather");
+  if (E && !dE) CK(cudaMemcpyAsync(E, tE, nE * 4, cudaMemcpyDeviceToHost, c->stream), "copy E");
+  if (A && !dA) CK(cudaMemcpyAsync(A, tA, nA * 4, cudaMemcpyDeviceToHost, c->stream), "copy A");
+  if (B && !dB) CK(cudaMemcpyAsync(B, tB, nA * 4, cudaMemcpyDeviceToHost, c->stream), "copy B");
+  CK(cudaFreeAsync(tmp, c->stream), "free scratch");
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  return EDAA_OK;
+}
+
+edaa_status edaa_grad(edaa_ctx* c, int cube, int run, float* gA, float* gB) {
+  if (!c) return fail(EDAA_ERR_ARG, "ctx is NULL");
+  if (cube < 0 || cube >= (int)c->cubes.size()) return fail(EDAA_ERR_ARG, "cube index out of range");
+  CubeHost& h = c->cubes[cube];
+  if (run < 0 || run >= h.M) return fail(EDAA_ERR_ARG, "run index out of range");
+  edaa_status st = check_status(c);
+  if (st != EDAA_OK) return st;
+  const size_t n = (size_t)h.N * h.p;
+  float* tmp = nullptr;
+  CK(cudaMallocAsync((void**)&tmp, 2 * n * 4, c->stream), "scratch");
+  const CubeDev* dcube = reinterpret_cast<const CubeDev*>(reinterpret_cast<const char*>(c->d_batch) +
+                                                          offsetof(Batch, c) + (size_t)cube * sizeof(CubeDev));
+  CK(launch_grad(dcube, h.dev, run, gA ? tmp : nullptr, gB ? tmp + n : nullptr, c->stream), "grad");
+  if (gA) CK(cudaMemcpyAsync(gA, tmp, n * 4, cudaMemcpyDefault, c->stream), "copy gA");
+  if (gB) CK(cudaMemcpyAsync(gB, tmp + n, n * 4, cudaMemcpyDefault, c->stream), "copy gB");
+  CK(cudaFreeAsync(tmp, c->stream), "free scratch");
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  return EDAA_OK;
+}
+
+edaa_status edaa_loss(edaa_ctx* c, int cube, double* loss) {
+  if (!c || !loss) return fail(EDAA_ERR_ARG, "ctx and loss are required");
+  if (cube < 0 || cube >= (int)c->cubes.size()) return fail(EDAA_ERR_ARG, "cube index out of range");
+  edaa_status st = check_status(c);
+  if (st != EDAA_OK) return st;
+  st = enqueue(c, MODE_FIT, 0, nullptr);
+  if (st != EDAA_OK) return st;
+  st = sync_status(c);
+  if (st != EDAA_OK) return st;
+  CubeHost& h = c->cubes[cube];
+  CK(cudaMemcpy(loss, h.dev.loss2, h.M * 8, cudaMemcpyDeviceToHost), "read loss");
+  return EDAA_OK;
+}
+
+edaa_status edaa_step_sizes(edaa_ctx* c, int cube, double* eta1, double* eta2) {
+  if (!c) return fail(EDAA_ERR_ARG, "ctx is NULL");
+  if (cube < 0 || cube >= (int)c->cubes.size()) return fail(EDAA_ERR_ARG, "cube index out of range");
+  edaa_status st = edaa_sync(c);
+  if (st != EDAA_OK) return st;
+  CubeHost& h = c->cubes[cube];
+  if (eta1) CK(cudaMemcpy(eta1, h.dev.eta1d, h.M * 8, cudaMemcpyDeviceToHost), "read eta1");
+  if (eta2) CK(cudaMemcpy(eta2, h.dev.eta2d, h.M * 8, cudaMemcpyDeviceToHost), "read eta2");
+  return EDAA_OK;
+}
+
+int edaa_outer_done(const edaa_ctx* c) { return c ? c->outer_done : -1; }
+
+edaa_status edaa_describe(const edaa_ctx* c, int cube, int* runs_per_group, int* pixel_tile, int* ctas_per_group,
+                          int* grid, int* launches_per_solve) {
+  if (!c) return fail(EDAA_ERR_ARG, "ctx is NULL");
+  if (cube < 0 || cube >= (int)c->cubes.size()) return fail(EDAA_ERR_ARG, "cube index out of range");
+  const CubeHost& h = c->cubes[cube];
+  if (runs_per_group) *runs_per_group = h.tile.Rm;
+  if (pixel_tile) *pixel_tile = h.Nt;
+  if (ctas_per_group) *ctas_per_group = h.Pg;
+  if (grid) *grid = c->grid;
+  if (launches_per_solve) *launches_per_solve = c->launches_last_solve;
+  return EDAA_OK;
+}
+
+void edaa_destroy(edaa_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->g_solve) cudaGraphExecDestroy(c->g_solve);
+  for (auto& h : c->cubes)
+    if (h.arena) cudaFree(h.arena);
+  if (c->d_batch) cudaFree(c->d_batch);
+  if (c->d_status) cudaFree(c->d_status);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+edaa_status edaa_selftest_barrier(int grid, int extra, double timeout_ms, void* stream) {
+  if (grid < 1 || grid > 4096 || extra < 0) return fail(EDAA_ERR_ARG, "grid must be 1..4096, extra >= 0");
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+  if (grid > sms) return fail(EDAA_ERR_ARG, "grid must not exceed the SM count (co-residency)");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* buf = nullptr;
+  CK(cudaMalloc(&buf, 64), "cudaMalloc");
+  cudaError_t e = cudaMemsetAsync(buf, 0, 64, s);
+  if (e == cudaSuccess)
+    e = launch_barrier_test((unsigned*)(buf + 4), buf, grid, grid + extra, (long long)(timeout_ms * 1e6), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, buf, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "barrier self-test");
+  if (st & kStatTimeout) return fail(EDAA_ERR_TIMEOUT, "barrier timed out as expected");
+  return EDAA_OK;
+}
+
+}  // extern "C"

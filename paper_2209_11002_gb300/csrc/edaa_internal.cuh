@@ -1,0 +1,160 @@
+// Internal declarations shared by the CUDA translation units of libedaa.
+// Layouts (all device memory, row-major):
+//   X     N x Ls float32, pixel i's L bands contiguous, CENTRED: the mean
+//         pixel xbar (of the l2-normalised pixels) is subtracted.  EDAA's
+//         iterates do not change under a common translation of the pixels
+//         (the gradients change by a constant per softmax column, which the
+//         softmax removes), and centring removes the large cancelling terms
+//         of R = E (A A^T) - X A^T.  E is kept centred too; xbar is added
+//         back wherever the paper's uncentred E is needed (step sizes,
+//         coherence, outputs, reported gradients).  Column L holds 1.0
+//         (a "ones band": contracting it with the softmax weights yields the
+//         softmax denominators for free), columns L+1..Ls-1 are zero.
+//         Ls = smallest multiple of 4 >= L+1 with Ls/4 odd, so 16-byte rows
+//         and conflict-free 128-bit shared-memory reads across pixels.
+//   logA  N x Mp   z = log a - max_j log a per pixel and run (A = softmax_j z);
+//                  column m*p+j is abundance j of run m, pixel-major
+//   logB  N x Mp   logits u of B in the frame log(N b): B = exp(u - lse - log N)
+//                  with lse stored as (log-sum-exp - log N); both stay near 0
+//                  while B is near uniform, where float32 spacing is finest
+//   Ef/Ed L x Mp   E = X B (float32 panel and float64 master copy)
+//   Rf    L x Mp   R = E (A A^T) - X A^T, the factor of the B-gradient X^T R
+//   XAt   L x Mp   X A^T (float64), AAt M x p x p (float64)
+//   part  Pg x (L+1) x Mp  per-CTA partial sums of X W (row L: sum of W)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace edaa {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxCubes = 16;
+constexpr int kMaxP = 8;
+constexpr int kMaxL = 319;
+
+// device status bits
+constexpr int kStatTimeout = 1;
+
+// kernel programs (sequences of phases)
+enum Mode { MODE_OUTER = 0, MODE_INIT = 1, MODE_FIT = 2 };
+enum Phase {
+  PH_A = 0,      // A-pass: K1 fused A-steps per pixel, partials of X A^T, A A^T
+  PH_AM = 1,     // merge A partials; R = E AAt - XAt
+  PH_B = 2,      // B-pass: one B-step, online-softmax partials of X B
+  PH_BM = 3,     // merge B partials: E, lse, R
+  PH_INITB = 4,  // B^0 logits from SplitMix64, partials of X B^0
+  PH_INITA = 5,  // A^0 = 1/p, partials of X A^T, A A^T
+  PH_ETA = 6,    // sigma_max^2(X B^0) by Jacobi, eta1, eta2
+  PH_FIT = 7,    // residual pass: sum |r|, max column sum, sum r^2 per run
+  PH_FITM = 8,   // merge fit partials, coherence
+  PH_BM0 = 9     // merge of the B^0 partials (reference logit 0.05 instead of -log N)
+};
+
+// Shifted accumulation: the passes accumulate X (W - w_ref) instead of X W,
+// with w_ref = 1/p for A and, for B, the weight of logit 0 in the frame
+// log(N b) (the weight of a uniform column) in the power-of-two softmax frame;
+// the merge adds w_ref * sum_i x_i back in FP64.  While A or B are close to
+// uniform (the first iterations) this keeps the FP32 rounding of the partial
+// sums proportional to the small deviation from uniform instead of to the
+// full weights.
+
+struct CubeDev {
+  int L, Ls, Lr, N, p, M, Mp, LT;
+  int Rm, RG, Pg, Nt, WP1, SPT, WP2, ntiles;
+  int cta0;                    // first pass work item of this cube
+  int lchunk, nlchunk, unit0;  // merge work items: M * nlchunk from unit0
+  int run0;                    // first run index of this cube in the batch
+  float* X;
+  double* xbar;    // L: mean pixel that was subtracted (zero when centring is off)
+  double* sx;      // L+1: FP64 sum over pixels of the centred X as stored; sx[L] = N
+  float* logA;
+  float* logB;
+  float* Ef;
+  double* Ed;
+  float* Rf;
+  double* XAt;
+  double* AAt;
+  float* lse;
+  float* eta1;
+  float* eta2;
+  double* eta1d;
+  double* eta2d;
+  double* sig2;
+  float* part;
+  float* pmax;
+  float* paa;
+  double* pfit;
+  double* fit;
+  double* fitmax;
+  double* loss2;
+  double* mu;
+  const uint64_t* seeds;
+  const double* gammas;
+};
+
+struct Batch {
+  int n_cubes;
+  int pass_items;     // total pass work items (one per (cube, run group, pixel group))
+  int merge_units;    // total merge work items
+  int total_runs;
+  int K1, K2;
+  int coh_mode;
+  long long timeout_ns;
+  int* status;
+  unsigned int* bar;  // [0] arrivals, [1] generation
+  CubeDev c[kMaxCubes];
+};
+
+// Shared-memory carve-up of a pass work item (in floats).
+struct PassSmem {
+  int RgS4, RgSo, RgW;
+  int off_ps, off_gs, off_xs, off_ss, off_ws, off_col, off_run, total;
+};
+
+__host__ __device__ inline PassSmem pass_smem(int L, int Ls, int Lr, int p, int Rm, int Nt) {
+  PassSmem s;
+  const int P4 = (p + 3) & ~3;
+  s.RgS4 = Rm * P4;
+  s.RgSo = (Rm * p) | 1;
+  int rw = s.RgS4;
+  if (((rw >> 2) & 1) == 0) rw += 4;
+  s.RgW = rw;
+  int o = 0;
+  s.off_ps = o; o += Lr * s.RgS4;
+  s.off_gs = o; o += (Rm * p * p + 3) & ~3;
+  s.off_xs = o; o += Nt * Ls;
+  s.off_ss = o; o += (Nt * s.RgSo + 3) & ~3;
+  s.off_ws = o; o += Nt * s.RgW;
+  s.off_col = o; o += 4 * s.RgS4;
+  s.off_run = o; o += (2 * Rm + 3) & ~3;
+  // end-of-pass reduction buffer ((L+1) x RgS4) reuses the region from off_xs
+  const int need = s.off_xs + (L + 1) * s.RgS4 + kWarps * Rm * 36;
+  if (need > o) o = need;
+  s.total = o;
+  return s;
+}
+
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+inline int padded_ld(int L) {
+  int ls = round_up(L + 1, 4);
+  if (((ls >> 2) & 1) == 0) ls += 4;
+  return ls;
+}
+
+// Launch helpers implemented in edaa_kernels.cu.
+cudaError_t launch_program(const Batch* d_batch, int mode, int n_outer, int ph_lo, int ph_hi, int grid,
+                           size_t smem, bool cooperative, cudaStream_t stream);
+cudaError_t launch_normalize(const float* Xin, float* X, double* scale, double* bsum, double* xbar, double* sx,
+                             int L, int Ls, int N, int normalize, int center, cudaStream_t s);
+int normalize_blocks(int N);
+cudaError_t launch_grad(const CubeDev* d_cube, const CubeDev& hc, int run, float* gA, float* gB, cudaStream_t s);
+cudaError_t launch_gather(const CubeDev& hc, int run, float* E, float* A, float* B, cudaStream_t s);
+cudaError_t launch_barrier_test(unsigned int* bar, int* status, int grid, int expected, long long timeout_ns,
+                                cudaStream_t s);
+cudaError_t set_program_smem(size_t smem);
+cudaError_t program_occupancy(int* blocks_per_sm, size_t smem);
+int program_phase_count(int mode, int n_outer, int K2);
+
+}  // namespace edaa

@@ -1,0 +1,723 @@
+// Device code of the streaming passes (A-pass, B-pass, fit pass), included by
+// the per-p translation units edaa_pass_p.cu (compiled once per p = 1..8) and
+// by edaa_kernels.cu for the shared helpers.
+#pragma once
+#include <math.h>
+#include <stdint.h>
+
+#include "edaa_internal.cuh"
+
+namespace edaa {
+
+#define EDAA_INF __int_as_float(0x7f800000)
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// order-preserving float <-> int map for atomicMax on floats of any sign
+__device__ __forceinline__ int ord_key(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord_val(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+
+// The B-pass keeps its online-softmax maximum as a power-of-two exponent e
+// (weights e^u 2^-e), so every rescale between tiles and CTAs and the shifted
+// reference weight 2^-e are exact powers of two: the merge can then add the
+// reference term back without any rounding mismatch.
+constexpr float kLog2e = 1.4426950408889634f;
+__device__ __forceinline__ float tile_exp(int key) {
+  const float m = ord_val(key);
+  return m == -EDAA_INF ? m : ceilf(m * kLog2e);
+}
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output number n of the
+// generator seeded with `seed` is the variant-13 finaliser of seed + n*gamma.
+__device__ __forceinline__ uint64_t splitmix64_out(uint64_t seed, uint64_t n) {
+  uint64_t z = seed + n * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// u ~ U[0,1) with 24 bits, exact in float32 (eq. initB0)
+__device__ __forceinline__ float uniform24(uint64_t seed, uint64_t n) {
+  return (float)(splitmix64_out(seed, n) >> 40) * (1.0f / 16777216.0f);
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  int v;
+  asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded grid barrier: generation counter + arrival counter.  A CTA that
+// waits longer than timeout_ns, or sees another CTA's time-out, sets the
+// status bit and returns false so that the kernel can exit; it never traps.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned expected, int* status, long long timeout_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned gen = ld_acquire_u32(bar + 1);
+    __threadfence();
+    const unsigned prev = atomicAdd(bar, 1u);
+    if (prev + 1u == expected) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire_u32(bar + 1) == gen) {
+        if (ld_volatile_i32(status) & kStatTimeout) { ok = 0; break; }
+        if ((long long)(global_ns() - t0) > timeout_ns) {
+          atomicOr(status, kStatTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Pass work item: one CTA, one run group (Rm runs), pixel tiles pg, pg+Pg, ...
+// Template: P endmembers, LT = ceil((L+1)/32) l-values per lane in phase 2.
+// ---------------------------------------------------------------------------
+template <int P>
+struct PassTraits {
+  static constexpr int P4 = (P + 3) & ~3;
+  static constexpr int PP = P * (P + 1) / 2;
+  static constexpr int RQ1M = (P <= 2) ? 4 : (P <= 4 ? 2 : 1);  // runs per warp, phase 1
+  static constexpr int SPTM = (P <= 4) ? 2 : 1;                  // pixels per lane, phase 1
+  static constexpr int RQ2M = (P <= 2) ? 4 : (P <= 4 ? 2 : 1);  // runs per warp, phase 2
+};
+
+template <int P>
+__device__ __forceinline__ void load_p4(const float* src, float (&v)[PassTraits<P>::P4]) {
+#pragma unroll
+  for (int h = 0; h < PassTraits<P>::P4 / 4; ++h) {
+    const float4 t = *reinterpret_cast<const float4*>(src + 4 * h);
+    v[4 * h + 0] = t.x;
+    v[4 * h + 1] = t.y;
+    v[4 * h + 2] = t.z;
+    v[4 * h + 3] = t.w;
+  }
+}
+
+__device__ __forceinline__ float f4c(const float4& v, int d) {
+  return d == 0 ? v.x : (d == 1 ? v.y : (d == 2 ? v.z : v.w));
+}
+
+// kind: 0 = A-pass (K1 steps; init => A^0), 1 = B-pass (init => B^0 logits)
+template <int P, int LT, bool IS_A>
+__device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeDev& cd, int rg, int pg,
+                                       float* smem, int K1, bool init) {
+  using TR = PassTraits<P>;
+  constexpr int P4 = TR::P4;
+  constexpr int PP = TR::PP;
+  constexpr int RQ1M = TR::RQ1M;
+  constexpr int SPTM = TR::SPTM;
+  constexpr int RQ2M = TR::RQ2M;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int L = cd.L, Ls = cd.Ls, Lr = cd.Lr, N = cd.N, Mp = cd.Mp, Rm = cd.Rm;
+  const int m0 = rg * Rm;
+  const int nr = min(Rm, cd.M - m0);
+  const int c0 = m0 * P, nc = nr * P;
+  const int Nt = cd.Nt;
+  const int WP1 = cd.WP1, WR1 = kWarps / WP1, SPT = cd.SPT;
+  const int WP2 = cd.WP2, WR2 = kWarps / WP2;
+  const int RQ1 = (Rm + WR1 - 1) / WR1, RQ2 = (Rm + WR2 - 1) / WR2;
+  const PassSmem sm = pass_smem(L, Ls, Lr, P, Rm, Nt);
+  float* Ps = smem + sm.off_ps;
+  float* Gs = smem + sm.off_gs;
+  float* Xs = smem + sm.off_xs;
+  float* Ss = smem + sm.off_ss;
+  float* Ws = smem + sm.off_ws;
+  float* colLse = smem + sm.off_col;
+  float* colM = colLse + sm.RgS4;
+  int* colKey = reinterpret_cast<int*>(colM + sm.RgS4);
+  float* runEta = smem + sm.off_run;
+  const int RgS4 = sm.RgS4, RgSo = sm.RgSo, RgW = sm.RgW;
+
+  // ---- stage the panel (E for A, R for B), per-run step sizes, column stats
+  const bool need_panel = !init;
+  if (need_panel) {
+    const float* panel = IS_A ? cd.Ef : cd.Rf;
+    for (int e = tid; e < Lr * RgS4; e += kThreads) {
+      const int l = e / RgS4, cc = e - l * RgS4, r = cc / P4, j = cc - r * P4;
+      float v = 0.f;
+      if (l < L && r < nr && j < P) v = panel[(size_t)l * Mp + c0 + r * P + j];
+      Ps[e] = v;
+    }
+  }
+  if (tid < Rm) runEta[tid] = (tid < nr) ? (IS_A ? cd.eta1[m0 + tid] : cd.eta2[m0 + tid]) : 0.f;
+  if (!IS_A) {
+    for (int c = tid; c < RgS4; c += kThreads) {
+      const int r = c / P4, j = c - r * P4;
+      colLse[c] = (!init && r < nr && j < P) ? cd.lse[c0 + r * P + j] : 0.f;
+      colM[c] = -EDAA_INF;
+      colKey[c] = ord_key(-EDAA_INF);
+    }
+  }
+  __syncthreads();
+  if (IS_A && need_panel && K1 > 0) {
+    for (int e = tid; e < nr * P * P; e += kThreads) {
+      const int r = e / (P * P), jk = e - r * P * P, j = jk / P, k = jk - j * P;
+      float s = 0.f;
+      for (int l = 0; l < L; ++l) s = fmaf(Ps[l * RgS4 + r * P4 + j], Ps[l * RgS4 + r * P4 + k], s);
+      Gs[e] = s;
+    }
+    __syncthreads();
+  }
+
+  const int wp = warp % WP1, wr = warp / WP1;
+  const int wp2 = warp % WP2, wr2 = warp / WP2;
+
+  float acc[LT][RQ2M][P];
+#pragma unroll
+  for (int k = 0; k < LT; ++k)
+#pragma unroll
+    for (int q = 0; q < RQ2M; ++q)
+#pragma unroll
+      for (int j = 0; j < P; ++j) acc[k][q][j] = 0.f;
+  float aa[RQ1M][PP];
+#pragma unroll
+  for (int q = 0; q < RQ1M; ++q)
+#pragma unroll
+    for (int e = 0; e < PP; ++e) aa[q][e] = 0.f;
+
+  float* St = IS_A ? cd.logA : cd.logB;
+  const float4* Xs4 = reinterpret_cast<const float4*>(Xs);
+  const float aref = 1.f / (float)P;  // A reference weight
+
+  for (int tile = pg; tile < cd.ntiles; tile += cd.Pg) {
+    const int i0 = tile * Nt;
+    const int ni = min(Nt, N - i0);
+    {  // X tile: ni contiguous rows of Ls floats; rows >= ni zero
+      const float4* Xg = reinterpret_cast<const float4*>(cd.X + (size_t)i0 * Ls);
+      float4* xs4 = reinterpret_cast<float4*>(Xs);
+      const int n4 = ni * (Ls >> 2), nt4 = Nt * (Ls >> 2);
+      for (int e = tid; e < nt4; e += kThreads) xs4[e] = (e < n4) ? __ldg(Xg + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (!init) {
+      for (int e = tid; e < ni * nc; e += kThreads) {
+        const int i = e / nc, cc = e - i * nc;
+        Ss[i * RgSo + cc] = St[(size_t)(i0 + i) * Mp + c0 + cc];
+      }
+    }
+    __syncthreads();
+
+    // ---- phase 1: c = P^T x_i per (pixel, run), then the element-wise update
+    float cr[SPTM][RQ1M][P];
+#pragma unroll
+    for (int s = 0; s < SPTM; ++s)
+#pragma unroll
+      for (int q = 0; q < RQ1M; ++q)
+#pragma unroll
+        for (int j = 0; j < P; ++j) cr[s][q][j] = 0.f;
+    if (need_panel && (!IS_A || K1 > 0)) {
+      for (int l = 0; l < Lr; l += 4) {
+        float4 xv[SPTM];
+#pragma unroll
+        for (int s = 0; s < SPTM; ++s) {
+          if (s < SPT) {
+            const int il = lane + 32 * (wp + WP1 * s);
+            xv[s] = Xs4[(il * Ls + l) >> 2];
+          } else {
+            xv[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < RQ1M; ++q) {
+          const int r = wr + WR1 * q;
+          if (q < RQ1 && r < nr) {
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+              float pv[P4];
+              load_p4<P>(Ps + (l + d) * RgS4 + r * P4, pv);
+#pragma unroll
+              for (int s = 0; s < SPTM; ++s) {
+                const float x = f4c(xv[s], d);
+#pragma unroll
+                for (int j = 0; j < P; ++j) cr[s][q][j] = fmaf(x, pv[j], cr[s][q][j]);
+              }
+            }
+          }
+        }
+      }
+    }
+
+    if (IS_A) {
+#pragma unroll
+      for (int s = 0; s < SPTM; ++s) {
+        if (s >= SPT) continue;
+        const int il = lane + 32 * (wp + WP1 * s);
+        const bool valid = il < ni;
+#pragma unroll
+        for (int q = 0; q < RQ1M; ++q) {
+          const int r = wr + WR1 * q;
+          if (!(q < RQ1 && r < nr)) continue;
+          // z = log a - max_j log a (max-normalised log abundances; 0 for uniform a)
+          float z[P];
+#pragma unroll
+          for (int j = 0; j < P; ++j) z[j] = init ? 0.f : (valid ? Ss[il * RgSo + r * P + j] : 0.f);
+          const float* G = Gs + r * P * P;
+          const float eta = runEta[r];
+          float ea[P];
+          float se = 0.f;
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            ea[j] = expf(z[j]);
+            se += ea[j];
+          }
+          for (int kk = 0; kk < K1; ++kk) {
+            // eq. (update_A) in softmax form: a+ = softmax(log a - eta (G a - c))
+            const float inv = 1.f / se;
+            float a[P];
+#pragma unroll
+            for (int j = 0; j < P; ++j) a[j] = ea[j] * inv;
+            float mx = -EDAA_INF;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              float g = -cr[s][q][j];
+#pragma unroll
+              for (int k = 0; k < P; ++k) g = fmaf(G[j * P + k], a[k], g);
+              z[j] = fmaf(-eta, g, z[j]);
+              mx = fmaxf(mx, z[j]);
+            }
+            se = 0.f;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              z[j] -= mx;
+              ea[j] = expf(z[j]);
+              se += ea[j];
+            }
+          }
+          // a_j = e^{z_j} / sum_k e^{z_k}.  The accumulated deviation a_j - 1/p is
+          // formed from d = expm1(z), exact to float rounding near uniform a
+          // (where a_j - 1/p itself is small): a_j - 1/p = (p d_j - sd) / (p (p + sd)).
+          float d[P];
+          float sd = 0.f;
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            d[j] = expm1f(z[j]);
+            sd += d[j];
+          }
+          const float den = 1.f / ((float)P + sd);
+          float a[P4], wa[P4];
+#pragma unroll
+          for (int j = 0; j < P4; ++j) {
+            const int jj = j < P ? j : 0;
+            a[j] = (j < P && valid) ? (1.f + d[jj]) * den : 0.f;
+            wa[j] = (j < P && valid) ? ((float)P * d[jj] - sd) * den * aref : 0.f;  // a - 1/p
+          }
+          if (valid) {
+#pragma unroll
+            for (int j = 0; j < P; ++j) Ss[il * RgSo + r * P + j] = z[j];
+          }
+#pragma unroll
+          for (int h = 0; h < P4 / 4; ++h)
+            *reinterpret_cast<float4*>(Ws + il * RgW + r * P4 + 4 * h) =
+                make_float4(wa[4 * h], wa[4 * h + 1], wa[4 * h + 2], wa[4 * h + 3]);
+          int e = 0;
+#pragma unroll
+          for (int j = 0; j < P; ++j)
+#pragma unroll
+            for (int k = j; k < P; ++k) aa[q][e++] += a[j] * a[k];
+        }
+      }
+      __syncthreads();
+    } else {
+      float ur[SPTM][RQ1M][P];
+#pragma unroll
+      for (int s = 0; s < SPTM; ++s) {
+        const int il = lane + 32 * (wp + WP1 * s);
+        const bool valid = (s < SPT) && il < ni;
+#pragma unroll
+        for (int q = 0; q < RQ1M; ++q) {
+          const int r = wr + WR1 * q;
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            float u = -EDAA_INF;
+            if (valid && q < RQ1 && r < nr) {
+              if (init) {
+                u = 0.1f * uniform24(cd.seeds[m0 + r], (uint64_t)(i0 + il) * P + j + 1);
+              } else {
+                u = Ss[il * RgSo + r * P + j] - colLse[r * P4 + j] - runEta[r] * cr[s][q][j];
+              }
+            }
+            ur[s][q][j] = u;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < RQ1M; ++q) {
+        const int r = wr + WR1 * q;
+        if (!(q < RQ1 && r < nr)) continue;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          float m = ur[0][q][j];
+#pragma unroll
+          for (int s = 1; s < SPTM; ++s) m = fmaxf(m, ur[s][q][j]);
+          m = warp_max(m);
+          if (lane == 0) atomicMax(&colKey[r * P4 + j], ord_key(m));
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < SPTM; ++s) {
+        if (s >= SPT) continue;
+        const int il = lane + 32 * (wp + WP1 * s);
+        const bool valid = il < ni;
+#pragma unroll
+        for (int q = 0; q < RQ1M; ++q) {
+          const int r = wr + WR1 * q;
+          if (!(q < RQ1 && r < nr)) continue;
+          float w[P4];
+#pragma unroll
+          for (int j = 0; j < P4; ++j) {
+            w[j] = 0.f;
+            if (j < P && valid) {
+              const int c = r * P4 + j;
+              const float Mn = fmaxf(colM[c], tile_exp(colKey[c]));  // power-of-two frame
+              // w = e^u 2^-Mn minus the reference weight 2^-Mn (logit 0: uniform b);
+              // near u = 0 the difference is 2^-Mn expm1(u), exact to rounding
+              const float u = ur[s][q][j];
+              w[j] = (fabsf(u) < 1.f) ? ldexpf(expm1f(u), -(int)Mn)
+                                      : exp2f(fmaf(u, kLog2e, -Mn)) - ldexpf(1.f, -(int)Mn);
+            }
+          }
+          if (valid) {
+#pragma unroll
+            for (int j = 0; j < P; ++j) Ss[il * RgSo + r * P + j] = ur[s][q][j];
+          }
+#pragma unroll
+          for (int h = 0; h < P4 / 4; ++h)
+            *reinterpret_cast<float4*>(Ws + il * RgW + r * P4 + 4 * h) =
+                make_float4(w[4 * h], w[4 * h + 1], w[4 * h + 2], w[4 * h + 3]);
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- write the new state back (coalesced rows)
+    for (int e = tid; e < ni * nc; e += kThreads) {
+      const int i = e / nc, cc = e - i * nc;
+      St[(size_t)(i0 + i) * Mp + c0 + cc] = Ss[i * RgSo + cc];
+    }
+
+    // ---- phase 2: acc[l][c] += sum_i X[i][l] W[i][c]  (l = 0..L, row L = ones band)
+    if (!IS_A) {
+#pragma unroll
+      for (int q = 0; q < RQ2M; ++q) {
+        const int r = wr2 + WR2 * q;
+        if (!(q < RQ2 && r < nr)) continue;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          const int c = r * P4 + j;
+          const float Mo = colM[c];
+          const float Mn = fmaxf(Mo, tile_exp(colKey[c]));
+          // exact rescale by a power of two (0 while nothing was accumulated)
+          const float sc = (Mo == Mn) ? 1.f : (Mo == -EDAA_INF ? 0.f : ldexpf(1.f, (int)(Mo - Mn)));
+#pragma unroll
+          for (int k = 0; k < LT; ++k) acc[k][q][j] *= sc;
+        }
+      }
+    }
+    for (int i = wp2; i < ni; i += WP2) {
+      float xv[LT];
+#pragma unroll
+      for (int k = 0; k < LT; ++k) {
+        const int l = lane + 32 * k;
+        xv[k] = (l <= L) ? Xs[i * Ls + l] : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < RQ2M; ++q) {
+        const int r = wr2 + WR2 * q;
+        if (!(q < RQ2 && r < nr)) continue;
+        float w[P4];
+        load_p4<P>(Ws + i * RgW + r * P4, w);
+#pragma unroll
+        for (int k = 0; k < LT; ++k)
+#pragma unroll
+          for (int j = 0; j < P; ++j) acc[k][q][j] = fmaf(xv[k], w[j], acc[k][q][j]);
+      }
+    }
+    __syncthreads();
+    if (!IS_A) {
+      for (int c = tid; c < RgS4; c += kThreads) {
+        colM[c] = fmaxf(colM[c], tile_exp(colKey[c]));
+        colKey[c] = ord_key(-EDAA_INF);
+      }
+    }
+  }  // tiles
+
+  // ---- end of pass: reduce phase-2 accumulators over pixel groups, write partials
+  float* buf = Xs;
+  for (int g = WP2 - 1; g >= 1; --g) {
+    __syncthreads();
+    if (wp2 == g) {
+#pragma unroll
+      for (int q = 0; q < RQ2M; ++q) {
+        const int r = wr2 + WR2 * q;
+        if (!(q < RQ2 && r < nr)) continue;
+#pragma unroll
+        for (int k = 0; k < LT; ++k) {
+          const int l = lane + 32 * k;
+          if (l <= L) {
+#pragma unroll
+            for (int j = 0; j < P; ++j) buf[l * RgS4 + r * P4 + j] = acc[k][q][j];
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (wp2 == 0) {
+#pragma unroll
+      for (int q = 0; q < RQ2M; ++q) {
+        const int r = wr2 + WR2 * q;
+        if (!(q < RQ2 && r < nr)) continue;
+#pragma unroll
+        for (int k = 0; k < LT; ++k) {
+          const int l = lane + 32 * k;
+          if (l <= L) {
+#pragma unroll
+            for (int j = 0; j < P; ++j) acc[k][q][j] += buf[l * RgS4 + r * P4 + j];
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (wp2 == 0) {
+    float* part = cd.part + (size_t)pg * (L + 1) * Mp;
+#pragma unroll
+    for (int q = 0; q < RQ2M; ++q) {
+      const int r = wr2 + WR2 * q;
+      if (!(q < RQ2 && r < nr)) continue;
+#pragma unroll
+      for (int k = 0; k < LT; ++k) {
+        const int l = lane + 32 * k;
+        if (l <= L) {
+#pragma unroll
+          for (int j = 0; j < P; ++j) part[(size_t)l * Mp + c0 + r * P + j] = acc[k][q][j];
+        }
+      }
+    }
+  }
+  if (IS_A) {
+    // A A^T: sum over lanes (fixed butterfly), then over the WP1 warps of a run set
+    float* abuf = buf + (L + 1) * RgS4;  // kWarps x Rm x 36 floats
+#pragma unroll
+    for (int q = 0; q < RQ1M; ++q) {
+      const int r = wr + WR1 * q;
+      const bool act = q < RQ1 && r < nr;
+#pragma unroll
+      for (int e = 0; e < PP; ++e) {
+        const float v = warp_sum(aa[q][e]);
+        if (act && lane == 0) abuf[(wp * Rm + r) * 36 + e] = v;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * PP; e += kThreads) {
+      const int r = e / PP, pe = e - r * PP;
+      float v = 0.f;
+      for (int w = 0; w < WP1; ++w) v += abuf[(w * Rm + r) * 36 + pe];
+      int j = 0, rem = pe;
+      while (rem >= P - j) { rem -= P - j; ++j; }
+      const int k = j + rem;
+      float* dst = cd.paa + ((size_t)pg * cd.M + m0 + r) * P * P;
+      dst[j * P + k] = v;
+      dst[k * P + j] = v;
+    }
+  } else {
+    for (int c = tid; c < nc; c += kThreads) {
+      const int r = c / P, j = c - r * P;
+      cd.pmax[(size_t)pg * Mp + c0 + c] = colM[r * P4 + j];
+    }
+  }
+  __syncthreads();
+}
+
+// Fit pass: per (pixel, run) the residual r = x_i - E a_i over the L bands;
+// accumulates sum |r| (entrywise l1), the largest per-pixel sum |r| (induced
+// l1, max column sum) and sum r^2, FP32 within a pixel, FP64 across pixels.
+template <int P>
+__device__ __noinline__ void fit_item(const CubeDev& cd, int rg, int pg, float* smem) {
+  using TR = PassTraits<P>;
+  constexpr int P4 = TR::P4;
+  constexpr int RQ1M = TR::RQ1M;
+  constexpr int SPTM = TR::SPTM;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int L = cd.L, Ls = cd.Ls, Lr = cd.Lr, N = cd.N, Mp = cd.Mp, Rm = cd.Rm;
+  const int m0 = rg * Rm, nr = min(Rm, cd.M - m0), c0 = m0 * P, nc = nr * P;
+  const int Nt = cd.Nt, WP1 = cd.WP1, WR1 = kWarps / WP1, SPT = cd.SPT;
+  const int RQ1 = (Rm + WR1 - 1) / WR1;
+  const PassSmem sm = pass_smem(L, Ls, Lr, P, Rm, Nt);
+  float* Ps = smem + sm.off_ps;
+  float* Xs = smem + sm.off_xs;
+  float* Ss = smem + sm.off_ss;
+  const int RgS4 = sm.RgS4, RgSo = sm.RgSo;
+  for (int e = tid; e < Lr * RgS4; e += kThreads) {
+    const int l = e / RgS4, cc = e - l * RgS4, r = cc / P4, j = cc - r * P4;
+    float v = 0.f;
+    if (l < L && r < nr && j < P) v = cd.Ef[(size_t)l * Mp + c0 + r * P + j];
+    Ps[e] = v;
+  }
+  __syncthreads();
+  const int wp = warp % WP1, wr = warp / WP1;
+  double s1[RQ1M], s2[RQ1M], smx[RQ1M];
+#pragma unroll
+  for (int q = 0; q < RQ1M; ++q) { s1[q] = 0.0; s2[q] = 0.0; smx[q] = 0.0; }
+  const float4* Xs4 = reinterpret_cast<const float4*>(Xs);
+  for (int tile = pg; tile < cd.ntiles; tile += cd.Pg) {
+    const int i0 = tile * Nt, ni = min(Nt, N - i0);
+    {
+      const float4* Xg = reinterpret_cast<const float4*>(cd.X + (size_t)i0 * Ls);
+      float4* xs4 = reinterpret_cast<float4*>(Xs);
+      const int n4 = ni * (Ls >> 2), nt4 = Nt * (Ls >> 2);
+      for (int e = tid; e < nt4; e += kThreads) xs4[e] = (e < n4) ? __ldg(Xg + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int e = tid; e < ni * nc; e += kThreads) {
+      const int i = e / nc, cc = e - i * nc;
+      Ss[i * RgSo + cc] = cd.logA[(size_t)(i0 + i) * Mp + c0 + cc];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < SPTM; ++s) {
+      if (s >= SPT) continue;
+      const int il = lane + 32 * (wp + WP1 * s);
+      const bool valid = il < ni;
+#pragma unroll
+      for (int q = 0; q < RQ1M; ++q) {
+        const int r = wr + WR1 * q;
+        if (!(q < RQ1 && r < nr)) continue;
+        float a[P], se = 0.f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          a[j] = valid ? expf(Ss[il * RgSo + r * P + j]) : 0.f;
+          se += a[j];
+        }
+        const float inv = valid ? 1.f / se : 0.f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) a[j] *= inv;
+        float t1 = 0.f, t2 = 0.f;
+        for (int l = 0; l < Lr; l += 4) {
+          const float4 xv = Xs4[(il * Ls + l) >> 2];
+#pragma unroll
+          for (int d = 0; d < 4; ++d) {
+            if (l + d < L) {
+              float pv[P4];
+              load_p4<P>(Ps + (l + d) * RgS4 + r * P4, pv);
+              float rr = f4c(xv, d);
+#pragma unroll
+              for (int j = 0; j < P; ++j) rr = fmaf(-pv[j], a[j], rr);
+              t1 += fabsf(rr);
+              t2 = fmaf(rr, rr, t2);
+            }
+          }
+        }
+        if (valid) {
+          s1[q] += (double)t1;
+          s2[q] += (double)t2;
+          smx[q] = fmax(smx[q], (double)t1);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // reduce over lanes, then over the WP1 warps sharing a run set
+  double* dbuf = reinterpret_cast<double*>(Xs);  // kWarps x Rm x 3
+#pragma unroll
+  for (int q = 0; q < RQ1M; ++q) {
+    const int r = wr + WR1 * q;
+    const double a1 = warp_sum_d(s1[q]);
+    const double a2 = warp_sum_d(s2[q]);
+    const double am = warp_max_d(smx[q]);
+    if (q < RQ1 && r < nr && lane == 0) {
+      dbuf[(wp * Rm + r) * 3 + 0] = a1;
+      dbuf[(wp * Rm + r) * 3 + 1] = am;
+      dbuf[(wp * Rm + r) * 3 + 2] = a2;
+    }
+  }
+  __syncthreads();
+  for (int r = tid; r < nr; r += kThreads) {
+    double a1 = 0.0, a2 = 0.0, am = 0.0;
+    for (int w = 0; w < WP1; ++w) {
+      a1 += dbuf[(w * Rm + r) * 3 + 0];
+      am = fmax(am, dbuf[(w * Rm + r) * 3 + 1]);
+      a2 += dbuf[(w * Rm + r) * 3 + 2];
+    }
+    double* dst = cd.pfit + ((size_t)pg * cd.M + m0 + r) * 3;
+    dst[0] = a1;
+    dst[1] = am;
+    dst[2] = a2;
+  }
+  __syncthreads();
+}
+
+template <int P>
+__device__ __forceinline__ void pass_dispatch_impl(const Batch* bt, const CubeDev& cd, int rg, int pg, float* smem,
+                                                 int ph) {
+  const int K1 = bt->K1;
+  if (ph == PH_FIT) {
+    fit_item<P>(cd, rg, pg, smem);
+    return;
+  }
+  const bool is_a = (ph == PH_A || ph == PH_INITA);
+  const bool init = (ph == PH_INITA || ph == PH_INITB);
+  const int k1 = (ph == PH_INITA) ? 0 : K1;
+  if (cd.LT <= 5) {
+    if (is_a) pass_item<P, 5, true>(bt, cd, rg, pg, smem, k1, init);
+    else pass_item<P, 5, false>(bt, cd, rg, pg, smem, k1, init);
+  } else if (cd.LT <= 7) {
+    if (is_a) pass_item<P, 7, true>(bt, cd, rg, pg, smem, k1, init);
+    else pass_item<P, 7, false>(bt, cd, rg, pg, smem, k1, init);
+  } else {
+    if (is_a) pass_item<P, 10, true>(bt, cd, rg, pg, smem, k1, init);
+    else pass_item<P, 10, false>(bt, cd, rg, pg, smem, k1, init);
+  }
+}
+
+
+// Defined (explicitly instantiated) in edaa_pass_p.cu, one object per p.
+template <int P>
+__device__ void pass_dispatch(const Batch* bt, const CubeDev& cd, int rg, int pg, float* smem, int ph);
+
+}  // namespace edaa

@@ -1,0 +1,85 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every entry point
+include/edaa.h declares, its host-side selection rule matches Algorithm 2 as
+the oracle states it, and without a GPU its compute calls fail loudly."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import edaa_oracle as O
+from paper_2209_11002_gb300 import build, edaa
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build_library()
+    return edaa.load_library()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "edaa.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(edaa_[a-z_]+)\s*\(", text)))
+
+
+def test_header_matches_binding_exports():
+    assert _declared() == sorted(edaa.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_config_defaults_are_the_papers(lib):
+    cfg = edaa.default_config()
+    assert (cfg.T, cfg.K1, cfg.K2) == (100, 5, 5)
+    assert cfg.fit_ratio == 1.05 and cfg.normalize == 1
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_select_rule_matches_oracle(lib, seed):
+    rng = np.random.default_rng(seed)
+    M = 12
+    fit = rng.uniform(10, 12, M)
+    mu = rng.uniform(0, 1, M)
+    if seed % 2:
+        fit[3] = np.nan
+        fit[5] = fit.min() * 1.05  # boundary is inclusive
+        mu[5] = -1.0
+    if seed == 4:
+        mu[:] = 0.5  # ties go to the lowest index
+    assert edaa.select_rule(fit, mu) == O.select(fit, mu)
+
+
+def test_select_rule_edge_cases(lib):
+    assert edaa.select_rule([np.nan, np.inf], [0.0, 0.0]) == -1
+    assert edaa.select_rule([1.0], [float("-inf")]) == 0
+
+
+def test_compute_calls_fail_without_gpu(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    X = np.ones((40, 5), np.float32)
+    with pytest.raises(edaa.EDAAError) as ei:
+        edaa.Context([dict(X=X, p=2, seeds=[1], gammas=[1.0])], T=1)
+    assert ei.value.status == edaa.EDAA_ERR_CUDA
+
+
+def test_argument_validation(lib):
+    X = np.ones((5, 40), np.float32)  # N=5 pixels, L=40 bands
+    bad = [dict(X=X, p=0, seeds=[1], gammas=[1.0]),          # p < 1
+           dict(X=X, p=6, seeds=[1], gammas=[1.0]),          # N < p
+           dict(X=X, p=2, seeds=[1], gammas=[-1.0]),         # gamma <= 0
+           dict(X=np.ones((40, 400), np.float32), p=2, seeds=[1], gammas=[1.0])]  # L > 319
+    codes = []
+    for c in bad:
+        with pytest.raises(edaa.EDAAError) as ei:
+            edaa.Context([c], T=1)
+        codes.append(ei.value.status)
+    assert codes[:3] == [edaa.EDAA_ERR_ARG] * 3
+    assert codes[3] == edaa.EDAA_ERR_UNSUPPORTED
