@@ -165,6 +165,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--outer", type=int, default=100, help="outer iterations T (100: the paper's)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -190,7 +192,7 @@ def main():
     # distinct ensembles per rank: same cube, run seeds drawn from a rank-specific stream
     seeds, gammas = synth.run_params(rank_seed(spec["seed"], rank), cube.M, spec["gamma_choices"])
     L, N, p, M = cube.L, cube.N, cube.p, cube.M
-    T, K1, K2 = 100, 5, 5
+    T, K1, K2 = args.outer, 5, 5
     stream = torch.cuda.Stream()
     Xd = torch.from_numpy(cube.pixel_major()).cuda()
     ctx = edaa.Context([dict(X=Xd, p=p, seeds=seeds, gammas=gammas)], stream=stream, T=T, K1=K1, K2=K2,
@@ -251,36 +253,37 @@ def main():
                 "effective_gbs": T * algorithmic_bytes_per_outer(L, N, p, M, K2) / kern_avg_s / 1e9}
 
     # end to end through the C ABI with host buffers
-    Xh = torch.from_numpy(cube.pixel_major()).pin_memory()
-    Eh = np.zeros((L, p), np.float32)
-    Ah = np.zeros((p, N), np.float32)
-    Bh = np.zeros((N, p), np.float32)
-    lib = edaa.load_library()
-    import ctypes
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(cube.pixel_major()).pin_memory()
+        Eh = np.zeros((L, p), np.float32)
+        Ah = np.zeros((p, N), np.float32)
+        Bh = np.zeros((N, p), np.float32)
+        lib = edaa.load_library()
 
-    def e2e_step():
-        ctx.reset(0, Xh)
-        ctx.step(T)
-        ctx.solve()
-        b, f, m = ctx.select(0)
-        edaa._check(lib.edaa_get(ctx.h, 0, b, edaa._ptr(Eh), edaa._ptr(Ah), edaa._ptr(Bh)), "edaa_get")
-        return b
+        def e2e_step():
+            ctx.reset(0, Xh)
+            ctx.step(T)
+            ctx.solve()
+            b, f, m = ctx.select(0)
+            edaa._check(lib.edaa_get(ctx.h, 0, b, edaa._ptr(Eh), edaa._ptr(Ah), edaa._ptr(Bh)), "edaa_get")
+            return b
 
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    n_e2e = max(3, args.steps // 2)
-    for _ in range(n_e2e):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * run_steps * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * L * 4,
-           "d2h_bytes_per_step": (L * p + 2 * N * p) * 4 + 2 * M * 8 + 4}
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_e2e = max(3, args.steps // 2)
+        for _ in range(n_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * run_steps * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * L * 4,
+               "d2h_bytes_per_step": (L * p + 2 * N * p) * 4 + 2 * M * 8 + 4}
 
     launches_solve = ctx.describe(0)["launches_per_solve"]
     launches = (1 if args.persistent else 5) + (1 if args.persistent else T * (2 + 2 * K2)) + launches_solve
