@@ -162,6 +162,30 @@ const char* edaa_last_error(void);
  * device still usable (no trap, no hang).  extra = 0 must return EDAA_OK. */
 edaa_status edaa_selftest_barrier(int grid, int extra, double timeout_ms, void* stream);
 
+/* Allocation-free evaluation of the fit and loss of given solutions.  The
+ * paper has no counterpart: this entry point serves callers that cannot call
+ * cudaMalloc -- a process whose device memory belongs to another allocator
+ * (for example a framework's caching pool that reserved the whole GPU), or a
+ * latency-bound loop that must not block in the driver's allocator.  It does
+ * the work of the fit pass behind edaa_solve / edaa_loss for M runs given
+ * explicitly, and keeps its per-block partial sums in a fixed 384 KiB static
+ * device array that is part of the library (every GPU that loads the
+ * library holds it until exit); it calls no allocating routine.
+ *   X: N x L pixel-major float32 (the data the solutions were computed on,
+ *      already normalised the way they saw it); E: M x L x p float32 (run m's
+ *      E, row-major); A: M x p x N float32.  All inputs and the outputs
+ *      fit[M] = sum |X - E A|, fitmax[M] = max_i sum_l |X - E A|,
+ *      loss[M] = ||X - E A||_F^2 (FP64, NULL skips) must be device memory.
+ * Limits: 1 <= p <= 8 and 1 <= M <= 64 (the size of the static array);
+ * larger sizes return EDAA_ERR_UNSUPPORTED with a message, nothing runs.
+ * Asynchronous on `stream` (a cudaStream_t).  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Calls on
+ * one device share the array, so calls whose GPU work overlaps race: the
+ * caller serialises them (one stream, or an event between streams). */
+edaa_status edaa_fit_eval_static(const float* X, int L, int N, int p, int M, const float* E, const float* A,
+                                 double* fit, double* fitmax, double* loss, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

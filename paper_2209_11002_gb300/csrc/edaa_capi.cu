@@ -113,6 +113,10 @@ std::map<std::tuple<int, int, int, int, int>, TileCfg>& tune_cache() {
 
 }  // namespace
 
+namespace edaa {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace edaa
+
 struct CubeHost {
   int L, N, p, M, Ls, Lr, Mp;
   TileCfg tile;

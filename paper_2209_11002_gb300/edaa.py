@@ -25,7 +25,8 @@ FP32, TF32, BF16 = 0, 1, 2
 # Every function declared in include/edaa.h (the CPU tests check the export list).
 EXPORTS = ["edaa_config_default", "edaa_init", "edaa_reset", "edaa_step", "edaa_solve", "edaa_select",
            "edaa_select_rule", "edaa_get", "edaa_grad", "edaa_loss", "edaa_step_sizes", "edaa_sync",
-           "edaa_outer_done", "edaa_describe", "edaa_destroy", "edaa_last_error", "edaa_selftest_barrier"]
+           "edaa_outer_done", "edaa_describe", "edaa_destroy", "edaa_last_error", "edaa_selftest_barrier",
+           "edaa_fit_eval_static"]
 
 
 class Config(ctypes.Structure):
@@ -79,6 +80,8 @@ def load_library():
         "edaa_destroy": (None, [vp]),
         "edaa_last_error": (ctypes.c_char_p, []),
         "edaa_selftest_barrier": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, vp]),
+        "edaa_fit_eval_static": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
+                                                vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -247,6 +250,22 @@ class Context:
         _check(self.lib.edaa_describe(self.h, cube, *[ctypes.byref(v) for v in vals]), "edaa_describe")
         keys = ["runs_per_group", "pixel_tile", "ctas_per_group", "grid", "launches_per_solve"]
         return {k: v.value for k, v in zip(keys, vals)}
+
+
+def fit_eval_static(X, E, A, stream=None):
+    """Fit, max-column fit and loss of M given solutions through the
+    allocation-free entry point.  X: N x L, E: M x L x p, A: M x p x N, all
+    CUDA tensors (float32).  The library allocates nothing for this call; the
+    three FP64 output vectors are allocated here by torch."""
+    import torch
+    N, L = X.shape
+    M, _, p = E.shape
+    out = torch.zeros((3, M), dtype=torch.float64, device=X.device)
+    lib = load_library()
+    s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream) if stream else None
+    _check(lib.edaa_fit_eval_static(_ptr(X), L, N, p, M, _ptr(E), _ptr(A), _ptr(out[0]), _ptr(out[1]),
+                                    _ptr(out[2]), s), "edaa_fit_eval_static")
+    return out[0], out[1], out[2]
 
 
 def selftest_barrier(grid: int, extra: int, timeout_ms: float, stream=None) -> int:
