@@ -162,6 +162,37 @@ const char* edaa_last_error(void);
  * device still usable (no trap, no hang).  extra = 0 must return EDAA_OK. */
 edaa_status edaa_selftest_barrier(int grid, int extra, double timeout_ms, void* stream);
 
+/* ---- Differentiable unrolled solve (one run) ------------------------------
+ * Algorithm 1 unrolled for T outer iterations with one step size per block:
+ * eta_A[t] for the K1 A-steps (eq. update_A) and eta_B[t] for the K2 B-steps
+ * (eq. update_B) of outer iteration t; A^0 = 1/p (eq. initA0), B^0 =
+ * softmax(0.1 u) with u from SplitMix64(seed) exactly as in edaa_init (eq.
+ * initB0).  X is used as given (no normalisation inside).  The forward keeps
+ * one checkpoint (log A, log B) per outer iteration; the backward recomputes
+ * each outer iteration from its checkpoint and runs hand-written adjoint
+ * kernels, returning d loss / d X and d loss / d eta from d loss / d E_hat
+ * and d loss / d A_hat, where E_hat = X B_hat and A_hat are the outputs.
+ * Limits: 1 <= p <= 8, p <= N, L <= 320, K1 <= 5.  All device buffers are
+ * allocated by edaa_unrolled_create; `stream` is a cudaStream_t. */
+typedef struct edaa_unrolled edaa_unrolled;
+
+edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T, int K1, int K2, void* stream);
+
+/* X: N x L pixel-major float32 (host or device); eta_A, eta_B: host arrays of
+ * length T; outputs E_out (L x p) and A_out (p x N), row-major, host or
+ * device, NULL skips.  Synchronous with respect to the host only for host
+ * outputs. */
+edaa_status edaa_unrolled_forward(edaa_unrolled* u, const float* X, uint64_t seed, const double* eta_A,
+                                  const double* eta_B, float* E_out, float* A_out);
+
+/* dE: L x p, dA: p x N (host or device, NULL = zero); outputs dX (N x L,
+ * host or device, NULL skips) and d_eta_A, d_eta_B (host, length T, NULL
+ * skips).  Needs a preceding forward; synchronises. */
+edaa_status edaa_unrolled_backward(edaa_unrolled* u, const float* dE, const float* dA, float* dX, double* d_eta_A,
+                                   double* d_eta_B);
+
+void edaa_unrolled_destroy(edaa_unrolled* u);
+
 /* Allocation-free evaluation of the fit and loss of given solutions.  The
  * paper has no counterpart: this entry point serves callers that cannot call
  * cudaMalloc -- a process whose device memory belongs to another allocator

@@ -21,7 +21,7 @@ LIB = os.path.join(OUT_DIR, "libedaa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, extra flags, object name); the pass bodies compile once per p
 SOURCES = [("edaa_kernels.cu", [], "edaa_kernels"), ("edaa_capi.cu", [], "edaa_capi"),
-           ("edaa_static.cu", [], "edaa_static")] + [
+           ("edaa_static.cu", [], "edaa_static"), ("edaa_unrolled.cu", [], "edaa_unrolled")] + [
     ("edaa_pass_p.cu", [f"-DEDAA_P={p}"], f"edaa_pass_p{p}") for p in range(1, 9)]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-rdc=true", "-Xcompiler", "-fPIC"]
 

@@ -26,7 +26,8 @@ FP32, TF32, BF16 = 0, 1, 2
 EXPORTS = ["edaa_config_default", "edaa_init", "edaa_reset", "edaa_step", "edaa_solve", "edaa_select",
            "edaa_select_rule", "edaa_get", "edaa_grad", "edaa_loss", "edaa_step_sizes", "edaa_sync",
            "edaa_outer_done", "edaa_describe", "edaa_destroy", "edaa_last_error", "edaa_selftest_barrier",
-           "edaa_fit_eval_static"]
+           "edaa_fit_eval_static", "edaa_unrolled_create", "edaa_unrolled_forward", "edaa_unrolled_backward",
+           "edaa_unrolled_destroy"]
 
 
 class Config(ctypes.Structure):
@@ -82,6 +83,10 @@ def load_library():
         "edaa_selftest_barrier": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, vp]),
         "edaa_fit_eval_static": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
                                                 vp, vp, vp, vp]),
+        "edaa_unrolled_create": (ctypes.c_int, [ctypes.POINTER(vp)] + [ctypes.c_int] * 6 + [vp]),
+        "edaa_unrolled_forward": (ctypes.c_int, [vp, vp, ctypes.c_uint64, dp, dp, vp, vp]),
+        "edaa_unrolled_backward": (ctypes.c_int, [vp, vp, vp, vp, dp, dp]),
+        "edaa_unrolled_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
