@@ -31,6 +31,71 @@ sys.path.insert(0, ROOT)
 METRIC = "ensemble EDAA steps/sec vs plain FP32 at matched loss; HBM GB/s vs peak"
 UNIT = "run-steps/s"
 WORKLOAD = "jasper-shape synthetic cube L=198 N=10000 p=4, M=50 runs, T=100, K1=K2=5, FP32"
+WORKLOADS = {
+    "jasper": WORKLOAD,
+    "samson": "samson-shape synthetic cube L=156 N=9025 p=3, M=1 run (plain single EDAA run), T=100, K1=K2=5, FP32",
+    "urban": "urban-shape synthetic cube L=162 N=94249 p=6, M=64 runs, T=100, K1=K2=5, FP32",
+    "uneven": "8 synthetic cubes of uneven L, N, p (seed 1004), M=16 runs each, one launch, T=100, K1=K2=5, FP32",
+    "apex-unrolled": "apex-shape synthetic cube L=285 N=13542 p=4, unrolled T=20, K1=K2=5, forward+backward, FP32",
+}
+
+
+def make_workload_cubes(name: str, rank: int):
+    from paper_2209_11002_gb300 import synth
+    if name == "uneven":
+        return synth.uneven_batch()
+    spec = {"jasper": synth.JASPER_ENSEMBLE, "samson": synth.SAMSON_EDAA, "urban": synth.URBAN_PRECISION}[name]
+    cube = synth.workload(spec)
+    # distinct ensembles per rank: same cube, run seeds drawn from a rank-specific stream
+    cube.seeds, cube.gammas = synth.run_params(rank_seed(spec["seed"], rank), cube.M, spec["gamma_choices"])
+    return [cube]
+
+
+def unrolled_workload(args, rank, world):
+    """Forward + backward of the differentiable unrolled solve (one run)."""
+    import numpy as np
+    import torch
+
+    from paper_2209_11002_gb300 import synth
+    from paper_2209_11002_gb300.autograd import EDAAUnrolled
+    cube = synth.workload(synth.APEX_UNROLLED)
+    T, K1, K2 = 20, 5, 5
+    X64 = cube.pixel_major().astype(np.float64)
+    Xg = torch.from_numpy((X64 / np.linalg.norm(X64, axis=1, keepdims=True)).astype(np.float32)).cuda()
+    Xg.requires_grad_(True)
+    eta = torch.full((T,), 0.1, dtype=torch.float64, requires_grad=True)
+    etb = torch.full((T,), 0.1 * (cube.p / cube.N) ** 0.5, dtype=torch.float64, requires_grad=True)
+    WE = torch.randn(cube.L, cube.p, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+
+    def step():
+        E, A = EDAAUnrolled.apply(Xg, eta, etb, cube.p, 1234, K1, K2)
+        R = Xg.t() - E @ A
+        loss = 0.5 * (R * R).sum() + (WE * E).sum()
+        loss.backward()
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = max_over_ranks(sum(ms), world, "cuda")
+    run_steps = T * (K1 + K2)
+    line = {"metric": "unrolled EDAA forward+backward run-steps/s", "value": whole_job_rate(run_steps * args.steps,
+                                                                                            world, t / 1e3),
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": {"workload": WORKLOADS["apex-unrolled"]}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
 
 
 def _peaks():
@@ -116,6 +181,23 @@ def rank_seed(base_seed: int, rank: int) -> int:
     return base_seed + 7919 * rank
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value over all ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Weak scaling: every rank processes the same units; the rate is all ranks'
+    units over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def run_oracle_sample(cube, n_runs: int, T: int, K1: int = 5, K2: int = 5):
     """Times the FP64 oracle on `n_runs` runs of `T` outer iterations."""
     from oracle import edaa_oracle as O
@@ -167,6 +249,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--outer", type=int, default=100, help="outer iterations T (100: the paper's)")
+    ap.add_argument("--workload", default="jasper", choices=sorted(WORKLOADS))
+    ap.add_argument("--autotune", type=int, default=1)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -186,18 +270,17 @@ def main():
     build.build_library()
     edaa.load_library()
 
-    spec = dict(synth.JASPER_ENSEMBLE)
-    spec["seed"] = rank_seed(spec["seed"], 0)
-    cube = synth.workload(spec)
-    # distinct ensembles per rank: same cube, run seeds drawn from a rank-specific stream
-    seeds, gammas = synth.run_params(rank_seed(spec["seed"], rank), cube.M, spec["gamma_choices"])
-    L, N, p, M = cube.L, cube.N, cube.p, cube.M
     T, K1, K2 = args.outer, 5, 5
+    if args.workload == "apex-unrolled":
+        return unrolled_workload(args, rank, world)
+    cubes = make_workload_cubes(args.workload, rank)
     stream = torch.cuda.Stream()
-    Xd = torch.from_numpy(cube.pixel_major()).cuda()
-    ctx = edaa.Context([dict(X=Xd, p=p, seeds=seeds, gammas=gammas)], stream=stream, T=T, K1=K1, K2=K2,
-                       persistent=args.persistent)
+    Xds = [torch.from_numpy(c.pixel_major()).cuda() for c in cubes]
+    ctx = edaa.Context([dict(X=Xd, p=c.p, seeds=c.seeds, gammas=c.gammas) for Xd, c in zip(Xds, cubes)],
+                       stream=stream, T=T, K1=K1, K2=K2, persistent=args.persistent, autotune=args.autotune)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    cube = cubes[0]
+    L, N, p, M = cube.L, cube.N, cube.p, cube.M
 
     def one_step(ev=None):
         ctx.reset()
@@ -207,7 +290,7 @@ def main():
         if ev is not None:
             ev[1].record(stream)
         ctx.solve()
-        return ctx.select(0)
+        return [ctx.select(ci) for ci in range(len(cubes))][0]
 
     for _ in range(args.warmup):
         one_step()
@@ -230,18 +313,14 @@ def main():
         kern_ms.append(kev[0].elapsed_time(kev[1]))
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    run_steps = M * T * (K1 + K2)
-    value = world * run_steps * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), world, "cuda")
+    run_steps = sum(c.M for c in cubes) * T * (K1 + K2)
+    value = whole_job_rate(run_steps * args.steps, world, total_ms / 1e3)
 
     # roofline of the dominant kernel: the persistent solve launch (T outer iterations)
     peaks, peak_kind = _peaks()
     props = torch.cuda.get_device_properties(local)
-    flops_launch = T * algorithmic_flops_per_outer(L, N, p, M, K1, K2)
+    flops_launch = T * sum(algorithmic_flops_per_outer(c.L, c.N, c.p, c.M, K1, K2) for c in cubes)
     kern_avg_s = statistics.mean(kern_ms) / 1e3
     achieved = flops_launch / kern_avg_s / 1e12
     peak = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
@@ -250,24 +329,26 @@ def main():
                 "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 x "
                                f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max clock)",
                 "kernel_ms": statistics.mean(kern_ms),
-                "effective_gbs": T * algorithmic_bytes_per_outer(L, N, p, M, K2) / kern_avg_s / 1e9}
+                "effective_gbs": T * sum(algorithmic_bytes_per_outer(c.L, c.N, c.p, c.M, K2) for c in cubes)
+                / kern_avg_s / 1e9}
 
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        Xh = torch.from_numpy(cube.pixel_major()).pin_memory()
-        Eh = np.zeros((L, p), np.float32)
-        Ah = np.zeros((p, N), np.float32)
-        Bh = np.zeros((N, p), np.float32)
+        Xhs = [torch.from_numpy(c.pixel_major()).pin_memory() for c in cubes]
+        outs = [(np.zeros((c.L, c.p), np.float32), np.zeros((c.p, c.N), np.float32), np.zeros((c.N, c.p), np.float32))
+                for c in cubes]
         lib = edaa.load_library()
 
         def e2e_step():
-            ctx.reset(0, Xh)
+            for ci, Xh in enumerate(Xhs):
+                ctx.reset(ci, Xh)
             ctx.step(T)
             ctx.solve()
-            b, f, m = ctx.select(0)
-            edaa._check(lib.edaa_get(ctx.h, 0, b, edaa._ptr(Eh), edaa._ptr(Ah), edaa._ptr(Bh)), "edaa_get")
-            return b
+            for ci in range(len(cubes)):
+                b, f, m = ctx.select(ci)
+                Eh, Ah, Bh = outs[ci]
+                edaa._check(lib.edaa_get(ctx.h, ci, b, edaa._ptr(Eh), edaa._ptr(Ah), edaa._ptr(Bh)), "edaa_get")
 
         for _ in range(2):
             e2e_step()
@@ -277,26 +358,25 @@ def main():
         for _ in range(n_e2e):
             e2e_step()
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * run_steps * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * L * 4,
-               "d2h_bytes_per_step": (L * p + 2 * N * p) * 4 + 2 * M * 8 + 4}
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+        e2e = {"value": whole_job_rate(run_steps * n_e2e, world, e2e_s), "unit": UNIT,
+               "h2d_bytes_per_step": sum(c.N * c.L * 4 for c in cubes),
+               "d2h_bytes_per_step": sum((c.L * c.p + 2 * c.N * c.p) * 4 + 2 * c.M * 8 + 4 for c in cubes)}
 
     launches_solve = ctx.describe(0)["launches_per_solve"]
     launches = (1 if args.persistent else 5) + (1 if args.persistent else T * (2 + 2 * K2)) + launches_solve
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch_runs": M * world, "L": L, "N": N, "p": p, "M": M,
+            "config": {"workload": WORKLOADS[args.workload] if args.outer == 100 else
+                       WORKLOADS[args.workload] + f" (T={T})", "global_batch_runs": sum(c.M for c in cubes) * world,
+                       "cubes": [dict(L=c.L, N=c.N, p=c.p, M=c.M) for c in cubes],
                        "T": T, "K1": K1, "K2": K2, "l2": "flushed between timed steps (512 MB write)",
-                       "persistent": args.persistent, "launch": ctx.describe(0)},
+                       "persistent": args.persistent, "autotune": args.autotune, "launch": ctx.describe(0)},
             "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches * args.steps,
             "selected_run": int(best)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_runs, To = 2, 50
+        n_runs, To = min(2, cube.M), (50 if cube.N * cube.L < 4e6 else 3)
         rate, dt = run_oracle_sample(cube, n_runs, To)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                                 "sample": f"{n_runs} runs x {To} outer iterations ({n_runs * To * 10} run-steps, "

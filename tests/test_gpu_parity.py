@@ -248,3 +248,22 @@ def test_jasper_shape_ensemble_sampled_runs():
             assert np.abs(A - ref["A"]).max() <= 1e-3
             assert abs(fit[m] - O.fit_l1(Xn, ref["E"], ref["A"])) / fit[m] <= 1e-3
     assert 0 <= best < 50 and np.all(np.isfinite(fit))
+
+
+def test_autotuned_launch_shape_keeps_results():
+    """The autotuner times candidate tile shapes at init and keeps the fastest;
+    whatever it picks, the result must still match the oracle."""
+    cube = synth.make_cube(44, 3000, 4, alpha=0.3, snr_db=25, M=10, gamma_choices=(0.5, 1.0, 2.0), seed=21)
+    T = 5
+    with _ctx([cube], T=T, autotune=1) as ctx:
+        shape = ctx.describe(0)
+        ctx.solve()
+        loss = ctx.loss(0)
+        Xn = O.normalize_pixels(cube.X)
+        for m in (0, 9):
+            ref = _oracle(cube, m, T)
+            E, A, B = ctx.get(0, m, device="cpu")
+            assert np.abs(A - ref["A"]).max() <= 1e-3
+            lr = O.objective(Xn, ref["A"], ref["B"])
+            assert abs(loss[m] - lr) / lr <= 1e-3
+    assert shape["runs_per_group"] >= 1 and shape["pixel_tile"] in (32, 64, 128)
