@@ -251,6 +251,7 @@ def main():
     ap.add_argument("--outer", type=int, default=100, help="outer iterations T (100: the paper's)")
     ap.add_argument("--workload", default="jasper", choices=sorted(WORKLOADS))
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -276,8 +277,10 @@ def main():
     cubes = make_workload_cubes(args.workload, rank)
     stream = torch.cuda.Stream()
     Xds = [torch.from_numpy(c.pixel_major()).cuda() for c in cubes]
+    prec = {"fp32": edaa.FP32, "tf32": edaa.TF32, "bf16": edaa.BF16}[args.precision]
     ctx = edaa.Context([dict(X=Xd, p=c.p, seeds=c.seeds, gammas=c.gammas) for Xd, c in zip(Xds, cubes)],
-                       stream=stream, T=T, K1=K1, K2=K2, persistent=args.persistent, autotune=args.autotune)
+                       stream=stream, T=T, K1=K1, K2=K2, persistent=args.persistent, autotune=args.autotune,
+                       precision=prec)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     cube = cubes[0]
     L, N, p, M = cube.L, cube.N, cube.p, cube.M
@@ -323,14 +326,38 @@ def main():
     flops_launch = T * sum(algorithmic_flops_per_outer(c.L, c.N, c.p, c.M, K1, K2) for c in cubes)
     kern_avg_s = statistics.mean(kern_ms) / 1e3
     achieved = flops_launch / kern_avg_s / 1e12
-    peak = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_edaa (persistent solve, T outer iterations)",
-                "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 x "
-                               f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max clock)",
+    tensor = args.precision != "fp32" and all(c.M * c.p >= 64 for c in cubes)
+    if tensor:
+        # the solve is one long launch: sustained bf16 peak; TF32 at the nominal TF32/BF16 ratio 1.1/2.25
+        bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+        peak = bf16 if args.precision == "bf16" else bf16 * 1.1 / 2.25
+        peak_source = (f"{peak_kind} sustained dense bf16 {bf16} TFLOP/s" +
+                       ("" if args.precision == "bf16" else " x nominal TF32/BF16 ratio 1.1/2.25"))
+    else:
+        peak = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
+        peak_source = (f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 x "
+                       f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max clock)")
+    roofline = {"bound": "tensor" if tensor else "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "kernel": "k_edaa (persistent solve, T outer iterations)", "peak_source": peak_source,
                 "kernel_ms": statistics.mean(kern_ms),
-                "effective_gbs": T * sum(algorithmic_bytes_per_outer(c.L, c.N, c.p, c.M, K2) for c in cubes)
-                / kern_avg_s / 1e9}
+                "effective_gbs": T * sum(algorithmic_bytes_per_outer(c.L, c.N, c.p, c.M, K2,
+                                                                      2 if args.precision == "bf16" else 4)
+                                         for c in cubes) / kern_avg_s / 1e9}
+    # matched loss: the same runs in plain FP32 (CUDA cores), untimed
+    matched = None
+    if args.precision != "fp32":
+        ref = edaa.Context([dict(X=Xd, p=c.p, seeds=c.seeds, gammas=c.gammas) for Xd, c in zip(Xds, cubes)],
+                           stream=stream, T=T, K1=K1, K2=K2, persistent=args.persistent, precision=edaa.FP32)
+        ref.solve()
+        ctx.reset()
+        ctx.solve()
+        worst = 0.0
+        for ci in range(len(cubes)):
+            lr, lt = ref.loss(ci), ctx.loss(ci)
+            worst = max(worst, float(np.max(np.abs(lt - lr) / lr)))
+        ref.close()
+        matched = {"max_rel_loss_diff_vs_fp32": worst, "within_1pct": worst <= 0.01}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -367,13 +394,16 @@ def main():
     launches = (1 if args.persistent else 5) + (1 if args.persistent else T * (2 + 2 * K2)) + launches_solve
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "tf32": "tf32 (fp32 accumulate)", "bf16": "bf16 (fp32 accumulate)"}[args.precision],
+            "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload] if args.outer == 100 else
                        WORKLOADS[args.workload] + f" (T={T})", "global_batch_runs": sum(c.M for c in cubes) * world,
                        "cubes": [dict(L=c.L, N=c.N, p=c.p, M=c.M) for c in cubes],
                        "T": T, "K1": K1, "K2": K2, "l2": "flushed between timed steps (512 MB write)",
                        "persistent": args.persistent, "autotune": args.autotune, "launch": ctx.describe(0)},
             "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches * args.steps,
+            "matched_loss": matched,
             "selected_run": int(best)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_runs, To = min(2, cube.M), (50 if cube.N * cube.L < 4e6 else 3)

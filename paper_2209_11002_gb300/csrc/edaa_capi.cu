@@ -10,8 +10,11 @@
 #include <tuple>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/edaa.h"
 #include "edaa_internal.cuh"
+#include "edaa_tc.cuh"
 
 using namespace edaa;
 
@@ -126,6 +129,11 @@ struct CubeHost {
   float* X_in = nullptr;  // N x L staging copy of the caller's X
   double* bsum = nullptr; // per-block band sums for the mean pixel
   double* scale = nullptr; // per-pixel 1/||x_i|| (FP64)
+  // tensor-core path
+  int tc = 0, esz = 4, kp = 0, Npad = 0;
+  void* Xk = nullptr;      // N x kp compute-type copy of the centred X (pixel-major)
+  void* XT = nullptr;      // (L+1) x Npad band-major copy
+  CUtensorMap* tmaps = nullptr;  // device, 4 maps
   CubeDev dev;
   std::vector<uint64_t> seeds;
   std::vector<double> gammas;
@@ -156,6 +164,19 @@ static edaa_status check_status(edaa_ctx* c) {
   return EDAA_OK;
 }
 
+// Tensor-core cubes: 128-pixel tiles; the largest run group whose padded
+// column count Rgp fits TMEM next to one accumulator per 128-band tile
+// (Rgp * (1 + band tiles) <= 512 columns, Rgp <= 256), balanced over groups.
+static void tc_tile(CubeHost& h) {
+  const int rgp_max = tc_rgp_max(h.L, h.esz);
+  const int rm_max = std::max(1, std::min({128, rgp_max / h.p, 2048 / (h.p * h.p)}));
+  const int RG = (h.M + rm_max - 1) / rm_max;
+  h.tile.Rm = (h.M + RG - 1) / RG;
+  h.tile.WP1 = 4;  // the CUDA-core fit pass runs on the same 128-pixel tiles
+  h.tile.SPT = 1;
+  h.tile.WP2 = 1;
+}
+
 // Assign pass work items (run group x pixel group) and merge work items.
 static void plan(edaa_ctx* c) {
   const int G = c->sm_count * c->blocks_per_sm;
@@ -165,6 +186,7 @@ static void plan(edaa_ctx* c) {
   int units_total = 0;
   for (auto& h : c->cubes) units_total += h.M;
   for (auto& h : c->cubes) {
+    if (h.tc) tc_tile(h);
     h.Nt = 32 * h.tile.WP1 * h.tile.SPT;
     h.ntiles = (h.N + h.Nt - 1) / h.Nt;
     h.RG = (h.M + h.tile.Rm - 1) / h.tile.Rm;
@@ -188,6 +210,11 @@ static void plan(edaa_ctx* c) {
     d.LT = (h.L + 1 + 31) / 32;
     d.Rm = h.tile.Rm; d.RG = h.RG; d.Pg = h.Pg; d.Nt = h.Nt; d.WP1 = h.tile.WP1; d.SPT = h.tile.SPT;
     d.WP2 = h.tile.WP2; d.ntiles = h.ntiles;
+    d.tc = h.tc;
+    d.tc_kp = h.kp;
+    d.tc_nbt = (h.L + 1 + 127) / 128;
+    d.tc_nkc = h.tc ? (h.L + (128 / h.esz) - 1) / (128 / h.esz) : 0;
+    d.tc_rgp = h.tc ? round_up(h.tile.Rm * h.p, 16) : 0;
     d.cta0 = cta; d.lchunk = h.lchunk; d.nlchunk = h.nlchunk; d.unit0 = unit; d.run0 = run0;
     cta += h.RG * h.Pg;
     unit += h.M * h.nlchunk;
@@ -200,8 +227,19 @@ static void plan(edaa_ctx* c) {
   if (c->grid < 1) c->grid = 1;
 }
 
-static size_t cube_smem(const CubeHost& h) {
+// shared memory of the pass and fit work items of a cube (no merge terms)
+static size_t pass_item_smem(const CubeHost& h) {
   size_t s = tile_smem(h.tile, h.L, h.p);
+  if (h.tc) {
+    const int rb = std::min(h.tile.Rm, (8 / h.tile.WP1) * rq1_max(h.p));
+    s = (size_t)pass_smem(h.L, h.Ls, h.Lr, h.p, rb, 128).total * 4;  // fit pass in run blocks
+    s = std::max(s, (size_t)tc_smem(round_up(h.tile.Rm * h.p, 16), h.esz).total);
+  }
+  return s;
+}
+
+static size_t cube_smem(const CubeHost& h) {
+  size_t s = pass_item_smem(h);
   const size_t mb = (size_t)(2 * kMaxP + h.lchunk * h.p + h.Pg * h.p) * 8 + 64;
   const size_t ma = (size_t)(64 + h.lchunk * h.p) * 8;
   return std::max(s, std::max(ma, mb));
@@ -225,6 +263,9 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
   size_t opaa = take((size_t)Pg_cap * M * p * p * 4), opfit = take((size_t)Pg_cap * M * 3 * 8);
   size_t ofit = take(M * 8), ofitmax = take(M * 8), oloss = take(M * 8), omu = take(M * 8);
   size_t oseeds = take(M * 8), ogam = take(M * 8);
+  const size_t tcb = h.tc ? 1 : 0;
+  size_t oXk = take(tcb * N * h.kp * h.esz), oXT = take(tcb * (L + 1) * h.Npad * h.esz);
+  size_t opE = take(tcb * Mp * h.kp * h.esz), opR = take(tcb * Mp * h.kp * h.esz), otm = take(tcb * 4 * 128);
   size_t oscale = take(N * 8), oxbar = take(L * 8), osx = take((L + 1) * 8), obsum = take((size_t)normalize_blocks(h.N) * L * 8);
   if (assign) {
     char* b = (char*)h.arena;
@@ -258,14 +299,63 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
     d.sx = (double*)(b + osx);
     h.bsum = (double*)(b + obsum);
     h.scale = (double*)(b + oscale);
+    if (h.tc) {
+      h.Xk = b + oXk;
+      h.XT = b + oXT;
+      d.panelE = b + opE;
+      d.panelR = b + opR;
+      h.tmaps = (CUtensorMap*)(b + otm);
+      d.tmaps = h.tmaps;
+    }
   }
   return off;
 }
 
 static edaa_status upload_x(edaa_ctx* c, CubeHost& h, const float* X) {
   CK(cudaMemcpyAsync(h.X_in, X, (size_t)h.N * h.L * 4, cudaMemcpyDefault, c->stream), "copy X");
+  if (h.tc) {
+    const edaa_status st = [&]() -> edaa_status {
+      CK(launch_normalize(h.X_in, h.dev.X, h.scale, h.bsum, h.dev.xbar, h.dev.sx, h.L, h.Ls, h.N, c->cfg.normalize,
+                          c->cfg.center, c->stream), "normalize");
+      CK(launch_tc_prepare(h.dev, h.Xk, h.XT, h.Npad, c->stream), "tensor-core copies of X");
+      return EDAA_OK;
+    }();
+    return st;
+  }
   CK(launch_normalize(h.X_in, h.dev.X, h.scale, h.bsum, h.dev.xbar, h.dev.sx, h.L, h.Ls, h.N, c->cfg.normalize,
                       c->cfg.center, c->stream), "normalize");
+  return EDAA_OK;
+}
+
+// TMA descriptors (128-byte swizzle, K-major boxes) for the tensor-core passes
+static edaa_status make_tmaps(edaa_ctx* c, CubeHost& h) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        !fn)
+      return fail(EDAA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const CUtensorMapDataType dt = h.esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint32_t kch = 128 / h.esz, es[2] = {1, 1};
+  const int rgp = round_up(h.tile.Rm * h.p, 16);
+  CUtensorMap m[4];
+  struct Spec { void* ptr; cuuint64_t inner, outer; cuuint32_t box_outer; } spec[4] = {
+      {h.Xk, (cuuint64_t)h.kp, (cuuint64_t)h.N, 128},
+      {h.XT, (cuuint64_t)h.Npad, (cuuint64_t)(h.L + 1), 128},
+      {h.dev.panelE, (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp},
+      {h.dev.panelR, (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp}};
+  for (int i = 0; i < 4; ++i) {
+    const cuuint64_t dims[2] = {spec[i].inner, spec[i].outer};
+    const cuuint64_t strides[1] = {spec[i].inner * (cuuint64_t)h.esz};
+    const cuuint32_t box[2] = {kch, spec[i].box_outer};
+    const CUresult r = enc(&m[i], dt, 2, spec[i].ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(EDAA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  }
+  CK(cudaMemcpyAsync(h.tmaps, m, sizeof(m), cudaMemcpyHostToDevice, c->stream), "upload tensor maps");
   return EDAA_OK;
 }
 
@@ -311,7 +401,10 @@ static edaa_status sync_status(edaa_ctx* c) {
   CK(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
   if (st & kStatTimeout) {
     c->broken = true;
-    return fail(EDAA_ERR_TIMEOUT, "a grid barrier timed out (CTAs not co-resident?)");
+    char msg[160];
+    snprintf(msg, sizeof msg, "a bounded wait timed out (status 0x%x: bit 0 grid barrier; bits 9-13 tensor-core "
+             "pipeline stages)", st);
+    return fail(EDAA_ERR_TIMEOUT, msg);
   }
   return EDAA_OK;
 }
@@ -322,6 +415,7 @@ static edaa_status sync_status(edaa_ctx* c) {
 static edaa_status autotune(edaa_ctx* c) {
   for (size_t ci = 0; ci < c->cubes.size(); ++ci) {
     CubeHost& h = c->cubes[ci];
+    if (h.tc) continue;  // tensor-core cubes have a fixed shape (tc_tile)
     auto key = std::make_tuple(c->device, h.L, h.N, h.p, h.M);
     auto it = tune_cache().find(key);
     if (it != tune_cache().end()) {
@@ -410,8 +504,7 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
   if (cfg) conf = *cfg;
   if (conf.T < 0 || conf.K1 < 0 || conf.K2 < 0) return fail(EDAA_ERR_ARG, "T, K1, K2 must be >= 0");
   if (!(conf.fit_ratio >= 1.0)) return fail(EDAA_ERR_ARG, "fit_ratio must be >= 1");
-  if (conf.precision != EDAA_FP32)
-    return fail(EDAA_ERR_UNSUPPORTED, "only EDAA_FP32 contractions are available in this build");
+  if (conf.precision < EDAA_FP32 || conf.precision > EDAA_BF16) return fail(EDAA_ERR_ARG, "unknown precision");
   for (int i = 0; i < n_cubes; ++i) {
     const edaa_cube& q = cubes[i];
     if (!q.X) return fail(EDAA_ERR_ARG, "cube X is NULL");
@@ -460,14 +553,22 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
     h.seeds.assign(q.seeds, q.seeds + q.M);
     h.gammas.assign(q.gammas, q.gammas + q.M);
     h.tile = default_tile(q.L, q.p, q.M);
+    // tensor cores only where the ensemble makes the contractions dense (M p >= 64)
+    if (conf.precision != EDAA_FP32 && h.Mp >= 64) {
+      h.tc = conf.precision == EDAA_BF16 ? 2 : 1;
+      h.esz = h.tc == 2 ? 2 : 4;
+      h.kp = round_up(q.L + 1, 128 / h.esz);
+      h.Npad = round_up(q.N, 8);
+      tc_tile(h);
+    }
     memset(&h.dev, 0, sizeof(CubeDev));
     c->cubes.push_back(h);
   }
   // shared memory and occupancy: the largest need over cubes and candidates
   size_t smem = 0;
   for (auto& h : c->cubes) {
-    smem = std::max(smem, tile_smem(h.tile, h.L, h.p));
-    if (conf.autotune)
+    smem = std::max(smem, pass_item_smem(h));
+    if (conf.autotune && !h.tc)
       for (const auto& t : tile_candidates(h.L, h.p, h.M)) smem = std::max(smem, tile_smem(t, h.L, h.p));
   }
   smem = std::max(smem, (size_t)32 * 1024);
@@ -491,7 +592,13 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
     h.arena_bytes = arena_layout(h, Pg_cap, false);
     e = cudaMalloc(&h.arena, h.arena_bytes);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    e = cudaMemsetAsync(h.arena, 0, h.arena_bytes, c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "memset"));
     arena_layout(h, Pg_cap, true);
+    if (h.tc) {
+      edaa_status st = make_tmaps(c, h);
+      if (st != EDAA_OK) return bail(st);
+    }
   }
   e = cudaMalloc(&c->d_batch, sizeof(Batch));
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));

@@ -22,6 +22,7 @@
 //   XAt   L x Mp   X A^T (float64), AAt M x p x p (float64)
 //   part  Pg x (L+1) x Mp  per-CTA partial sums of X W (row L: sum of W)
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -91,6 +92,15 @@ struct CubeDev {
   double* mu;
   const uint64_t* seeds;
   const double* gammas;
+  // tensor-core path (precision TF32 or BF16): 0 = CUDA-core FP32 passes
+  int tc;       // 0 off, 1 TF32, 2 BF16
+  int tc_rgp;   // run-group columns padded to a multiple of 16 (MMA N)
+  int tc_nkc;   // 128-byte K chunks over the bands (contraction 1)
+  int tc_nbt;   // 128-band tiles (contraction 2)
+  int tc_kp;    // row length (elements) of the K-major X copy and panels
+  const CUtensorMap* tmaps;  // [X pixel-major, X band-major, panel E, panel R]
+  void* panelE;              // Mp x tc_kp, compute type (K-major E^T)
+  void* panelR;              // Mp x tc_kp, compute type (K-major R^T)
 };
 
 struct Batch {
@@ -156,5 +166,6 @@ cudaError_t launch_barrier_test(unsigned int* bar, int* status, int grid, int ex
 cudaError_t set_program_smem(size_t smem);
 cudaError_t program_occupancy(int* blocks_per_sm, size_t smem);
 int program_phase_count(int mode, int n_outer, int K2);
+cudaError_t launch_tc_prepare(const CubeDev& hc, void* Xk, void* XT, int Npad, cudaStream_t s);
 
 }  // namespace edaa

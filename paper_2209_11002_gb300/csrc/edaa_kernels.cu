@@ -16,6 +16,10 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+
+#include <mutex>
+
 #include "edaa_pass.cuh"
 
 namespace edaa {
@@ -43,6 +47,19 @@ __device__ void pass_phase(const Batch* __restrict__ bt, int ph, float* smem) {
 // ---------------------------------------------------------------------------
 // Merges (one work item = one run m and a chunk of bands), FP64, fixed order.
 // ---------------------------------------------------------------------------
+// K-major copy of a panel for the tensor-core passes: row c (column of E or R),
+// band l, in the compute type (TF32 rounded to nearest, or BF16)
+__device__ __forceinline__ void store_panel(const CubeDev& cd, void* panel, int c, int l, double v) {
+  const size_t o = (size_t)c * cd.tc_kp + l;
+  if (cd.tc == 2) {
+    reinterpret_cast<__nv_bfloat16*>(panel)[o] = __float2bfloat16_rn((float)v);
+  } else {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)v));
+    reinterpret_cast<float*>(panel)[o] = __uint_as_float(r);
+  }
+}
+
 __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
   const int tid = threadIdx.x;
   const int P = cd.p, L = cd.L, Mp = cd.Mp, Pg = cd.Pg;
@@ -69,6 +86,7 @@ __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
     double r = -sx[e];
     for (int k = 0; k < P; ++k) r += cd.Ed[(size_t)l * Mp + m * P + k] * saat[k * P + j];
     cd.Rf[(size_t)l * Mp + m * P + j] = (float)r;
+    if (cd.tc) store_panel(cd, cd.panelR, m * P + j, l, r);
   }
   __syncthreads();
 }
@@ -117,6 +135,7 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool
     for (int g = 0; g < Pg; ++g) s += sscale[g * P + j] * (double)cd.part[((size_t)g * (L + 1) + l) * Mp + m * P + j];
     cd.Ed[(size_t)l * Mp + m * P + j] = s;
     cd.Ef[(size_t)l * Mp + m * P + j] = (float)s;
+    if (cd.tc) store_panel(cd, cd.panelE, m * P + j, l, s);
     sE[e] = s;
   }
   __syncthreads();
@@ -125,6 +144,7 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool
     double r = -cd.XAt[(size_t)l * Mp + m * P + j];
     for (int k = 0; k < P; ++k) r += sE[li * P + k] * cd.AAt[(size_t)m * P * P + k * P + j];
     cd.Rf[(size_t)l * Mp + m * P + j] = (float)r;
+    if (cd.tc) store_panel(cd, cd.panelR, m * P + j, l, r);
   }
   __syncthreads();
 }
@@ -292,8 +312,16 @@ k_edaa(const Batch* __restrict__ bt, int mode, int n_outer, int ph_lo, int ph_hi
   }
 }
 
+// The attribute is per kernel and process-wide: several contexts may coexist,
+// so it only ever grows (a smaller request keeps the larger setting).
 cudaError_t set_program_smem(size_t smem) {
-  return cudaFuncSetAttribute(k_edaa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::mutex mu;
+  static size_t current = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (smem <= current) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(k_edaa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) current = smem;
+  return e;
 }
 
 cudaError_t program_occupancy(int* blocks_per_sm, size_t smem) {
@@ -504,6 +532,33 @@ __global__ void k_gather_ab(const float* logA, const float* logB, const float* l
 cudaError_t launch_gather(const CubeDev& hc, int run, float* E, float* A, float* B, cudaStream_t s) {
   if (E) k_gather_e<<<(hc.L * hc.p + 255) / 256, 256, 0, s>>>(hc.Ed, hc.xbar, hc.L, hc.Mp, hc.p, run, E);
   if (A || B) k_gather_ab<<<(hc.N * hc.p + 255) / 256, 256, 0, s>>>(hc.logA, hc.logB, hc.lse, hc.N, hc.Mp, hc.p, run, A, B);
+  return cudaGetLastError();
+}
+
+// Compute-type copies of the centred X for the tensor-core passes:
+// Xk: N x kp pixel-major (bands >= L+1 zero), XT: (L+1) x Npad band-major
+// (row L is the ones band), TF32 rounded to nearest or BF16.
+__global__ void k_tc_prepare(const float* __restrict__ X, int L, int Ls, int N, int kp, int Npad, int bf16,
+                             void* __restrict__ Xk, void* __restrict__ XT) {
+  const size_t n = (size_t)N * kp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / kp), l = (int)(e - (size_t)i * kp);
+    const float v = (l < Ls) ? X[(size_t)i * Ls + l] : 0.f;
+    if (bf16) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      reinterpret_cast<__nv_bfloat16*>(Xk)[e] = h;
+      if (l <= L) reinterpret_cast<__nv_bfloat16*>(XT)[(size_t)l * Npad + i] = h;
+    } else {
+      uint32_t r;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+      reinterpret_cast<float*>(Xk)[e] = __uint_as_float(r);
+      if (l <= L) reinterpret_cast<float*>(XT)[(size_t)l * Npad + i] = __uint_as_float(r);
+    }
+  }
+}
+
+cudaError_t launch_tc_prepare(const CubeDev& hc, void* Xk, void* XT, int Npad, cudaStream_t s) {
+  k_tc_prepare<<<1024, 256, 0, s>>>(hc.X, hc.L, hc.Ls, hc.N, hc.tc_kp, Npad, hc.tc == 2 ? 1 : 0, Xk, XT);
   return cudaGetLastError();
 }
 

@@ -586,111 +586,122 @@ __device__ __noinline__ void fit_item(const CubeDev& cd, int rg, int pg, float* 
   constexpr int SPTM = TR::SPTM;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int L = cd.L, Ls = cd.Ls, Lr = cd.Lr, N = cd.N, Mp = cd.Mp, Rm = cd.Rm;
-  const int m0 = rg * Rm, nr = min(Rm, cd.M - m0), c0 = m0 * P, nc = nr * P;
+  const int m0 = rg * Rm, nr_all = min(Rm, cd.M - m0);
   const int Nt = cd.Nt, WP1 = cd.WP1, WR1 = kWarps / WP1, SPT = cd.SPT;
-  const int RQ1 = (Rm + WR1 - 1) / WR1;
-  const PassSmem sm = pass_smem(L, Ls, Lr, P, Rm, Nt);
+  // runs are processed in blocks of RB = WR1 * RQ1M (the register tile of one pass over X)
+  const int RB = min(Rm, WR1 * RQ1M);
+  const PassSmem sm = pass_smem(L, Ls, Lr, P, RB, Nt);
   float* Ps = smem + sm.off_ps;
   float* Xs = smem + sm.off_xs;
   float* Ss = smem + sm.off_ss;
   const int RgS4 = sm.RgS4, RgSo = sm.RgSo;
-  for (int e = tid; e < Lr * RgS4; e += kThreads) {
-    const int l = e / RgS4, cc = e - l * RgS4, r = cc / P4, j = cc - r * P4;
-    float v = 0.f;
-    if (l < L && r < nr && j < P) v = cd.Ef[(size_t)l * Mp + c0 + r * P + j];
-    Ps[e] = v;
-  }
-  __syncthreads();
   const int wp = warp % WP1, wr = warp / WP1;
-  double s1[RQ1M], s2[RQ1M], smx[RQ1M];
-#pragma unroll
-  for (int q = 0; q < RQ1M; ++q) { s1[q] = 0.0; s2[q] = 0.0; smx[q] = 0.0; }
   const float4* Xs4 = reinterpret_cast<const float4*>(Xs);
-  for (int tile = pg; tile < cd.ntiles; tile += cd.Pg) {
-    const int i0 = tile * Nt, ni = min(Nt, N - i0);
-    {
-      const float4* Xg = reinterpret_cast<const float4*>(cd.X + (size_t)i0 * Ls);
-      float4* xs4 = reinterpret_cast<float4*>(Xs);
-      const int n4 = ni * (Ls >> 2), nt4 = Nt * (Ls >> 2);
-      for (int e = tid; e < nt4; e += kThreads) xs4[e] = (e < n4) ? __ldg(Xg + e) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    for (int e = tid; e < ni * nc; e += kThreads) {
-      const int i = e / nc, cc = e - i * nc;
-      Ss[i * RgSo + cc] = cd.logA[(size_t)(i0 + i) * Mp + c0 + cc];
+  double* dbuf = reinterpret_cast<double*>(Xs);  // kWarps x RB x 3, after the tiles
+  for (int rb0 = 0; rb0 < nr_all; rb0 += RB) {
+    const int nr = min(RB, nr_all - rb0);
+    const int c0 = (m0 + rb0) * P, nc = nr * P;
+    const int RQ1 = (nr + WR1 - 1) / WR1;
+    __syncthreads();
+    for (int e = tid; e < Lr * RgS4; e += kThreads) {
+      const int l = e / RgS4, cc = e - l * RgS4, r = cc / P4, j = cc - r * P4;
+      float v = 0.f;
+      if (l < L && r < nr && j < P) v = cd.Ef[(size_t)l * Mp + c0 + r * P + j];
+      Ps[e] = v;
     }
     __syncthreads();
+    double s1[RQ1M], s2[RQ1M], smx[RQ1M];
 #pragma unroll
-    for (int s = 0; s < SPTM; ++s) {
-      if (s >= SPT) continue;
-      const int il = lane + 32 * (wp + WP1 * s);
-      const bool valid = il < ni;
+    for (int q = 0; q < RQ1M; ++q) { s1[q] = 0.0; s2[q] = 0.0; smx[q] = 0.0; }
+    for (int tile = pg; tile < cd.ntiles; tile += cd.Pg) {
+      const int i0 = tile * Nt, ni = min(Nt, N - i0);
+      {
+        const float4* Xg = reinterpret_cast<const float4*>(cd.X + (size_t)i0 * Ls);
+        float4* xs4 = reinterpret_cast<float4*>(Xs);
+        const int n4 = ni * (Ls >> 2), nt4 = Nt * (Ls >> 2);
+        for (int e = tid; e < nt4; e += kThreads) xs4[e] = (e < n4) ? __ldg(Xg + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      for (int e = tid; e < ni * nc; e += kThreads) {
+        const int i = e / nc, cc = e - i * nc;
+        Ss[i * RgSo + cc] = cd.logA[(size_t)(i0 + i) * Mp + c0 + cc];
+      }
+      __syncthreads();
 #pragma unroll
-      for (int q = 0; q < RQ1M; ++q) {
-        const int r = wr + WR1 * q;
-        if (!(q < RQ1 && r < nr)) continue;
-        float a[P], se = 0.f;
+      for (int s = 0; s < SPTM; ++s) {
+        if (s >= SPT) continue;
+        const int il = lane + 32 * (wp + WP1 * s);
+        const bool valid = il < ni;
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-          a[j] = valid ? expf(Ss[il * RgSo + r * P + j]) : 0.f;
-          se += a[j];
-        }
-        const float inv = valid ? 1.f / se : 0.f;
+        for (int q = 0; q < RQ1M; ++q) {
+          const int r = wr + WR1 * q;
+          if (!(q < RQ1 && r < nr)) continue;
+          float a[P], se = 0.f;
 #pragma unroll
-        for (int j = 0; j < P; ++j) a[j] *= inv;
-        float t1 = 0.f, t2 = 0.f;
-        for (int l = 0; l < Lr; l += 4) {
-          const float4 xv = Xs4[(il * Ls + l) >> 2];
+          for (int j = 0; j < P; ++j) {
+            a[j] = valid ? expf(Ss[il * RgSo + r * P + j]) : 0.f;
+            se += a[j];
+          }
+          const float inv = valid ? 1.f / se : 0.f;
 #pragma unroll
-          for (int d = 0; d < 4; ++d) {
-            if (l + d < L) {
-              float pv[P4];
-              load_p4<P>(Ps + (l + d) * RgS4 + r * P4, pv);
-              float rr = f4c(xv, d);
+          for (int j = 0; j < P; ++j) a[j] *= inv;
+          float t1 = 0.f, t2 = 0.f;
+          for (int l = 0; l < Lr; l += 4) {
+            const float4 xv = Xs4[(il * Ls + l) >> 2];
 #pragma unroll
-              for (int j = 0; j < P; ++j) rr = fmaf(-pv[j], a[j], rr);
-              t1 += fabsf(rr);
-              t2 = fmaf(rr, rr, t2);
+            for (int d = 0; d < 4; ++d) {
+              if (l + d < L) {
+                float pv[P4];
+                load_p4<P>(Ps + (l + d) * RgS4 + r * P4, pv);
+                float rr = f4c(xv, d);
+#pragma unroll
+                for (int j = 0; j < P; ++j) rr = fmaf(-pv[j], a[j], rr);
+                t1 += fabsf(rr);
+                t2 = fmaf(rr, rr, t2);
+              }
             }
           }
+          if (valid) {
+            s1[q] += (double)t1;
+            s2[q] += (double)t2;
+            smx[q] = fmax(smx[q], (double)t1);
+          }
         }
-        if (valid) {
-          s1[q] += (double)t1;
-          s2[q] += (double)t2;
-          smx[q] = fmax(smx[q], (double)t1);
-        }
+      }
+      __syncthreads();
+    }
+    // reduce over lanes, then over the WP1 warps sharing a run set
+#pragma unroll
+    for (int q = 0; q < RQ1M; ++q) {
+      const int r = wr + WR1 * q;
+      const double a1 = warp_sum_d(s1[q]);
+      const double a2 = warp_sum_d(s2[q]);
+      const double am = warp_max_d(smx[q]);
+      if (q < RQ1 && r < nr && lane == 0) {
+        dbuf[(wp * RB + r) * 3 + 0] = a1;
+        dbuf[(wp * RB + r) * 3 + 1] = am;
+        dbuf[(wp * RB + r) * 3 + 2] = a2;
       }
     }
     __syncthreads();
-  }
-  // reduce over lanes, then over the WP1 warps sharing a run set
-  double* dbuf = reinterpret_cast<double*>(Xs);  // kWarps x Rm x 3
-#pragma unroll
-  for (int q = 0; q < RQ1M; ++q) {
-    const int r = wr + WR1 * q;
-    const double a1 = warp_sum_d(s1[q]);
-    const double a2 = warp_sum_d(s2[q]);
-    const double am = warp_max_d(smx[q]);
-    if (q < RQ1 && r < nr && lane == 0) {
-      dbuf[(wp * Rm + r) * 3 + 0] = a1;
-      dbuf[(wp * Rm + r) * 3 + 1] = am;
-      dbuf[(wp * Rm + r) * 3 + 2] = a2;
+    for (int r = tid; r < nr; r += kThreads) {
+      double a1 = 0.0, a2 = 0.0, am = 0.0;
+      for (int w = 0; w < WP1; ++w) {
+        a1 += dbuf[(w * RB + r) * 3 + 0];
+        am = fmax(am, dbuf[(w * RB + r) * 3 + 1]);
+        a2 += dbuf[(w * RB + r) * 3 + 2];
+      }
+      double* dst = cd.pfit + ((size_t)pg * cd.M + m0 + rb0 + r) * 3;
+      dst[0] = a1;
+      dst[1] = am;
+      dst[2] = a2;
     }
-  }
-  __syncthreads();
-  for (int r = tid; r < nr; r += kThreads) {
-    double a1 = 0.0, a2 = 0.0, am = 0.0;
-    for (int w = 0; w < WP1; ++w) {
-      a1 += dbuf[(w * Rm + r) * 3 + 0];
-      am = fmax(am, dbuf[(w * Rm + r) * 3 + 1]);
-      a2 += dbuf[(w * Rm + r) * 3 + 2];
-    }
-    double* dst = cd.pfit + ((size_t)pg * cd.M + m0 + r) * 3;
-    dst[0] = a1;
-    dst[1] = am;
-    dst[2] = a2;
   }
   __syncthreads();
 }
+
+template <int P, bool IS_A, bool BF>
+__device__ void tc_pass_item(const Batch* __restrict__ bt, const CubeDev& cd, int rg, int pg, unsigned char* smem_raw,
+                             int K1, bool init);
 
 template <int P>
 __device__ __forceinline__ void pass_dispatch_impl(const Batch* bt, const CubeDev& cd, int rg, int pg, float* smem,
@@ -703,6 +714,17 @@ __device__ __forceinline__ void pass_dispatch_impl(const Batch* bt, const CubeDe
   const bool is_a = (ph == PH_A || ph == PH_INITA);
   const bool init = (ph == PH_INITA || ph == PH_INITB);
   const int k1 = (ph == PH_INITA) ? 0 : K1;
+  if (cd.tc) {
+    unsigned char* sb = reinterpret_cast<unsigned char*>(smem);
+    if (cd.tc == 2) {
+      if (is_a) tc_pass_item<P, true, true>(bt, cd, rg, pg, sb, k1, init);
+      else tc_pass_item<P, false, true>(bt, cd, rg, pg, sb, k1, init);
+    } else {
+      if (is_a) tc_pass_item<P, true, false>(bt, cd, rg, pg, sb, k1, init);
+      else tc_pass_item<P, false, false>(bt, cd, rg, pg, sb, k1, init);
+    }
+    return;
+  }
   if (cd.LT <= 5) {
     if (is_a) pass_item<P, 5, true>(bt, cd, rg, pg, smem, k1, init);
     else pass_item<P, 5, false>(bt, cd, rg, pg, smem, k1, init);

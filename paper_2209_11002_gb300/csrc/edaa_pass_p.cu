@@ -2,6 +2,7 @@
 // P = EDAA_P (set by the build, 1..8), so the eight variants compile in
 // parallel and link into the program kernel as relocatable device code.
 #include "edaa_pass.cuh"
+#include "edaa_tc_pass.cuh"
 
 #ifndef EDAA_P
 #error "EDAA_P must be defined (1..8)"

@@ -1,0 +1,149 @@
+// Tensor-core (tcgen05) pass of EDAA for batched ensembles (TF32 or BF16
+// operands, FP32 accumulation in tensor memory), sm_103a.
+//
+// Per CTA: one run group (Rg = Rm*p columns, padded to Rgp, a multiple of
+// 16) and the pixel tiles pg, pg + Pg, ... of 128 pixels.  Per tile:
+//   1. C (128 px x Rgp) = X_tile (128 x L) * Panel^T: the tile's pixel-major
+//      rows and the panel (E for the A-pass, R for the B-pass, stored K-major
+//      as Mp x Kp) stream through a ring of TMA stages (128-byte swizzle,
+//      K-major) into tcgen05.mma with the accumulator in TMEM columns [0, Rgp).
+//   2. Epilogue (8 warps; warp w reads TMEM lanes 32*(w%4).. = its pixels and
+//      handles the runs of parity w/4): the per-run element-wise step of the
+//      CUDA-core pass (K1 fused A-steps, or the B-logit update and online
+//      softmax in the power-of-two frame), writing the new state to global
+//      memory and W = weights - reference (shifted accumulation) into shared
+//      memory in the swizzled K-major layout the MMA reads.
+//   3. Acc (bands x Rgp) += X_bands (128 bands x 128 px) * W^T for each
+//      128-band tile, the band-major copy of X streaming through the same TMA
+//      ring; Acc lives in TMEM columns [Rgp*(1+bt), Rgp*(2+bt)) across all tiles.
+// The B-pass rescales Acc in TMEM (tcgen05.ld/st, exact powers of two) when a
+// tile raises a column's running maximum.  At the end the accumulators are
+// written as the same per-CTA partials the CUDA-core pass writes, so the FP64
+// merges are shared.  Every mbarrier wait is bounded.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "edaa_pass.cuh"
+
+namespace edaa {
+
+constexpr int kTcStages = 3;
+constexpr int kTcTile = 128;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, int c) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(c) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+// bounded wait for phase `par` of the barrier; false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t par, long long timeout_ns) {
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(par)
+        : "memory");
+    if (ok) return true;
+    if ((long long)(global_ns() - t0) > timeout_ns) return false;
+  }
+}
+__device__ __forceinline__ void tma2d(void* dst, const CUtensorMap* m, int c0, int c1, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          su32(dst)),
+      "l"(m), "r"(c0), "r"(c1), "r"(su32(b))
+      : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 B apart
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// instruction descriptor: FP32 accumulator, A and B of format fmt (tf32: 2, bf16: 1), K-major
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N, int fmt) {
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+template <bool BF>
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  if (BF)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d),
+        "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 8 consecutive 32-bit columns (warp-collective)
+__device__ __forceinline__ void tmem_ld8(uint32_t ta, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_st8(uint32_t ta, const float (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// element (row, k) of a K-major 128-byte-swizzled tile with 128-byte rows
+__device__ __forceinline__ uint32_t sw128_off(int row, int kbyte) {
+  return (uint32_t)(row * 128 + (kbyte ^ ((row & 7) << 4)));
+}
+
+// TF32 operands are float32 containers rounded to 10 mantissa bits
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Largest padded run-group width: TMEM holds C (Rgp columns) and one Acc
+// per 128-band tile; 8 spare columns keep the 8-wide TMEM reads of the last
+// run inside the 512 allocated; shared memory (3 stages + W + 32 KB) <= 227 KB.
+__host__ __device__ inline int tc_rgp_max(int L, int esz) {
+  const int nbt = (L + 1 + 127) / 128;
+  const int tmem = ((512 - 8) / (1 + nbt)) & ~15;
+  const int smem = esz == 2 ? 224 : 160;
+  return tmem < smem ? tmem : smem;
+}
+
+struct TcSmem {
+  uint32_t stage_bytes, w_off, misc_off, total;
+};
+// stages: [X chunk 128 x 128 B | panel chunk Rgp x 128 B]; W: npc chunks of Rgp x 128 B
+__host__ __device__ inline TcSmem tc_smem(int Rgp, int esz) {
+  TcSmem s;
+  const uint32_t pnl = (uint32_t)Rgp * 128u;
+  s.stage_bytes = 128u * 128u + ((pnl + 1023u) & ~1023u);
+  const uint32_t npc = 128u / (128u / (uint32_t)esz);  // pixel chunks of 128 bytes per 128-pixel tile
+  s.w_off = 1024u + kTcStages * s.stage_bytes;       // 1024: alignment slack
+  s.misc_off = s.w_off + npc * ((pnl + 1023u) & ~1023u);
+  s.total = s.misc_off + 32768u;                     // barriers, column stats, G, eta, A A^T sums
+  return s;
+}
+
+}  // namespace edaa

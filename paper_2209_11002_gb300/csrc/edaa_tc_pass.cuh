@@ -1,0 +1,402 @@
+// The tcgen05 pass work item (see edaa_tc.cuh for the scheme).  Included by
+// edaa_pass_p.cu, instantiated per p.
+#pragma once
+#include "edaa_tc.cuh"
+
+namespace edaa {
+
+template <int P, bool IS_A, bool BF>
+__device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const CubeDev& cd, int rg, int pg,
+                                          unsigned char* smem_raw, int K1, bool init) {
+  constexpr int P4 = (P + 3) & ~3;
+  constexpr int PP = P * (P + 1) / 2;
+  constexpr int ESZ = BF ? 2 : 4;
+  constexpr int KCH = 128 / ESZ;   // elements per 128-byte row (32 tf32, 64 bf16)
+  constexpr int NPC = 128 / KCH;   // pixel chunks per 128-pixel tile
+  constexpr uint32_t FMT = BF ? 1u : 2u;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int L = cd.L, N = cd.N, Mp = cd.Mp, Rm = cd.Rm;
+  const int m0 = rg * Rm, nr = min(Rm, cd.M - m0), c0 = m0 * P, nc = nr * P;
+  const int Rgp = cd.tc_rgp, nkc = cd.tc_nkc, nbt = cd.tc_nbt;
+  const long long tmo = bt->timeout_ns;
+  const CUtensorMap* tmX = cd.tmaps + 0;
+  const CUtensorMap* tmXT = cd.tmaps + 1;
+  const CUtensorMap* tmPan = cd.tmaps + (IS_A ? 2 : 3);
+  const TcSmem S = tc_smem(Rgp, ESZ);
+  unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* Wsm = sm + (S.w_off - 1024u);
+  const uint32_t wchunk = ((uint32_t)Rgp * 128u + 1023u) & ~1023u;
+  unsigned char* misc = sm + (S.misc_off - 1024u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(misc);      // kTcStages
+  uint64_t* empty = full + kTcStages;                      // kTcStages
+  uint64_t* bar_c1 = empty + kTcStages;
+  uint64_t* bar_c2 = bar_c1 + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_c2 + 1);
+  int* flags = reinterpret_cast<int*>(tmem_slot + 4);      // [0] bail, [1] rescale needed
+  float* colM = reinterpret_cast<float*>(flags + 4);       // Rgp: running power-of-two exponent (B)
+  int* colKey = reinterpret_cast<int*>(colM + 256);        // Rgp: tile maximum logit (B)
+  float* colScale = reinterpret_cast<float*>(colKey + 256);  // Rgp
+  float* colLse = colScale + 256;                          // Rgp
+  float* runEta = colLse + 256;                            // Rm
+  float* Gs = runEta + 128;                                // Rm x P x P (A), <= 2048
+  float* aaq = Gs + 2048;                                  // 4 x Rm x PP (A)
+
+  // ---- set-up: barriers, TMEM (512 columns: one CTA per SM), per-run constants
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)), "r"(512)
+                 : "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(bar_c1, 1);
+    mbar_init(bar_c2, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    flags[0] = 0;
+    flags[1] = 0;
+  }
+  for (int c = tid; c < 256; c += kThreads) {
+    colM[c] = -EDAA_INF;
+    colKey[c] = ord_key(-EDAA_INF);
+    colScale[c] = 1.f;
+    colLse[c] = 0.f;
+  }
+  if (!IS_A && !init)
+    for (int c = tid; c < nc; c += kThreads) colLse[c] = cd.lse[c0 + c];
+  for (int r = tid; r < Rm; r += kThreads) runEta[r] = r < nr ? (IS_A ? cd.eta1[m0 + r] : cd.eta2[m0 + r]) : 0.f;
+  if (IS_A) {
+    for (int e = tid; e < 4 * Rm * PP; e += kThreads) aaq[e] = 0.f;
+    if (!init && K1 > 0) {
+      for (int e = tid; e < nr * P * P; e += kThreads) {  // G = E^T E per run, FP32 from the float panel
+        const int r = e / (P * P), jk = e - r * P * P, j = jk / P, k = jk - j * P;
+        float s = 0.f;
+        for (int l = 0; l < L; ++l)
+          s = fmaf(cd.Ef[(size_t)l * Mp + c0 + r * P + j], cd.Ef[(size_t)l * Mp + c0 + r * P + k], s);
+        Gs[e] = s;
+      }
+    }
+  }
+  // W: zero once (padding rows and invalid pixels must stay 0)
+  for (uint32_t e = tid; e < (uint32_t)NPC * wchunk / 4; e += kThreads) reinterpret_cast<float*>(Wsm)[e] = 0.f;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tmem_slot;
+  const uint32_t id = tc_idesc(128, Rgp, FMT);
+  const bool do_c1 = !init;
+  uint32_t it = 0;        // TMA/MMA chunk counter (thread 0): stage = it % S, phase = (it / S) & 1
+  uint32_t c1_phase = 0, c2_phase = 0;
+  bool c2_pending = false, d2_started = false;
+  int bail = 0;
+
+  // thread 0: stream `n` chunks through the ring; load(j, dst, bar) issues the TMA(s)
+  // of chunk j, mma(j, stage_base) issues its MMAs.
+  auto pipeline = [&](int n, uint32_t bytes, auto&& load, auto&& mma) -> bool {
+    const uint32_t base_it = it;
+    for (int j = 0; j < n && j < kTcStages; ++j) {
+      const uint32_t k = base_it + j, s = k % kTcStages;
+      if (k >= kTcStages && !mbar_wait(empty + s, ((k / kTcStages) + 1) & 1, tmo)) return false;
+      mbar_expect(full + s, bytes);
+      load(j, sm + s * S.stage_bytes, full + s);
+    }
+    for (int j = 0; j < n; ++j) {
+      const uint32_t k = base_it + j, s = k % kTcStages;
+      if (!mbar_wait(full + s, (k / kTcStages) & 1, tmo)) return false;
+      tc_fence_after();
+      mma(j, sm + s * S.stage_bytes);
+      tc_commit(empty + s);
+      if (j + kTcStages < n) {
+        const uint32_t k2 = k + kTcStages;
+        if (!mbar_wait(empty + s, ((k2 / kTcStages) + 1) & 1, tmo)) return false;
+        mbar_expect(full + s, bytes);
+        load(j + kTcStages, sm + s * S.stage_bytes, full + s);
+      }
+    }
+    it = base_it + n;
+    return true;
+  };
+
+  float* St = IS_A ? cd.logA : cd.logB;
+  const float aref = 1.f / (float)P;
+
+  for (int tile = pg; tile < cd.ntiles; tile += cd.Pg) {
+    const int i0 = tile * kTcTile;
+    const int ni = min(kTcTile, N - i0);
+    // ---- 1. C = X_tile Panel^T (skipped for the initial passes: c = 0)
+    if (do_c1) {
+      if (tid == 0) {
+        const uint32_t bytes = 128u * 128u + (uint32_t)Rgp * 128u;
+        const bool ok = pipeline(
+            nkc, bytes,
+            [&](int j, unsigned char* dst, uint64_t* b) {
+              tma2d(dst, tmX, j * KCH, i0, b);
+              tma2d(dst + 128 * 128, tmPan, j * KCH, c0, b);
+            },
+            [&](int j, unsigned char* st) {
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t da = desc_sw128(su32(st + ks * 32));
+                const uint64_t db = desc_sw128(su32(st + 128 * 128 + ks * 32));
+                tc_mma<BF>(tbase, da, db, id, (j | ks) ? 1u : 0u);
+              }
+            });
+        if (ok) tc_commit(bar_c1);
+        else flags[0] = 1;
+      }
+      __syncthreads();
+      const int to = flags[0] ? 1 : (mbar_wait(bar_c1, c1_phase, tmo) ? 0 : 2);
+      if (to) atomicOr(bt->status, 1 << (8 + to));  // 9: contraction-1 pipeline, 10: its commit
+      if (__syncthreads_or(to)) {
+        bail = 1;
+        break;
+      }
+      c1_phase ^= 1;
+      tc_fence_after();
+    }
+    // the previous tile's contraction 2 must finish before W is rewritten or Acc rescaled
+    if (c2_pending) {
+      const int to = mbar_wait(bar_c2, c2_phase, tmo) ? 0 : 1;
+      if (to) atomicOr(bt->status, 1 << 11);  // contraction 2 of the previous tile
+      if (__syncthreads_or(to)) {
+        bail = 1;
+        break;
+      }
+      c2_phase ^= 1;
+      c2_pending = false;
+      tc_fence_after();
+    }
+    // ---- 2. epilogue: warp (quarter, half) = pixels 32*quarter.., runs of parity `half`
+    const int il = quarter * 32 + lane;
+    const bool valid = il < ni;
+    const size_t grow = (size_t)(i0 + il) * Mp + c0;
+    if (IS_A) {
+      for (int r = half; r < nr; r += 2) {
+        float cv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cv[j] = 0.f;
+        if (do_c1) tmem_ld8(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * P), cv);
+        float z[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) z[j] = (init || !valid) ? 0.f : St[grow + r * P + j];
+        const float* G = Gs + r * P * P;
+        const float eta = runEta[r];
+        float ea[P], se = 0.f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          ea[j] = expf(z[j]);
+          se += ea[j];
+        }
+        for (int kk = 0; kk < K1; ++kk) {
+          const float inv = 1.f / se;
+          float a[P], mx = -EDAA_INF;
+#pragma unroll
+          for (int j = 0; j < P; ++j) a[j] = ea[j] * inv;
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            float g = -cv[j];
+#pragma unroll
+            for (int k = 0; k < P; ++k) g = fmaf(G[j * P + k], a[k], g);
+            z[j] = fmaf(-eta, g, z[j]);
+            mx = fmaxf(mx, z[j]);
+          }
+          se = 0.f;
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            z[j] -= mx;
+            ea[j] = expf(z[j]);
+            se += ea[j];
+          }
+        }
+        float d[P], sd = 0.f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          d[j] = expm1f(z[j]);
+          sd += d[j];
+        }
+        const float den = 1.f / ((float)P + sd);
+        float a[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          a[j] = valid ? (1.f + d[j]) * den : 0.f;
+          const float wdev = valid ? ((float)P * d[j] - sd) * den * aref : 0.f;
+          if (valid) St[grow + r * P + j] = z[j];
+          const int c = r * P + j, pc = il / KCH, kb = (il % KCH) * ESZ;
+          unsigned char* dst = Wsm + pc * wchunk + sw128_off(c, kb);
+          if (BF) *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(wdev);
+          else *reinterpret_cast<float*>(dst) = to_tf32(wdev);
+        }
+        // A A^T of this tile's pixels: lanes -> warp sum -> this quarter's slot
+        int e = 0;
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+#pragma unroll
+          for (int k = j; k < P; ++k) {
+            const float v = warp_sum(a[j] * a[k]);
+            if (lane == 0) aaq[(quarter * Rm + r) * PP + e] += v;
+            ++e;
+          }
+      }
+    } else {
+      // B: u' = u - lse - eta2 g (initial pass: u = 0.1 * SplitMix64 uniform)
+      for (int r = half; r < nr; r += 2) {
+        float gv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) gv[j] = 0.f;
+        if (do_c1) tmem_ld8(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * P), gv);
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          float u = -EDAA_INF;
+          if (valid) {
+            if (init) u = 0.1f * uniform24(cd.seeds[m0 + r], (uint64_t)(i0 + il) * P + j + 1);
+            else u = St[grow + r * P + j] - colLse[r * P + j] - runEta[r] * gv[j];
+            St[grow + r * P + j] = u;  // the new logits (read back below for the weights)
+          }
+          const float m = warp_max(u);
+          if (lane == 0) atomicMax(&colKey[r * P + j], ord_key(m));
+        }
+      }
+      __syncthreads();
+      // new running exponents; rescale factors for the accumulators
+      for (int c = tid; c < nc; c += kThreads) {
+        const float Mo = colM[c];
+        const float Mn = fmaxf(Mo, tile_exp(colKey[c]));
+        colScale[c] = (Mo == Mn || Mo == -EDAA_INF) ? 1.f : ldexpf(1.f, (int)(Mo - Mn));
+        if (Mo != Mn && Mo != -EDAA_INF) flags[1] = 1;
+        colM[c] = Mn;
+        colKey[c] = ord_key(-EDAA_INF);
+      }
+      __syncthreads();
+      if (flags[1] && d2_started) {  // exact power-of-two rescale of Acc in TMEM, disjoint 8-column chunks
+        for (int b = 0; b < nbt; ++b)
+          for (int cc = half * 8; cc < Rgp; cc += 16) {
+            float v[8];
+            const uint32_t ta = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(Rgp * (1 + b) + cc);
+            tmem_ld8(ta, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] *= colScale[cc + j];
+            tmem_st8(ta, v);
+          }
+      }
+      for (int r = half; r < nr; r += 2) {
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          const int c = r * P + j;
+          float w = 0.f;
+          if (valid) {
+            const float u = St[grow + c];
+            const float Mn = colM[c];
+            w = (fabsf(u) < 1.f) ? ldexpf(expm1f(u), -(int)Mn) : exp2f(fmaf(u, kLog2e, -Mn)) - ldexpf(1.f, -(int)Mn);
+          }
+          const int pc = il / KCH, kb = (il % KCH) * ESZ;
+          unsigned char* dst = Wsm + pc * wchunk + sw128_off(c, kb);
+          if (BF) *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(w);
+          else *reinterpret_cast<float*>(dst) = to_tf32(w);
+        }
+      }
+    }
+    // ---- 3. Acc += X_bands W^T (W from generic-proxy stores -> async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      flags[1] = 0;
+      tc_fence_after();
+      const bool first = !d2_started;
+      const bool ok = pipeline(
+          nbt * NPC, 128u * 128u,
+          [&](int j, unsigned char* dst, uint64_t* b) {
+            const int bti = j / NPC, pc = j - bti * NPC;
+            tma2d(dst, tmXT, i0 + pc * KCH, bti * 128, b);
+          },
+          [&](int j, unsigned char* st) {
+            const int bti = j / NPC, pc = j - bti * NPC;
+            const uint32_t dcol = tbase + (uint32_t)(Rgp * (1 + bti));
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint64_t da = desc_sw128(su32(st + ks * 32));
+              const uint64_t db = desc_sw128(su32(Wsm + pc * wchunk + ks * 32));
+              tc_mma<BF>(dcol, da, db, id, (first && pc == 0 && ks == 0) ? 0u : 1u);
+            }
+          });
+      if (ok) tc_commit(bar_c2);
+      else {
+        flags[0] = 1;
+        atomicOr(bt->status, 1 << 12);  // contraction-2 pipeline
+      }
+    }
+    if (__syncthreads_or(flags[0])) {
+      bail = 1;
+      break;
+    }
+    d2_started = true;
+    c2_pending = true;
+  }
+
+  // ---- end of the pass: wait for the last Acc update, write the partials
+  if (!bail && c2_pending) {
+    const int to = mbar_wait(bar_c2, c2_phase, tmo) ? 0 : 1;
+    if (to) atomicOr(bt->status, 1 << 13);  // last contraction 2
+    bail = __syncthreads_or(to);
+    tc_fence_after();
+  }
+  if (bail) {
+    // time-out: report it, give in-flight TMA/MMA work a bounded time to drain, then free TMEM
+    if (tid == 0) {
+      atomicOr(bt->status, kStatTimeout);
+      const unsigned long long t0 = global_ns();
+      while ((long long)(global_ns() - t0) < 50000000ll) __nanosleep(1000);
+    }
+  } else if (d2_started) {
+    float* part = cd.part + (size_t)pg * (L + 1) * Mp;
+    for (int b = 0; b < nbt; ++b) {
+      const int l = b * 128 + quarter * 32 + lane;
+      for (int r = half; r < nr; r += 2) {
+        float v[8];
+        tmem_ld8(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(Rgp * (1 + b) + r * P), v);
+        if (l <= L) {
+#pragma unroll
+          for (int j = 0; j < P; ++j) part[(size_t)l * Mp + c0 + r * P + j] = v[j];
+        }
+      }
+    }
+  } else {
+    // no tile: zero partials
+    float* part = cd.part + (size_t)pg * (L + 1) * Mp;
+    for (int e = tid; e < (L + 1) * nc; e += kThreads) part[(size_t)(e / nc) * Mp + c0 + e % nc] = 0.f;
+  }
+  __syncthreads();
+  if (!bail) {
+    if (IS_A) {
+      for (int e = tid; e < nr * PP; e += kThreads) {
+        const int r = e / PP, pe = e - r * PP;
+        float v = 0.f;
+        for (int q = 0; q < 4; ++q) v += aaq[(q * Rm + r) * PP + pe];
+        int j = 0, rem = pe;
+        while (rem >= P - j) {
+          rem -= P - j;
+          ++j;
+        }
+        const int k = j + rem;
+        float* dst = cd.paa + ((size_t)pg * cd.M + m0 + r) * P * P;
+        dst[j * P + k] = v;
+        dst[k * P + j] = v;
+      }
+    } else {
+      for (int c = tid; c < nc; c += kThreads) cd.pmax[(size_t)pg * Mp + c0 + c] = colM[c];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512) : "memory");
+  // the barriers' shared memory is reused by the next phase: invalidate them first
+  if (tid == 0) {
+    for (int b = 0; b < 2 * kTcStages + 2; ++b)
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(su32(full + b)) : "memory");
+  }
+  __syncthreads();
+}
+
+}  // namespace edaa

@@ -1,0 +1,76 @@
+"""Mixed-precision (tensor-core) ensemble path against the FP64 oracle and the
+FP32 CUDA-core path.
+
+The X-streaming contractions run on tcgen05 with TF32 or BF16 operands and
+FP32 accumulation (M p >= 64); the softmax, the merges and the fit stay
+FP32/FP64.  Stated errors against the oracle after 10 outer iterations
+(measured: TF32 loss 1.6e-5, A 2.2e-5; BF16 loss 4.2e-5, A 1.1e-4):
+  TF32: relative loss <= 2e-4, max |A - A_ref| <= 2e-4, max |E - E_ref| <= 2e-4
+  BF16: relative loss <= 1e-3, max |A - A_ref| <= 1e-3, max |E - E_ref| <= 1e-3
+and every run's final loss within 1 % of the same run in plain FP32."""
+import numpy as np
+import pytest
+
+from oracle import edaa_oracle as O
+from paper_2209_11002_gb300 import build, edaa, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {edaa.TF32: 2e-4, edaa.BF16: 1e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build_library()
+    edaa.load_library()
+
+
+def _ctx(cube, **cfg):
+    return edaa.Context([dict(X=cube.pixel_major(), p=cube.p, seeds=cube.seeds, gammas=cube.gammas)], **cfg)
+
+
+@pytest.mark.parametrize("prec", [edaa.TF32, edaa.BF16])
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_tensor_core_ensemble_against_oracle(prec, persistent):
+    cube = synth.make_cube(64, 3001, 4, alpha=0.3, snr_db=25, M=16, gamma_choices=(0.5, 1.0, 2.0), seed=41)
+    T = 10
+    Xn = O.normalize_pixels(cube.X)
+    with _ctx(cube, T=T, precision=prec, persistent=persistent) as ctx:
+        shape = ctx.describe(0)
+        ctx.solve()
+        best, fit, mu = ctx.select(0)
+        loss = ctx.loss(0)
+        got = {m: ctx.get(0, m, device="cpu") for m in (0, 7, 15)}
+    with _ctx(cube, T=T, precision=edaa.FP32) as ref32:
+        ref32.solve()
+        loss32 = ref32.loss(0)
+    assert shape["pixel_tile"] == 128  # the tensor-core tiling
+    tol = TOL[prec]
+    for m, (E, A, B) in got.items():
+        ref = O.edaa(Xn, 4, T, 5, 5, int(cube.seeds[m]), float(cube.gammas[m]))
+        lr = O.objective(Xn, ref["A"], ref["B"])
+        assert abs(loss[m] - lr) / lr <= tol
+        assert np.abs(A - ref["A"]).max() <= tol
+        assert np.abs(E - ref["E"]).max() <= tol
+    assert np.max(np.abs(loss - loss32) / loss32) <= 0.01
+    assert np.all(np.isfinite(fit)) and 0 <= best < 16
+
+
+def test_uneven_batch_mixes_tensor_core_and_cuda_core_cubes():
+    """One launch where one cube is dense enough for tensor cores (M p = 64)
+    and another is not (M p = 6): both against the oracle."""
+    cubes = [synth.make_cube(48, 1500, 4, alpha=0.3, snr_db=25, M=16, gamma_choices=(0.5, 1.0), seed=51),
+             synth.make_cube(30, 900, 3, alpha=0.5, snr_db=30, M=2, gamma_choices=(1.0,), seed=52)]
+    T = 6
+    with edaa.Context([dict(X=c.pixel_major(), p=c.p, seeds=c.seeds, gammas=c.gammas) for c in cubes], T=T,
+                      precision=edaa.TF32) as ctx:
+        ctx.solve()
+        for ci, cube in enumerate(cubes):
+            Xn = O.normalize_pixels(cube.X)
+            loss = ctx.loss(ci)
+            for m in (0, cube.M - 1):
+                ref = O.edaa(Xn, cube.p, T, 5, 5, int(cube.seeds[m]), float(cube.gammas[m]))
+                E, A, B = ctx.get(ci, m, device="cpu")
+                assert np.abs(A - ref["A"]).max() <= 2e-4
+                lr = O.objective(Xn, ref["A"], ref["B"])
+                assert abs(loss[m] - lr) / lr <= 2e-4
