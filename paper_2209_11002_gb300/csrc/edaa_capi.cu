@@ -203,7 +203,7 @@ static void plan(edaa_ctx* c) {
     h.lchunk = lch;
     h.nlchunk = (h.L + lch - 1) / lch;
     // the B-merge keeps Pg x p scale factors in shared memory
-    const int pg_fit = (int)((c->smem / 8 - 16 - (size_t)2 * kMaxP - (size_t)lch * h.p) / h.p);
+    const int pg_fit = (int)((c->smem / 8 - 16 - (size_t)2 * kMaxP - (size_t)2 * lch * h.p) / h.p);
     if (h.Pg > pg_fit) h.Pg = std::max(1, pg_fit);
     CubeDev& d = h.dev;
     d.L = h.L; d.Ls = h.Ls; d.Lr = h.Lr; d.N = h.N; d.p = h.p; d.M = h.M; d.Mp = h.Mp;
@@ -240,8 +240,8 @@ static size_t pass_item_smem(const CubeHost& h) {
 
 static size_t cube_smem(const CubeHost& h) {
   size_t s = pass_item_smem(h);
-  const size_t mb = (size_t)(2 * kMaxP + h.lchunk * h.p + h.Pg * h.p) * 8 + 64;
-  const size_t ma = (size_t)(64 + h.lchunk * h.p) * 8;
+  const size_t mb = (size_t)(2 * kMaxP + 2 * h.lchunk * h.p + h.Pg * h.p) * 8 + 64;
+  const size_t ma = (size_t)(64 + 2 * h.lchunk * h.p) * 8;
   return std::max(s, std::max(ma, mb));
 }
 
@@ -263,6 +263,7 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
   size_t opaa = take((size_t)Pg_cap * M * p * p * 4), opfit = take((size_t)Pg_cap * M * 3 * 8);
   size_t ofit = take(M * 8), ofitmax = take(M * 8), oloss = take(M * 8), omu = take(M * 8);
   size_t oseeds = take(M * 8), ogam = take(M * 8);
+  size_t orho = take(L * Mp * 8), obref = take(Mp * 4);  // nlchunk <= L band chunks
   const size_t tcb = h.tc ? 1 : 0;
   size_t oXk = take(tcb * N * h.kp * h.esz), oXT = take(tcb * (L + 1) * h.Npad * h.esz);
   size_t opE = take(tcb * Mp * h.kp * h.esz), opR = take(tcb * Mp * h.kp * h.esz), otm = take(tcb * 4 * 128);
@@ -295,6 +296,8 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
     d.mu = (double*)(b + omu);
     d.seeds = (const uint64_t*)(b + oseeds);
     d.gammas = (const double*)(b + ogam);
+    d.rho = (double*)(b + orho);
+    d.bref = (int*)(b + obref);
     d.xbar = (double*)(b + oxbar);
     d.sx = (double*)(b + osx);
     h.bsum = (double*)(b + obsum);

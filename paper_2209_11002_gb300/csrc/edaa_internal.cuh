@@ -90,6 +90,8 @@ struct CubeDev {
   double* fitmax;
   double* loss2;
   double* mu;
+  double* rho;     // nlchunk x Mp: per band chunk, sum_l E[l][c] R[l][c] (FP64) for the next B-pass
+  int* bref;       // Mp: reference exponent k of the B-pass just run (weights shifted by 2^k)
   const uint64_t* seeds;
   const double* gammas;
   // tensor-core path (precision TF32 or BF16): 0 = CUDA-core FP32 passes

@@ -60,11 +60,26 @@ __device__ __forceinline__ void store_panel(const CubeDev& cd, void* panel, int 
   }
 }
 
+// rho[lc][c] = sum over the chunk's bands of E[l][c] R[l][c], in a fixed
+// order (lanes strided over the bands, then a butterfly): the reference
+// exponent of the next B-pass is derived from these sums.
+__device__ void chunk_rho(const CubeDev& cd, int m, int lc, int nl, const double* sprod) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, P = cd.p;
+  if (warp < P) {
+    double s = 0.0;
+    for (int li = lane; li < nl; li += 32) s += sprod[li * P + warp];
+    s = warp_sum_d(s);
+    if (lane == 0) cd.rho[(size_t)lc * cd.Mp + m * P + warp] = s;
+  }
+  __syncthreads();
+}
+
 __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
   const int tid = threadIdx.x;
   const int P = cd.p, L = cd.L, Mp = cd.Mp, Pg = cd.Pg;
   double* saat = reinterpret_cast<double*>(smem);  // P*P
   double* sx = saat + 64;                          // lchunk * P
+  double* sprod = sx + cd.lchunk * P;              // lchunk * P: E R products
   for (int e = tid; e < P * P; e += kThreads) {
     double s = 0.0;
     for (int g = 0; g < Pg; ++g) s += (double)cd.paa[((size_t)g * cd.M + m) * P * P + e];
@@ -87,8 +102,10 @@ __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
     for (int k = 0; k < P; ++k) r += cd.Ed[(size_t)l * Mp + m * P + k] * saat[k * P + j];
     cd.Rf[(size_t)l * Mp + m * P + j] = (float)r;
     if (cd.tc) store_panel(cd, cd.panelR, m * P + j, l, r);
+    sprod[e] = cd.Ed[(size_t)l * Mp + m * P + j] * r;
   }
   __syncthreads();
+  chunk_rho(cd, m, lc, nl, sprod);
 }
 
 __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool init) {
@@ -97,7 +114,8 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool
   double* sS = reinterpret_cast<double*>(smem);  // kMaxP: softmax denominators
   double* sW = sS + kMaxP;                        // kMaxP: w_ref / S
   double* sE = sW + kMaxP;                        // lchunk * P
-  double* sscale = sE + cd.lchunk * P;            // Pg * P
+  double* sprod = sE + cd.lchunk * P;             // lchunk * P: E R products
+  double* sscale = sprod + cd.lchunk * P;         // Pg * P
   (void)init;
   const double logN = log((double)cd.N);
   if (warp < P) {
@@ -115,9 +133,9 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool
     }
     S = warp_sum_d(S);
     if (lane == 0) {
-      // shifted accumulation: every pixel contributed w - 2^-e_g, i.e. 2^-mx in
-      // the merged frame; add N * 2^-mx back to the denominator
-      const double wref = ldexp(1.0, -(int)mx);
+      // shifted accumulation: every pixel contributed w - 2^(k-e_g), i.e.
+      // 2^(k-mx) in the merged frame; add N * 2^(k-mx) back to the denominator
+      const double wref = ldexp(1.0, cd.bref[c] - (int)mx);
       S += wref * (double)cd.N;
       sS[j] = S;
       sW[j] = wref / S;
@@ -145,8 +163,10 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool
     for (int k = 0; k < P; ++k) r += sE[li * P + k] * cd.AAt[(size_t)m * P * P + k * P + j];
     cd.Rf[(size_t)l * Mp + m * P + j] = (float)r;
     if (cd.tc) store_panel(cd, cd.panelR, m * P + j, l, r);
+    sprod[e] = sE[e] * r;
   }
   __syncthreads();
+  chunk_rho(cd, m, lc, nl, sprod);
 }
 
 __device__ void merge_phase(const Batch* __restrict__ bt, int ph, float* smem) {

@@ -46,9 +46,42 @@ __device__ __forceinline__ float ord_val(int k) { return __int_as_float(k >= 0 ?
 // reference weight 2^-e are exact powers of two: the merge can then add the
 // reference term back without any rounding mismatch.
 constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.69314718055994531f;
 __device__ __forceinline__ float tile_exp(int key) {
   const float m = ord_val(key);
   return m == -EDAA_INF ? m : ceilf(m * kLog2e);
+}
+
+// Reference of the shifted B accumulation.  Column c subtracts the weight of
+// the logit k ln 2 from every pixel and the merge adds N 2^k back.  Near
+// uniform B (logits near 0) k = 0, so the summands are the small deviations
+// from uniform.  Far from uniform, logit 0 can sit far above every logit of
+// the column, and a reference of 2^0 would then dwarf the sum it is taken
+// from; so k is capped by a lower bound of log mean_i e^{u_i} that is known
+// before the pass.  With u_i = log(N b_i) - eta2 c_i, c = X^T R, Jensen's
+// inequality under the weights b gives
+//     log mean_i e^{u_i} = log sum_i b_i e^{-eta2 c_i} >= -eta2 sum_i b_i c_i
+//                        = -eta2 E_c^T R_c,            E = X B, eq. (update_B),
+// hence N 2^k <= sqrt(2) sum_i e^{u_i}: no overflow and no cancellation worse
+// than a factor of about two.  The per-chunk sums are added in a fixed order,
+// so every CTA and the merge compute the same k.
+__device__ __forceinline__ int ref_exponent(const CubeDev& cd, int m, int c) {
+  double s = 0.0;
+  for (int lc = 0; lc < cd.nlchunk; ++lc) s += cd.rho[(size_t)lc * cd.Mp + c];
+  const double t = -cd.eta2d[m] * s * 1.4426950408889634;
+  if (!(fabs(t) < 16384.0)) return t < 0.0 ? -16384 : 0;  // also non-finite
+  return (int)rint(t);
+}
+
+// Shifted weight of logit u in the power-of-two frame Mn with reference 2^k:
+// e^u 2^-Mn - 2^(k-Mn).  Near the reference the difference is formed by
+// expm1 and is exact to rounding.
+__device__ __forceinline__ float shifted_weight(float u, float Mn, int k) {
+  if (k == 0)
+    return (fabsf(u) < 1.f) ? ldexpf(expm1f(u), -(int)Mn) : exp2f(fmaf(u, kLog2e, -Mn)) - ldexpf(1.f, -(int)Mn);
+  const float s = fmaf(u, kLog2e, -(float)k);  // log2 of e^u / 2^k
+  return (fabsf(s) < 1.5f) ? ldexpf(expm1f(s * kLn2), k - (int)Mn)
+                           : exp2f(fmaf(u, kLog2e, -Mn)) - ldexpf(1.f, k - (int)Mn);
 }
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output number n of the
@@ -172,6 +205,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
   float* colLse = smem + sm.off_col;
   float* colM = colLse + sm.RgS4;
   int* colKey = reinterpret_cast<int*>(colM + sm.RgS4);
+  int* colRef = colKey + sm.RgS4;  // B: reference exponent k of the shifted weights
   float* runEta = smem + sm.off_run;
   const int RgS4 = sm.RgS4, RgSo = sm.RgSo, RgW = sm.RgW;
 
@@ -190,9 +224,13 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
   if (!IS_A) {
     for (int c = tid; c < RgS4; c += kThreads) {
       const int r = c / P4, j = c - r * P4;
-      colLse[c] = (!init && r < nr && j < P) ? cd.lse[c0 + r * P + j] : 0.f;
+      const bool live = r < nr && j < P;
+      colLse[c] = (!init && live) ? cd.lse[c0 + r * P + j] : 0.f;
       colM[c] = -EDAA_INF;
       colKey[c] = ord_key(-EDAA_INF);
+      const int k = (!init && live) ? ref_exponent(cd, m0 + r, c0 + r * P + j) : 0;
+      colRef[c] = k;
+      if (pg == 0 && live) cd.bref[c0 + r * P + j] = k;
     }
   }
   __syncthreads();
@@ -416,11 +454,8 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
             if (j < P && valid) {
               const int c = r * P4 + j;
               const float Mn = fmaxf(colM[c], tile_exp(colKey[c]));  // power-of-two frame
-              // w = e^u 2^-Mn minus the reference weight 2^-Mn (logit 0: uniform b);
-              // near u = 0 the difference is 2^-Mn expm1(u), exact to rounding
-              const float u = ur[s][q][j];
-              w[j] = (fabsf(u) < 1.f) ? ldexpf(expm1f(u), -(int)Mn)
-                                      : exp2f(fmaf(u, kLog2e, -Mn)) - ldexpf(1.f, -(int)Mn);
+              // w = e^u 2^-Mn minus the reference weight 2^(k-Mn) (k = 0: uniform b)
+              w[j] = shifted_weight(ur[s][q][j], Mn, colRef[c]);
             }
           }
           if (valid) {

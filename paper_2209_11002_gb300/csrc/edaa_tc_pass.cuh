@@ -38,8 +38,9 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   int* colKey = reinterpret_cast<int*>(colM + 256);        // Rgp: tile maximum logit (B)
   float* colScale = reinterpret_cast<float*>(colKey + 256);  // Rgp
   float* colLse = colScale + 256;                          // Rgp
-  float* runEta = colLse + 256;                            // Rm
-  float* Gs = runEta + 128;                                // Rm x P x P (A), <= 2048
+  float* runEta = colLse + 256;                            // Rm (<= 128)
+  int* colRef = reinterpret_cast<int*>(runEta + 128);      // Rgp: reference exponent k (B)
+  float* Gs = reinterpret_cast<float*>(colRef + 256);      // Rm x P x P (A), <= 2048
   float* aaq = Gs + 2048;                                  // 4 x Rm x PP (A)
 
   // ---- set-up: barriers, TMEM (512 columns: one CTA per SM), per-run constants
@@ -64,8 +65,15 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     colScale[c] = 1.f;
     colLse[c] = 0.f;
   }
-  if (!IS_A && !init)
-    for (int c = tid; c < nc; c += kThreads) colLse[c] = cd.lse[c0 + c];
+  if (!IS_A)
+    for (int c = tid; c < 256; c += kThreads) {
+      const int k = (!init && c < nc) ? ref_exponent(cd, m0 + c / P, c0 + c) : 0;
+      colRef[c] = k;
+      if (c < nc) {
+        if (!init) colLse[c] = cd.lse[c0 + c];
+        if (pg == 0) cd.bref[c0 + c] = k;
+      }
+    }
   for (int r = tid; r < Rm; r += kThreads) runEta[r] = r < nr ? (IS_A ? cd.eta1[m0 + r] : cd.eta2[m0 + r]) : 0.f;
   if (IS_A) {
     for (int e = tid; e < 4 * Rm * PP; e += kThreads) aaq[e] = 0.f;
@@ -287,8 +295,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
           float w = 0.f;
           if (valid) {
             const float u = St[grow + c];
-            const float Mn = colM[c];
-            w = (fabsf(u) < 1.f) ? ldexpf(expm1f(u), -(int)Mn) : exp2f(fmaf(u, kLog2e, -Mn)) - ldexpf(1.f, -(int)Mn);
+            w = shifted_weight(u, colM[c], colRef[c]);
           }
           const int pc = il / KCH, kb = (il % KCH) * ESZ;
           unsigned char* dst = Wsm + pc * wchunk + sw128_off(c, kb);

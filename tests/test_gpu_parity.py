@@ -72,6 +72,31 @@ def test_gradients_per_outer_iteration(persistent):
     assert max(max(v) for v in errs.values()) <= 1e-5
 
 
+def test_large_step_factors_urban_shape():
+    """gamma = 8 and 4, the top of the step-factor set S, on the Urban-shaped
+    cube (L=162, N=94249, p=6).  One B-step there moves whole columns of
+    logits by tens of nats, to maxima well below zero, so the shifted
+    accumulation has to take its reference below the column's mean weight.
+    The loss at every outer boundary t <= 3 within 1e-4 of the oracle, and
+    A, E within 1e-3 at t = 3."""
+    cube = synth.workload(synth.URBAN_PRECISION, M=2)
+    cube.gammas = np.array([8.0, 4.0])
+    T = 3
+    refs = [_oracle(cube, m, T, record=True) for m in range(2)]
+    with _ctx([cube], T=T) as ctx:
+        for t in range(T + 1):
+            loss = ctx.loss(0)
+            for m in range(2):
+                lr = refs[m]["hist"]["loss"][t]
+                assert np.isfinite(loss[m]) and abs(loss[m] - lr) / lr <= 1e-4, (t, m, loss[m], lr)
+            if t < T:
+                ctx.step(1)
+        for m in range(2):
+            E, A, B = ctx.get(0, m, device="cpu")
+            assert np.abs(A - refs[m]["A"]).max() <= 1e-3
+            assert np.abs(E - refs[m]["E"]).max() <= 1e-3
+
+
 def test_centring_is_an_exact_reparametrisation():
     """Running on X minus its mean pixel leaves EDAA's iterates unchanged."""
     cube = synth.make_cube(40, 1800, 4, alpha=0.4, snr_db=25, M=3, gamma_choices=(0.5, 1.0, 2.0), seed=20)
