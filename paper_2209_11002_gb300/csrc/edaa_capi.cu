@@ -207,6 +207,7 @@ static void plan(edaa_ctx* c) {
     if (h.Pg > pg_fit) h.Pg = std::max(1, pg_fit);
     CubeDev& d = h.dev;
     d.L = h.L; d.Ls = h.Ls; d.Lr = h.Lr; d.N = h.N; d.p = h.p; d.M = h.M; d.Mp = h.Mp;
+    d.Nst = round_up(h.N, 32);
     d.LT = (h.L + 1 + 31) / 32;
     d.Rm = h.tile.Rm; d.RG = h.RG; d.Pg = h.Pg; d.Nt = h.Nt; d.WP1 = h.tile.WP1; d.SPT = h.tile.SPT;
     d.WP2 = h.tile.WP2; d.ntiles = h.ntiles;
@@ -255,7 +256,8 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
     return o;
   };
   const size_t N = h.N, L = h.L, Mp = h.Mp, M = h.M, p = h.p, Ls = h.Ls;
-  size_t oX = take(N * Ls * 4), oXin = take(N * L * 4), oA = take(N * Mp * 4), oB = take(N * Mp * 4);
+  const size_t Nst = round_up(h.N, 32);  // state rows: one run column over the pixels
+  size_t oX = take(N * Ls * 4), oXin = take(N * L * 4), oA = take(Nst * Mp * 4), oB = take(Nst * Mp * 4);
   size_t oEf = take(L * Mp * 4), oEd = take(L * Mp * 8), oRf = take(L * Mp * 4), oXAt = take(L * Mp * 8);
   size_t oAAt = take(M * p * p * 8), olse = take(Mp * 4), oe1 = take(M * 4), oe2 = take(M * 4);
   size_t oe1d = take(M * 8), oe2d = take(M * 8), osig = take(M * 8);
@@ -264,6 +266,7 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
   size_t ofit = take(M * 8), ofitmax = take(M * 8), oloss = take(M * 8), omu = take(M * 8);
   size_t oseeds = take(M * 8), ogam = take(M * 8);
   size_t orho = take(L * Mp * 8), obref = take(Mp * 4);  // nlchunk <= L band chunks
+  size_t ogpart = take(L * M * p * p * 8);
   const size_t tcb = h.tc ? 1 : 0;
   size_t oXk = take(tcb * N * h.kp * h.esz), oXT = take(tcb * (L + 1) * h.Npad * h.esz);
   size_t opE = take(tcb * Mp * h.kp * h.esz), opR = take(tcb * Mp * h.kp * h.esz), otm = take(tcb * 4 * 128);
@@ -298,6 +301,7 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
     d.gammas = (const double*)(b + ogam);
     d.rho = (double*)(b + orho);
     d.bref = (int*)(b + obref);
+    d.gpart = (double*)(b + ogpart);
     d.xbar = (double*)(b + oxbar);
     d.sx = (double*)(b + osx);
     h.bsum = (double*)(b + obsum);

@@ -12,9 +12,11 @@
 //         softmax denominators for free), columns L+1..Ls-1 are zero.
 //         Ls = smallest multiple of 4 >= L+1 with Ls/4 odd, so 16-byte rows
 //         and conflict-free 128-bit shared-memory reads across pixels.
-//   logA  N x Mp   z = log a - max_j log a per pixel and run (A = softmax_j z);
-//                  column m*p+j is abundance j of run m, pixel-major
-//   logB  N x Mp   logits u of B in the frame log(N b): B = exp(u - lse - log N)
+//   logA  Mp x Nst z = log a - max_j log a per pixel and run (A = softmax_j z);
+//                  row m*p+j is abundance j of run m over the pixels, rows
+//                  padded to Nst = N rounded up to 32 (a warp's 32 pixels of
+//                  one column are one 128-byte line)
+//   logB  Mp x Nst logits u of B in the frame log(N b): B = exp(u - lse - log N)
 //                  with lse stored as (log-sum-exp - log N); both stay near 0
 //                  while B is near uniform, where float32 spacing is finest
 //   Ef/Ed L x Mp   E = X B (float32 panel and float64 master copy)
@@ -62,6 +64,7 @@ enum Phase {
 
 struct CubeDev {
   int L, Ls, Lr, N, p, M, Mp, LT;
+  int Nst;                     // row length of the state arrays logA / logB (N rounded up to 32)
   int Rm, RG, Pg, Nt, WP1, SPT, WP2, ntiles;
   int cta0;                    // first pass work item of this cube
   int lchunk, nlchunk, unit0;  // merge work items: M * nlchunk from unit0
@@ -92,6 +95,7 @@ struct CubeDev {
   double* mu;
   double* rho;     // nlchunk x Mp: per band chunk, sum_l E[l][c] R[l][c] (FP64) for the next B-pass
   int* bref;       // Mp: reference exponent k of the B-pass just run (weights shifted by 2^k)
+  double* gpart;   // nlchunk x M x p x p: per band chunk, E^T E of each run (FP64)
   const uint64_t* seeds;
   const double* gammas;
   // tensor-core path (precision TF32 or BF16): 0 = CUDA-core FP32 passes

@@ -74,6 +74,25 @@ __device__ void chunk_rho(const CubeDev& cd, int m, int lc, int nl, const double
   __syncthreads();
 }
 
+// Sum over the Pg per-CTA partials of one element (stride apart), each
+// scaled by scale[g * sstride] when scale is given.  Eight independent
+// chains keep eight loads in flight; they are combined in a fixed tree, so
+// the result does not depend on the launch mode.
+__device__ __forceinline__ double sum_partials(const float* __restrict__ v, size_t stride, int Pg,
+                                               const double* scale, int sstride) {
+  double c[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int g = 0;
+  for (; g + 8 <= Pg; g += 8) {
+    float x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = v[(size_t)(g + q) * stride];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) c[q] += (scale ? scale[(g + q) * sstride] : 1.0) * (double)x[q];
+  }
+  for (int q = 0; g < Pg; ++g, ++q) c[q] += (scale ? scale[g * sstride] : 1.0) * (double)v[(size_t)g * stride];
+  return ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+}
+
 __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
   const int tid = threadIdx.x;
   const int P = cd.p, L = cd.L, Mp = cd.Mp, Pg = cd.Pg;
@@ -82,7 +101,7 @@ __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
   double* sprod = sx + cd.lchunk * P;              // lchunk * P: E R products
   for (int e = tid; e < P * P; e += kThreads) {
     double s = 0.0;
-    for (int g = 0; g < Pg; ++g) s += (double)cd.paa[((size_t)g * cd.M + m) * P * P + e];
+    s += sum_partials(cd.paa + (size_t)m * P * P + e, (size_t)cd.M * P * P, Pg, nullptr, 0);
     saat[e] = s;
     if (lc == 0) cd.AAt[(size_t)m * P * P + e] = s;
   }
@@ -91,7 +110,7 @@ __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
   for (int e = tid; e < nl * P; e += kThreads) {
     const int l = l0 + e / P, j = e - (e / P) * P;
     double s = aref * cd.sx[l];  // shifted accumulation: add back (1/p) sum_i x_i
-    for (int g = 0; g < Pg; ++g) s += (double)cd.part[((size_t)g * (L + 1) + l) * Mp + m * P + j];
+    s += sum_partials(cd.part + (size_t)l * Mp + m * P + j, (size_t)(L + 1) * Mp, Pg, nullptr, 0);
     cd.XAt[(size_t)l * Mp + m * P + j] = s;
     sx[e] = s;
   }
@@ -150,13 +169,21 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool
   for (int e = tid; e < nl * P; e += kThreads) {
     const int l = l0 + e / P, j = e - (e / P) * P;
     double s = sW[j] * cd.sx[l];
-    for (int g = 0; g < Pg; ++g) s += sscale[g * P + j] * (double)cd.part[((size_t)g * (L + 1) + l) * Mp + m * P + j];
+    s += sum_partials(cd.part + (size_t)l * Mp + m * P + j, (size_t)(L + 1) * Mp, Pg, sscale + j, P);
     cd.Ed[(size_t)l * Mp + m * P + j] = s;
     cd.Ef[(size_t)l * Mp + m * P + j] = (float)s;
     if (cd.tc) store_panel(cd, cd.panelE, m * P + j, l, s);
     sE[e] = s;
   }
   __syncthreads();
+  // G = E^T E of run m over this chunk's bands, bands in order (the tensor-core
+  // A-pass sums the chunks; the CUDA-core A-pass forms G from its staged panel)
+  for (int e = tid; e < P * P; e += kThreads) {
+    const int j = e / P, k = e - j * P;
+    double g = 0.0;
+    for (int li = 0; li < nl; ++li) g += sE[li * P + j] * sE[li * P + k];
+    cd.gpart[((size_t)lc * cd.M + m) * P * P + e] = g;
+  }
   for (int e = tid; e < nl * P; e += kThreads) {
     const int li = e / P, l = l0 + li, j = e - li * P;
     double r = -cd.XAt[(size_t)l * Mp + m * P + j];
@@ -501,7 +528,7 @@ __global__ void k_grad(const CubeDev* __restrict__ cdp, int m, float* gA, float*
   float a[kMaxP], ga[kMaxP], gb[kMaxP];
   float se = 0.f;
   for (int j = 0; j < P; ++j) {
-    a[j] = expf(cd.logA[(size_t)i * Mp + m * P + j]);
+    a[j] = expf(cd.logA[(size_t)(m * P + j) * cd.Nst + i]);
     se += a[j];
     ga[j] = 0.f;
     gb[j] = 0.f;
@@ -535,15 +562,15 @@ __global__ void k_gather_e(const double* Ed, const double* xbar, int L, int Mp, 
   const int l = e / p, j = e % p;
   E[e] = (float)(Ed[(size_t)l * Mp + m * p + j] + xbar[l]);
 }
-__global__ void k_gather_ab(const float* logA, const float* logB, const float* lse, int N, int Mp, int p, int m,
+__global__ void k_gather_ab(const float* logA, const float* logB, const float* lse, int N, int Nst, int p, int m,
                             float* A, float* B) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * p) return;
   const int i = e / p, j = e % p;
-  const size_t src = (size_t)i * Mp + m * p + j;
+  const size_t src = (size_t)(m * p + j) * Nst + i;
   if (A) {  // softmax over the p max-normalised log abundances of pixel i
     double se = 0.0;
-    for (int k = 0; k < p; ++k) se += exp((double)logA[(size_t)i * Mp + m * p + k]);
+    for (int k = 0; k < p; ++k) se += exp((double)logA[(size_t)(m * p + k) * Nst + i]);
     A[(size_t)j * N + i] = (float)(exp((double)logA[src]) / se);
   }
   if (B) B[e] = (float)exp((double)logB[src] - (double)lse[m * p + j] - log((double)N));
@@ -551,7 +578,7 @@ __global__ void k_gather_ab(const float* logA, const float* logB, const float* l
 
 cudaError_t launch_gather(const CubeDev& hc, int run, float* E, float* A, float* B, cudaStream_t s) {
   if (E) k_gather_e<<<(hc.L * hc.p + 255) / 256, 256, 0, s>>>(hc.Ed, hc.xbar, hc.L, hc.Mp, hc.p, run, E);
-  if (A || B) k_gather_ab<<<(hc.N * hc.p + 255) / 256, 256, 0, s>>>(hc.logA, hc.logB, hc.lse, hc.N, hc.Mp, hc.p, run, A, B);
+  if (A || B) k_gather_ab<<<(hc.N * hc.p + 255) / 256, 256, 0, s>>>(hc.logA, hc.logB, hc.lse, hc.N, hc.Nst, hc.p, run, A, B);
   return cudaGetLastError();
 }
 

@@ -275,8 +275,8 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
     }
     if (!init) {
       for (int e = tid; e < ni * nc; e += kThreads) {
-        const int i = e / nc, cc = e - i * nc;
-        Ss[i * RgSo + cc] = St[(size_t)(i0 + i) * Mp + c0 + cc];
+        const int cc = e / ni, i = e - cc * ni;
+        Ss[i * RgSo + cc] = St[(size_t)(c0 + cc) * cd.Nst + i0 + i];
       }
     }
     __syncthreads();
@@ -471,10 +471,10 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
       __syncthreads();
     }
 
-    // ---- write the new state back (coalesced rows)
+    // ---- write the new state back (coalesced along pixels)
     for (int e = tid; e < ni * nc; e += kThreads) {
-      const int i = e / nc, cc = e - i * nc;
-      St[(size_t)(i0 + i) * Mp + c0 + cc] = Ss[i * RgSo + cc];
+      const int cc = e / ni, i = e - cc * ni;
+      St[(size_t)(c0 + cc) * cd.Nst + i0 + i] = Ss[i * RgSo + cc];
     }
 
     // ---- phase 2: acc[l][c] += sum_i X[i][l] W[i][c]  (l = 0..L, row L = ones band)
@@ -657,8 +657,8 @@ __device__ __noinline__ void fit_item(const CubeDev& cd, int rg, int pg, float* 
         for (int e = tid; e < nt4; e += kThreads) xs4[e] = (e < n4) ? __ldg(Xg + e) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       for (int e = tid; e < ni * nc; e += kThreads) {
-        const int i = e / nc, cc = e - i * nc;
-        Ss[i * RgSo + cc] = cd.logA[(size_t)(i0 + i) * Mp + c0 + cc];
+        const int cc = e / ni, i = e - cc * ni;
+        Ss[i * RgSo + cc] = cd.logA[(size_t)(c0 + cc) * cd.Nst + i0 + i];
       }
       __syncthreads();
 #pragma unroll
@@ -735,8 +735,8 @@ __device__ __noinline__ void fit_item(const CubeDev& cd, int rg, int pg, float* 
 }
 
 template <int P, bool IS_A, bool BF>
-__device__ void tc_pass_item(const Batch* __restrict__ bt, const CubeDev& cd, int rg, int pg, unsigned char* smem_raw,
-                             int K1, bool init);
+__device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const CubeDev& cd, int rg, int pg,
+                                          unsigned char* smem_raw, int K1, bool init);
 
 template <int P>
 __device__ __forceinline__ void pass_dispatch_impl(const Batch* bt, const CubeDev& cd, int rg, int pg, float* smem,

@@ -109,6 +109,34 @@ __device__ __forceinline__ void tmem_st8(uint32_t ta, const float (&v)[8]) {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+// the same load without the wait: several loads are issued, then one tmem_wait_ld()
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t ta, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(ta));
+}
+// waits for the thread's outstanding TMEM loads; r is tied to the wait so its uses stay after it
+__device__ __forceinline__ void tmem_wait_ld8(uint32_t (&r)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+               :
+               : "memory");
+}
+
+// Hardware base-2 exponential and reciprocal (relative error near 2^-22).
+// The tensor-core passes use them: their results feed TF32/BF16 operands
+// (2^-11 / 2^-9), so the approximation stays far below the operand rounding.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // element (row, k) of a K-major 128-byte-swizzled tile with 128-byte rows
 __device__ __forceinline__ uint32_t sw128_off(int row, int kbyte) {
   return (uint32_t)(row * 128 + (kbyte ^ ((row & 7) << 4)));

@@ -8,12 +8,12 @@ namespace edaa {
 template <int P, bool IS_A, bool BF>
 __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const CubeDev& cd, int rg, int pg,
                                           unsigned char* smem_raw, int K1, bool init) {
-  constexpr int P4 = (P + 3) & ~3;
   constexpr int PP = P * (P + 1) / 2;
   constexpr int ESZ = BF ? 2 : 4;
   constexpr int KCH = 128 / ESZ;   // elements per 128-byte row (32 tf32, 64 bf16)
   constexpr int NPC = 128 / KCH;   // pixel chunks per 128-pixel tile
   constexpr uint32_t FMT = BF ? 1u : 2u;
+  constexpr int kRB = 4;           // runs whose state is loaded together in the B epilogue
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int quarter = warp & 3, half = warp >> 2;
   const int L = cd.L, N = cd.N, Mp = cd.Mp, Rm = cd.Rm;
@@ -40,7 +40,8 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   float* colLse = colScale + 256;                          // Rgp
   float* runEta = colLse + 256;                            // Rm (<= 128)
   int* colRef = reinterpret_cast<int*>(runEta + 128);      // Rgp: reference exponent k (B)
-  float* Gs = reinterpret_cast<float*>(colRef + 256);      // Rm x P x P (A), <= 2048
+  float* colRefW = reinterpret_cast<float*>(colRef + 256);  // Rgp: 2^(k - Mn), the reference weight (B)
+  float* Gs = colRefW + 256;                               // Rm x P x P (A), <= 2048
   float* aaq = Gs + 2048;                                  // 4 x Rm x PP (A)
 
   // ---- set-up: barriers, TMEM (512 columns: one CTA per SM), per-run constants
@@ -64,6 +65,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     colKey[c] = ord_key(-EDAA_INF);
     colScale[c] = 1.f;
     colLse[c] = 0.f;
+    colRefW[c] = 0.f;
   }
   if (!IS_A)
     for (int c = tid; c < 256; c += kThreads) {
@@ -78,12 +80,11 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   if (IS_A) {
     for (int e = tid; e < 4 * Rm * PP; e += kThreads) aaq[e] = 0.f;
     if (!init && K1 > 0) {
-      for (int e = tid; e < nr * P * P; e += kThreads) {  // G = E^T E per run, FP32 from the float panel
-        const int r = e / (P * P), jk = e - r * P * P, j = jk / P, k = jk - j * P;
-        float s = 0.f;
-        for (int l = 0; l < L; ++l)
-          s = fmaf(cd.Ef[(size_t)l * Mp + c0 + r * P + j], cd.Ef[(size_t)l * Mp + c0 + r * P + k], s);
-        Gs[e] = s;
+      for (int e = tid; e < nr * P * P; e += kThreads) {  // G = E^T E per run from the merge's band-chunk sums
+        const int r = e / (P * P), jk = e - r * P * P;
+        double s = 0.0;
+        for (int lc = 0; lc < cd.nlchunk; ++lc) s += cd.gpart[((size_t)lc * cd.M + m0 + r) * P * P + jk];
+        Gs[e] = (float)s;
       }
     }
   }
@@ -95,62 +96,77 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   const uint32_t tbase = *tmem_slot;
   const uint32_t id = tc_idesc(128, Rgp, FMT);
   const bool do_c1 = !init;
-  uint32_t it = 0;        // TMA/MMA chunk counter (thread 0): stage = it % S, phase = (it / S) & 1
+
+  // ---- the chunk stream (thread 0).  Per tile: contraction 1 (nkc chunks of X
+  // and the panel; not in the initial passes), then contraction 2 (nbt * NPC
+  // chunks of the band-major X).  Chunk k uses ring stage k % kTcStages.  Loads
+  // run up to kTcStages chunks ahead of the MMAs, so contraction 2's X streams
+  // in during the epilogue and the next tile's contraction 1 during
+  // contraction 2.
+  const int nc2 = nbt * NPC;
+  const int per_tile = (do_c1 ? nkc : 0) + nc2;
+  const int ntl = pg < cd.ntiles ? (cd.ntiles - pg + cd.Pg - 1) / cd.Pg : 0;
+  const uint32_t total = (uint32_t)(ntl * per_tile);
+  uint32_t loaded = 0, issued = 0;
+  auto load_chunk = [&](uint32_t k) -> bool {
+    const uint32_t s = k % kTcStages;
+    if (k >= kTcStages && !mbar_wait(empty + s, ((k / kTcStages) + 1) & 1, tmo)) return false;
+    const int q = (int)(k / (uint32_t)per_tile), j = (int)(k - (uint32_t)(q * per_tile));
+    const int ti0 = (pg + q * cd.Pg) * kTcTile;
+    unsigned char* dst = sm + s * S.stage_bytes;
+    if (do_c1 && j < nkc) {
+      mbar_expect(full + s, 128u * 128u + (uint32_t)Rgp * 128u);
+      tma2d(dst, tmX, j * KCH, ti0, full + s);
+      tma2d(dst + 128 * 128, tmPan, j * KCH, c0, full + s);
+    } else {
+      const int jj = j - (do_c1 ? nkc : 0), bti = jj / NPC, pc = jj - bti * NPC;
+      mbar_expect(full + s, 128u * 128u);
+      tma2d(dst, tmXT, ti0 + pc * KCH, bti * 128, full + s);
+    }
+    return true;
+  };
+  auto fill = [&]() -> bool {
+    while (loaded < total && loaded < issued + kTcStages) {
+      if (!load_chunk(loaded)) return false;
+      ++loaded;
+    }
+    return true;
+  };
+  // MMAs of the next chunk; its stage is released by the MMAs' commit
+  auto consume = [&](auto&& mma) -> bool {
+    const uint32_t k = issued, s = k % kTcStages;
+    if (!mbar_wait(full + s, (k / kTcStages) & 1, tmo)) return false;
+    tc_fence_after();
+    mma(sm + s * S.stage_bytes);
+    tc_commit(empty + s);
+    ++issued;
+    return fill();
+  };
+  if (tid == 0 && !fill()) flags[0] = 1;
+
   uint32_t c1_phase = 0, c2_phase = 0;
   bool c2_pending = false, d2_started = false;
   int bail = 0;
-
-  // thread 0: stream `n` chunks through the ring; load(j, dst, bar) issues the TMA(s)
-  // of chunk j, mma(j, stage_base) issues its MMAs.
-  auto pipeline = [&](int n, uint32_t bytes, auto&& load, auto&& mma) -> bool {
-    const uint32_t base_it = it;
-    for (int j = 0; j < n && j < kTcStages; ++j) {
-      const uint32_t k = base_it + j, s = k % kTcStages;
-      if (k >= kTcStages && !mbar_wait(empty + s, ((k / kTcStages) + 1) & 1, tmo)) return false;
-      mbar_expect(full + s, bytes);
-      load(j, sm + s * S.stage_bytes, full + s);
-    }
-    for (int j = 0; j < n; ++j) {
-      const uint32_t k = base_it + j, s = k % kTcStages;
-      if (!mbar_wait(full + s, (k / kTcStages) & 1, tmo)) return false;
-      tc_fence_after();
-      mma(j, sm + s * S.stage_bytes);
-      tc_commit(empty + s);
-      if (j + kTcStages < n) {
-        const uint32_t k2 = k + kTcStages;
-        if (!mbar_wait(empty + s, ((k2 / kTcStages) + 1) & 1, tmo)) return false;
-        mbar_expect(full + s, bytes);
-        load(j + kTcStages, sm + s * S.stage_bytes, full + s);
-      }
-    }
-    it = base_it + n;
-    return true;
-  };
-
   float* St = IS_A ? cd.logA : cd.logB;
   const float aref = 1.f / (float)P;
+  const uint32_t tl = (uint32_t)(quarter * 32) << 16;  // this warp's TMEM lane block
 
-  for (int tile = pg; tile < cd.ntiles; tile += cd.Pg) {
-    const int i0 = tile * kTcTile;
+  for (int q = 0; q < ntl; ++q) {
+    const int i0 = (pg + q * cd.Pg) * kTcTile;
     const int ni = min(kTcTile, N - i0);
     // ---- 1. C = X_tile Panel^T (skipped for the initial passes: c = 0)
     if (do_c1) {
-      if (tid == 0) {
-        const uint32_t bytes = 128u * 128u + (uint32_t)Rgp * 128u;
-        const bool ok = pipeline(
-            nkc, bytes,
-            [&](int j, unsigned char* dst, uint64_t* b) {
-              tma2d(dst, tmX, j * KCH, i0, b);
-              tma2d(dst + 128 * 128, tmPan, j * KCH, c0, b);
-            },
-            [&](int j, unsigned char* st) {
+      if (tid == 0 && !flags[0]) {
+        bool ok = true;
+        for (int j = 0; j < nkc && ok; ++j)
+          ok = consume([&](unsigned char* st) {
 #pragma unroll
-              for (int ks = 0; ks < 4; ++ks) {
-                const uint64_t da = desc_sw128(su32(st + ks * 32));
-                const uint64_t db = desc_sw128(su32(st + 128 * 128 + ks * 32));
-                tc_mma<BF>(tbase, da, db, id, (j | ks) ? 1u : 0u);
-              }
-            });
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint64_t da = desc_sw128(su32(st + ks * 32));
+              const uint64_t db = desc_sw128(su32(st + 128 * 128 + ks * 32));
+              tc_mma<BF>(tbase, da, db, id, (j | ks) ? 1u : 0u);
+            }
+          });
         if (ok) tc_commit(bar_c1);
         else flags[0] = 1;
       }
@@ -179,26 +195,52 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     // ---- 2. epilogue: warp (quarter, half) = pixels 32*quarter.., runs of parity `half`
     const int il = quarter * 32 + lane;
     const bool valid = il < ni;
-    const size_t grow = (size_t)(i0 + il) * Mp + c0;
+    const size_t Nst = (size_t)cd.Nst;
+    const size_t gpix = (size_t)c0 * Nst + i0 + il;  // state of column c of this pixel: gpix + c * Nst
+    const bool ld_state = !init && valid;
+    unsigned char* wl = Wsm + (il / KCH) * wchunk;   // this pixel's 128-byte K chunk of W
+    const int kb = (il % KCH) * ESZ;
+    auto store_w = [&](int c, float w) {
+      unsigned char* dst = wl + c * 128 + (kb ^ ((c & 7) << 4));
+      if (BF) *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(w);
+      else *reinterpret_cast<float*>(dst) = to_tf32(w);
+    };
     if (IS_A) {
+      // eq. (update_A), K1 steps in base 2 (y = z log2 e); the state and the
+      // TMEM row of the next run of this warp are loaded one run ahead
+      float zn[P];
+      uint32_t cn[8];
+#pragma unroll
+      for (int j = 0; j < P; ++j) zn[j] = (ld_state && half < nr) ? St[gpix + (half * P + j) * Nst] : 0.f;
+      if (do_c1 && half < nr) tmem_ld8_issue(tbase + tl + (uint32_t)(half * P), cn);
       for (int r = half; r < nr; r += 2) {
-        float cv[8];
+        float cv[P], y[P];
+        if (do_c1) {
+          tmem_wait_ld8(cn);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) cv[j] = 0.f;
-        if (do_c1) tmem_ld8(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * P), cv);
-        float z[P];
+          for (int j = 0; j < P; ++j) cv[j] = __uint_as_float(cn[j]);
+        } else {
 #pragma unroll
-        for (int j = 0; j < P; ++j) z[j] = (init || !valid) ? 0.f : St[grow + r * P + j];
+          for (int j = 0; j < P; ++j) cv[j] = 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < P; ++j) y[j] = zn[j] * kLog2e;
+        if (r + 2 < nr) {
+#pragma unroll
+          for (int j = 0; j < P; ++j) zn[j] = ld_state ? St[gpix + ((r + 2) * P + j) * Nst] : 0.f;
+          if (do_c1) tmem_ld8_issue(tbase + tl + (uint32_t)((r + 2) * P), cn);
+        }
         const float* G = Gs + r * P * P;
-        const float eta = runEta[r];
+        const float e2 = runEta[r] * kLog2e;
         float ea[P], se = 0.f;
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-          ea[j] = expf(z[j]);
+          ea[j] = ex2_approx(y[j]);
           se += ea[j];
         }
         for (int kk = 0; kk < K1; ++kk) {
-          const float inv = 1.f / se;
+          // a+ = softmax(log a - eta (G a - c)), G = E^T E, c = E^T x
+          const float inv = rcp_approx(se);
           float a[P], mx = -EDAA_INF;
 #pragma unroll
           for (int j = 0; j < P; ++j) a[j] = ea[j] * inv;
@@ -207,67 +249,77 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
             float g = -cv[j];
 #pragma unroll
             for (int k = 0; k < P; ++k) g = fmaf(G[j * P + k], a[k], g);
-            z[j] = fmaf(-eta, g, z[j]);
-            mx = fmaxf(mx, z[j]);
+            y[j] = fmaf(-e2, g, y[j]);
+            mx = fmaxf(mx, y[j]);
           }
           se = 0.f;
 #pragma unroll
           for (int j = 0; j < P; ++j) {
-            z[j] -= mx;
-            ea[j] = expf(z[j]);
+            y[j] -= mx;
+            ea[j] = ex2_approx(y[j]);
             se += ea[j];
           }
         }
-        float d[P], sd = 0.f;
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-          d[j] = expm1f(z[j]);
-          sd += d[j];
-        }
-        const float den = 1.f / ((float)P + sd);
+        const float inv = rcp_approx(se);
         float a[P];
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-          a[j] = valid ? (1.f + d[j]) * den : 0.f;
-          const float wdev = valid ? ((float)P * d[j] - sd) * den * aref : 0.f;
-          if (valid) St[grow + r * P + j] = z[j];
-          const int c = r * P + j, pc = il / KCH, kb = (il % KCH) * ESZ;
-          unsigned char* dst = Wsm + pc * wchunk + sw128_off(c, kb);
-          if (BF) *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(wdev);
-          else *reinterpret_cast<float*>(dst) = to_tf32(wdev);
+          a[j] = valid ? ea[j] * inv : 0.f;
+          if (valid) St[gpix + (r * P + j) * Nst] = y[j] * kLn2;
+          store_w(r * P + j, valid ? a[j] - aref : 0.f);  // shifted accumulation: a - 1/p
         }
-        // A A^T of this tile's pixels: lanes -> warp sum -> this quarter's slot
+        // A A^T of this tile's pixels: products in 2^-24 fixed point, summed
+        // exactly over the warp's 32 pixels (integer warp reduction)
         int e = 0;
 #pragma unroll
         for (int j = 0; j < P; ++j)
 #pragma unroll
           for (int k = j; k < P; ++k) {
-            const float v = warp_sum(a[j] * a[k]);
-            if (lane == 0) aaq[(quarter * Rm + r) * PP + e] += v;
+            const int v = __reduce_add_sync(0xffffffffu, __float2int_rn(a[j] * a[k] * 16777216.f));
+            if (lane == 0) aaq[(quarter * Rm + r) * PP + e] += (float)v * (1.f / 16777216.f);
             ++e;
           }
       }
     } else {
-      // B: u' = u - lse - eta2 g (initial pass: u = 0.1 * SplitMix64 uniform)
-      for (int r = half; r < nr; r += 2) {
-        float gv[8];
+      // eq. (update_B): u' = u - lse - eta2 g (initial pass: u = 0.1 * SplitMix64
+      // uniform).  The old logits and TMEM rows of kRB runs are loaded together.
+      for (int r0 = half; r0 < nr; r0 += 2 * kRB) {
+        float uo[kRB][P];
+        uint32_t gr[kRB][8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) gv[j] = 0.f;
-        if (do_c1) tmem_ld8(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * P), gv);
+        for (int b = 0; b < kRB; ++b)
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-          float u = -EDAA_INF;
-          if (valid) {
-            if (init) u = 0.1f * uniform24(cd.seeds[m0 + r], (uint64_t)(i0 + il) * P + j + 1);
-            else u = St[grow + r * P + j] - colLse[r * P + j] - runEta[r] * gv[j];
-            St[grow + r * P + j] = u;  // the new logits (read back below for the weights)
+          for (int j = 0; j < P; ++j)
+            uo[b][j] = (ld_state && r0 + 2 * b < nr) ? St[gpix + ((r0 + 2 * b) * P + j) * Nst] : 0.f;
+        if (do_c1) {
+#pragma unroll
+          for (int b = 0; b < kRB; ++b)
+            if (r0 + 2 * b < nr) tmem_ld8_issue(tbase + tl + (uint32_t)((r0 + 2 * b) * P), gr[b]);
+#pragma unroll
+          for (int b = 0; b < kRB; ++b)
+            if (r0 + 2 * b < nr) tmem_wait_ld8(gr[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < kRB; ++b) {
+          const int r = r0 + 2 * b;
+          if (r >= nr) break;
+          const float eta = runEta[r];
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            const int c = r * P + j;
+            float u = -EDAA_INF;
+            if (valid) {
+              if (init) u = 0.1f * uniform24(cd.seeds[m0 + r], (uint64_t)(i0 + il) * P + j + 1);
+              else u = uo[b][j] - colLse[c] - eta * (do_c1 ? __uint_as_float(gr[b][j]) : 0.f);
+              St[gpix + c * Nst] = u;  // the new logits (read back below for the weights)
+            }
+            const int key = __reduce_max_sync(0xffffffffu, ord_key(u));
+            if (lane == 0) atomicMax(&colKey[c], key);
           }
-          const float m = warp_max(u);
-          if (lane == 0) atomicMax(&colKey[r * P + j], ord_key(m));
         }
       }
       __syncthreads();
-      // new running exponents; rescale factors for the accumulators
+      // new running exponents, rescale factors for the accumulators, reference weights
       for (int c = tid; c < nc; c += kThreads) {
         const float Mo = colM[c];
         const float Mn = fmaxf(Mo, tile_exp(colKey[c]));
@@ -275,32 +327,36 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
         if (Mo != Mn && Mo != -EDAA_INF) flags[1] = 1;
         colM[c] = Mn;
         colKey[c] = ord_key(-EDAA_INF);
+        colRefW[c] = ldexpf(1.f, colRef[c] - (int)Mn);
       }
       __syncthreads();
       if (flags[1] && d2_started) {  // exact power-of-two rescale of Acc in TMEM, disjoint 8-column chunks
         for (int b = 0; b < nbt; ++b)
           for (int cc = half * 8; cc < Rgp; cc += 16) {
             float v[8];
-            const uint32_t ta = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(Rgp * (1 + b) + cc);
+            const uint32_t ta = tbase + tl + (uint32_t)(Rgp * (1 + b) + cc);
             tmem_ld8(ta, v);
 #pragma unroll
             for (int j = 0; j < 8; ++j) v[j] *= colScale[cc + j];
             tmem_st8(ta, v);
           }
       }
-      for (int r = half; r < nr; r += 2) {
+      // shifted weights e^u 2^-Mn - 2^(k-Mn) (the reference is added back in the merge)
+      for (int r0 = half; r0 < nr; r0 += 2 * kRB) {
+        float un[kRB][P];
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-          const int c = r * P + j;
-          float w = 0.f;
-          if (valid) {
-            const float u = St[grow + c];
-            w = shifted_weight(u, colM[c], colRef[c]);
+        for (int b = 0; b < kRB; ++b)
+#pragma unroll
+          for (int j = 0; j < P; ++j) un[b][j] = (valid && r0 + 2 * b < nr) ? St[gpix + ((r0 + 2 * b) * P + j) * Nst] : 0.f;
+#pragma unroll
+        for (int b = 0; b < kRB; ++b) {
+          const int r = r0 + 2 * b;
+          if (r >= nr) break;
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            const int c = r * P + j;
+            store_w(c, valid ? ex2_approx(fmaf(un[b][j], kLog2e, -colM[c])) - colRefW[c] : 0.f);
           }
-          const int pc = il / KCH, kb = (il % KCH) * ESZ;
-          unsigned char* dst = Wsm + pc * wchunk + sw128_off(c, kb);
-          if (BF) *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(w);
-          else *reinterpret_cast<float*>(dst) = to_tf32(w);
         }
       }
     }
@@ -311,15 +367,12 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     if (tid == 0) {
       flags[1] = 0;
       tc_fence_after();
-      const bool first = !d2_started;
-      const bool ok = pipeline(
-          nbt * NPC, 128u * 128u,
-          [&](int j, unsigned char* dst, uint64_t* b) {
-            const int bti = j / NPC, pc = j - bti * NPC;
-            tma2d(dst, tmXT, i0 + pc * KCH, bti * 128, b);
-          },
-          [&](int j, unsigned char* st) {
-            const int bti = j / NPC, pc = j - bti * NPC;
+      if (!flags[0]) {
+        const bool first = !d2_started;
+        bool ok = true;
+        for (int j = 0; j < nc2 && ok; ++j) {
+          const int bti = j / NPC, pc = j - bti * NPC;
+          ok = consume([&](unsigned char* st) {
             const uint32_t dcol = tbase + (uint32_t)(Rgp * (1 + bti));
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
@@ -328,10 +381,12 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
               tc_mma<BF>(dcol, da, db, id, (first && pc == 0 && ks == 0) ? 0u : 1u);
             }
           });
-      if (ok) tc_commit(bar_c2);
-      else {
-        flags[0] = 1;
-        atomicOr(bt->status, 1 << 12);  // contraction-2 pipeline
+        }
+        if (ok) tc_commit(bar_c2);
+        else {
+          flags[0] = 1;
+          atomicOr(bt->status, 1 << 12);  // contraction-2 pipeline
+        }
       }
     }
     if (__syncthreads_or(flags[0])) {
@@ -362,7 +417,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
       const int l = b * 128 + quarter * 32 + lane;
       for (int r = half; r < nr; r += 2) {
         float v[8];
-        tmem_ld8(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(Rgp * (1 + b) + r * P), v);
+        tmem_ld8(tbase + tl + (uint32_t)(Rgp * (1 + b) + r * P), v);
         if (l <= L) {
 #pragma unroll
           for (int j = 0; j < P; ++j) part[(size_t)l * Mp + c0 + r * P + j] = v[j];
