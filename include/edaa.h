@@ -68,6 +68,9 @@ typedef struct {
                          softmax axis), and centring avoids the cancellation in
                          E A A^T - X A^T; outputs and reported gradients are in
                          the paper's uncentred terms either way.                   */
+  int trace;          /* 1: record when each phase of a launch sequence starts and
+                         ends (GPU global timer; read with edaa_trace_read).  0
+                         (default): no recording.                                   */
 } edaa_config;
 
 typedef struct {
@@ -137,6 +140,20 @@ edaa_status edaa_loss(edaa_ctx* ctx, int cube, double* loss);
 
 /* Step sizes in use for cube `cube` (host arrays of length M; NULL skips). */
 edaa_status edaa_step_sizes(edaa_ctx* ctx, int cube, double* eta1, double* eta2);
+
+/* Phase trace (needs config.trace = 1).  For the last launch sequence of
+ * kind `which` (0: the outer iterations of the last edaa_step / edaa_solve,
+ * 1: initialisation, 2: the fit and coherence phases of edaa_solve), writes up
+ * to `cap` entries: phase[i] (0 A-pass, 1 A-merge, 2 B-pass, 3 B-merge,
+ * 4 initial B-pass, 5 initial A-pass, 6 step sizes, 7 fit pass, 8 fit merge,
+ * 9 first B-merge), start_us[i] (when the first block began it, relative to
+ * the sequence's first phase) and dur_us[i] (until the last block finished
+ * it), from the GPU's global timer; *n receives the number of phases
+ * recorded (at most 4096 per sequence).  Host arrays; synchronises the
+ * context's stream.  A persistent launch includes the grid-barrier wait in
+ * each phase's time.  EDAA_ERR_STATE when tracing is off. */
+edaa_status edaa_trace_read(edaa_ctx* ctx, int which, int cap, int* n, int* phase, double* start_us,
+                            double* dur_us);
 
 /* Synchronises the context's stream and reports the device status word. */
 edaa_status edaa_sync(edaa_ctx* ctx);

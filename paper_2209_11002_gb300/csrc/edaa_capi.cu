@@ -149,6 +149,8 @@ struct edaa_ctx {
   Batch* d_batch = nullptr;
   int* d_status = nullptr;
   unsigned* d_bar = nullptr;
+  unsigned long long* d_trace = nullptr;  // phase trace: 3 x kTraceCap starts, then 3 x kTraceCap ends
+  int trace_n[3] = {0, 0, 0};             // phases of the last sequence of each mode
   size_t smem = 0;
   int grid = 0;
   int outer_done = 0;
@@ -197,13 +199,13 @@ static void plan(edaa_ctx* c) {
     const int per = (h.ntiles + h.Pg - 1) / h.Pg;
     h.Pg = (h.ntiles + per - 1) / per;
     // merge chunks: aim for about G units in total
-    const int want = std::max(1, (int)ceil((double)G * h.M / std::max(1, units_total) / h.M));
-    int lch = std::max(1, (h.L + want - 1) / want);
-    lch = std::min(lch, 256 / h.p);
+    // merge units (run x band chunk): one wave over the grid where possible
+    const int want = std::max(1, G / std::max(1, units_total));
+    const int lch = std::max(1, (h.L + want - 1) / want);
     h.lchunk = lch;
     h.nlchunk = (h.L + lch - 1) / lch;
     // the B-merge keeps Pg x p scale factors in shared memory
-    const int pg_fit = (int)((c->smem / 8 - 16 - (size_t)2 * kMaxP - (size_t)2 * lch * h.p) / h.p);
+    const int pg_fit = (int)(((long long)(c->smem / 8) - merge_smem(lch, h.p, 0).total) / h.p);
     if (h.Pg > pg_fit) h.Pg = std::max(1, pg_fit);
     CubeDev& d = h.dev;
     d.L = h.L; d.Ls = h.Ls; d.Lr = h.Lr; d.N = h.N; d.p = h.p; d.M = h.M; d.Mp = h.Mp;
@@ -241,9 +243,7 @@ static size_t pass_item_smem(const CubeHost& h) {
 
 static size_t cube_smem(const CubeHost& h) {
   size_t s = pass_item_smem(h);
-  const size_t mb = (size_t)(2 * kMaxP + 2 * h.lchunk * h.p + h.Pg * h.p) * 8 + 64;
-  const size_t ma = (size_t)(64 + 2 * h.lchunk * h.p) * 8;
-  return std::max(s, std::max(ma, mb));
+  return std::max(s, (size_t)merge_smem(h.lchunk, h.p, h.Pg).total * 8);
 }
 
 // Partial buffers are sized for the largest pixel-group count a plan can use.
@@ -377,6 +377,12 @@ static edaa_status push_batch(edaa_ctx* c) {
 static edaa_status enqueue(edaa_ctx* c, int mode, int n_outer, int* launches) {
   const int nph = program_phase_count(mode, n_outer, c->cfg.K2);
   if (nph <= 0) return EDAA_OK;
+  if (c->d_trace) {
+    const size_t n = (size_t)std::min(nph, kTraceCap);
+    CK(cudaMemsetAsync(c->d_trace + (size_t)mode * kTraceCap, 0xFF, n * 8, c->stream), "reset trace");
+    CK(cudaMemsetAsync(c->d_trace + (size_t)(3 + mode) * kTraceCap, 0, n * 8, c->stream), "reset trace");
+    c->trace_n[mode] = (int)n;
+  }
   if (c->cfg.persistent && nph > 1) {
     CK(launch_program(c->d_batch, mode, n_outer, 0, nph, c->grid, c->smem, true, c->stream), "persistent launch");
     if (launches) *launches += 1;
@@ -482,6 +488,7 @@ void edaa_config_default(edaa_config* cfg) {
   cfg->autotune = 0;
   cfg->barrier_timeout_ms = 2000.0;
   cfg->center = 1;
+  cfg->trace = 0;
 }
 
 const char* edaa_last_error(void) { return g_err.c_str(); }
@@ -575,6 +582,7 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
   size_t smem = 0;
   for (auto& h : c->cubes) {
     smem = std::max(smem, pass_item_smem(h));
+    smem = std::max(smem, (size_t)merge_smem(h.L, h.p, 256).total * 8);  // any band chunk, up to 256 partials
     if (conf.autotune && !h.tc)
       for (const auto& t : tile_candidates(h.L, h.p, h.M)) smem = std::max(smem, tile_smem(t, h.L, h.p));
   }
@@ -614,6 +622,13 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
   c->d_bar = (unsigned*)(c->d_status + 4);
   c->hb.status = c->d_status;
   c->hb.bar = c->d_bar;
+  c->hb.trace_start = c->hb.trace_end = nullptr;
+  if (conf.trace) {
+    e = cudaMalloc(&c->d_trace, (size_t)6 * kTraceCap * 8);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    c->hb.trace_start = c->d_trace;
+    c->hb.trace_end = c->d_trace + 3 * kTraceCap;
+  }
   for (size_t i = 0; i < c->cubes.size(); ++i) {
     CubeHost& h = c->cubes[i];
     e = cudaMemcpyAsync((void*)h.dev.seeds, h.seeds.data(), h.M * 8, cudaMemcpyHostToDevice, c->stream);
@@ -824,6 +839,28 @@ edaa_status edaa_describe(const edaa_ctx* c, int cube, int* runs_per_group, int*
   return EDAA_OK;
 }
 
+edaa_status edaa_trace_read(edaa_ctx* c, int which, int cap, int* n, int* phase, double* start_us, double* dur_us) {
+  if (!c || !n) return fail(EDAA_ERR_ARG, "ctx or n is NULL");
+  if (which < 0 || which > 2) return fail(EDAA_ERR_ARG, "which must be 0, 1 or 2");
+  if (!c->d_trace) return fail(EDAA_ERR_STATE, "tracing is off (config.trace = 0)");
+  const int m = c->trace_n[which];
+  std::vector<unsigned long long> t0(std::max(m, 1)), t1(std::max(m, 1));
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  if (m > 0) {
+    CK(cudaMemcpy(t0.data(), c->d_trace + (size_t)which * kTraceCap, (size_t)m * 8, cudaMemcpyDeviceToHost), "read trace");
+    CK(cudaMemcpy(t1.data(), c->d_trace + (size_t)(3 + which) * kTraceCap, (size_t)m * 8, cudaMemcpyDeviceToHost),
+       "read trace");
+  }
+  const unsigned long long base = m > 0 ? t0[0] : 0;
+  for (int i = 0; i < m && i < cap; ++i) {
+    if (phase) phase[i] = program_phase_id(which, i, c->cfg.K2);
+    if (start_us) start_us[i] = ((double)t0[i] - (double)base) * 1e-3;
+    if (dur_us) dur_us[i] = ((double)t1[i] - (double)t0[i]) * 1e-3;
+  }
+  *n = m;
+  return EDAA_OK;
+}
+
 void edaa_destroy(edaa_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -832,6 +869,7 @@ void edaa_destroy(edaa_ctx* c) {
     if (h.arena) cudaFree(h.arena);
   if (c->d_batch) cudaFree(c->d_batch);
   if (c->d_status) cudaFree(c->d_status);
+  if (c->d_trace) cudaFree(c->d_trace);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

@@ -41,6 +41,7 @@ constexpr int kStatTimeout = 1;
 
 // kernel programs (sequences of phases)
 enum Mode { MODE_OUTER = 0, MODE_INIT = 1, MODE_FIT = 2 };
+constexpr int kTraceCap = 4096;  // traced phases per launch sequence
 enum Phase {
   PH_A = 0,      // A-pass: K1 fused A-steps per pixel, partials of X A^T, A A^T
   PH_AM = 1,     // merge A partials; R = E AAt - XAt
@@ -119,6 +120,9 @@ struct Batch {
   long long timeout_ns;
   int* status;
   unsigned int* bar;  // [0] arrivals, [1] generation
+  // phase trace (null when off): [mode][phase] first-start / last-end global-timer ns
+  unsigned long long* trace_start;
+  unsigned long long* trace_end;
   CubeDev c[kMaxCubes];
 };
 
@@ -153,6 +157,25 @@ __host__ __device__ inline PassSmem pass_smem(int L, int Ls, int Lr, int p, int 
 
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
+// Shared memory of a merge work item (one run, one chunk of lchunk bands), in doubles.
+struct MergeSmem {
+  int saat, sw, ssx, sxa, sE, sraw, sprod, sscale, total;
+};
+__host__ __device__ inline MergeSmem merge_smem(int lchunk, int p, int Pg) {
+  MergeSmem s;
+  int o = 0;
+  s.saat = o; o += 64;                // A A^T of the run
+  s.sw = o; o += 2 * kMaxP;           // B: frame, then reference weight and denominator per column
+  s.ssx = o; o += lchunk;             // centred band sums of the chunk
+  s.sxa = o; o += lchunk * p;         // X A^T of the chunk
+  s.sE = o; o += lchunk * p;          // E of the chunk
+  s.sraw = o; o += (lchunk + 1) * p;  // B: scaled partial sums (last row: the ones band)
+  s.sprod = o; o += lchunk * p;       // E R products
+  s.sscale = o; o += Pg * p;          // B: per-CTA scale factors
+  s.total = o;
+  return s;
+}
+
 inline int padded_ld(int L) {
   int ls = round_up(L + 1, 4);
   if (((ls >> 2) & 1) == 0) ls += 4;
@@ -172,6 +195,7 @@ cudaError_t launch_barrier_test(unsigned int* bar, int* status, int grid, int ex
 cudaError_t set_program_smem(size_t smem);
 cudaError_t program_occupancy(int* blocks_per_sm, size_t smem);
 int program_phase_count(int mode, int n_outer, int K2);
+int program_phase_id(int mode, int s, int K2);
 cudaError_t launch_tc_prepare(const CubeDev& hc, void* Xk, void* XT, int Npad, cudaStream_t s);
 
 }  // namespace edaa

@@ -74,105 +74,180 @@ __device__ void chunk_rho(const CubeDev& cd, int m, int lc, int nl, const double
   __syncthreads();
 }
 
-// Sum over the Pg per-CTA partials of one element (stride apart), each
-// scaled by scale[g * sstride] when scale is given.  Eight independent
-// chains keep eight loads in flight; they are combined in a fixed tree, so
-// the result does not depend on the launch mode.
-__device__ __forceinline__ double sum_partials(const float* __restrict__ v, size_t stride, int Pg,
-                                               const double* scale, int sstride) {
-  double c[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  int g = 0;
-  for (; g + 8 <= Pg; g += 8) {
-    float x[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = v[(size_t)(g + q) * stride];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) c[q] += (scale ? scale[(g + q) * sstride] : 1.0) * (double)x[q];
-  }
-  for (int q = 0; g < Pg; ++g, ++q) c[q] += (scale ? scale[g * sstride] : 1.0) * (double)v[(size_t)g * stride];
-  return ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+// Float-float accumulation (Knuth's TwoSum: s + e == hi + x exactly).  This
+// GPU's FP64 rate is a small fraction of its FP32 rate; two-float sums keep
+// about 44 bits at FP32 speed.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += e;
 }
 
+// Where element e's Pg per-CTA partials live: v[g * stride], each scaled by
+// sc[g * sstride] when sc is given (exact powers of two <= 1).
+struct PartialRow {
+  const float* v;
+  size_t stride;
+  const float* sc;
+  int sstride;
+};
+
+// Sums of the per-CTA partials of ne elements.  A team of lanes (a power of
+// two, as many as the block allows) shares one element: lane `sub` takes
+// g = sub, sub + team, ..., sixteen float-float chains per lane with their
+// loads in flight together, then a fixed tree over the chains and a fixed
+// butterfly over the team.  The team size and every order depend only on ne
+// and Pg, so the launch mode does not change the result.  store(e, sum)
+// receives each element's total once.
+template <typename Row, typename Store>
+__device__ void team_sums(int ne, int Pg, Row row, Store store) {
+  constexpr int W = 16;
+  int team = 32;
+  while (team > 1 && ne * team > kThreads) team >>= 1;
+  const int per = kThreads / team, sub = (int)threadIdx.x & (team - 1);
+  for (int e0 = 0; e0 < ne; e0 += per) {
+    const int e = e0 + (int)threadIdx.x / team;
+    float hi[W], lo[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) hi[q] = lo[q] = 0.f;
+    if (e < ne) {
+      const PartialRow r = row(e);
+      for (int g0 = sub; g0 < Pg; g0 += W * team) {
+        float x[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          const int g = g0 + q * team;
+          x[q] = g < Pg ? r.v[(size_t)g * r.stride] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          const int g = g0 + q * team;
+          if (g < Pg) ff_add(hi[q], lo[q], r.sc ? r.sc[g * r.sstride] * x[q] : x[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int w = W / 2; w >= 1; w >>= 1)
+#pragma unroll
+      for (int q = 0; q < w; ++q) {
+        ff_add(hi[q], lo[q], hi[q + w]);
+        lo[q] += lo[q + w];
+      }
+    for (int o = team / 2; o >= 1; o >>= 1) {  // every lane of the warp takes part
+      const float h2 = __shfl_xor_sync(0xffffffffu, hi[0], o);
+      const float l2 = __shfl_xor_sync(0xffffffffu, lo[0], o);
+      ff_add(hi[0], lo[0], h2);
+      lo[0] += l2;
+    }
+    if (e < ne && sub == 0) store(e, (double)hi[0] + (double)lo[0]);
+  }
+}
+
+// A-merge of run m over band chunk lc: X A^T = sum of the partials + (1/p) sum_i x_i
+// (shifted accumulation), A A^T, and R = E A A^T - X A^T for the next B-pass.
+// Every load that does not depend on another is issued in the first round.
 __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
   const int tid = threadIdx.x;
-  const int P = cd.p, L = cd.L, Mp = cd.Mp, Pg = cd.Pg;
-  double* saat = reinterpret_cast<double*>(smem);  // P*P
-  double* sx = saat + 64;                          // lchunk * P
-  double* sprod = sx + cd.lchunk * P;              // lchunk * P: E R products
-  for (int e = tid; e < P * P; e += kThreads) {
-    double s = 0.0;
-    s += sum_partials(cd.paa + (size_t)m * P * P + e, (size_t)cd.M * P * P, Pg, nullptr, 0);
-    saat[e] = s;
-    if (lc == 0) cd.AAt[(size_t)m * P * P + e] = s;
-  }
+  const int P = cd.p, L = cd.L, Mp = cd.Mp, Pg = cd.Pg, c0 = m * P;
+  const MergeSmem ms = merge_smem(cd.lchunk, P, Pg);
+  double* sd = reinterpret_cast<double*>(smem);
+  double *saat = sd + ms.saat, *ssx = sd + ms.ssx, *sxa = sd + ms.sxa, *sE = sd + ms.sE, *sprod = sd + ms.sprod;
   const int l0 = lc * cd.lchunk, nl = min(cd.lchunk, L - l0);
+  for (int e = tid; e < nl * P; e += kThreads) sE[e] = cd.Ed[(size_t)(l0 + e / P) * Mp + c0 + e % P];
+  for (int e = tid; e < nl; e += kThreads) ssx[e] = cd.sx[l0 + e];
+  team_sums(
+      P * P + nl * P, Pg,
+      [&](int e) {
+        if (e < P * P) return PartialRow{cd.paa + (size_t)m * P * P + e, (size_t)cd.M * P * P, nullptr, 0};
+        const int f = e - P * P, li = f / P, j = f - li * P;
+        return PartialRow{cd.part + (size_t)(l0 + li) * Mp + c0 + j, (size_t)(L + 1) * Mp, nullptr, 0};
+      },
+      [&](int e, double v) {
+        if (e < P * P) saat[e] = v;
+        else sxa[e - P * P] = v;
+      });
+  __syncthreads();
+  if (lc == 0)
+    for (int e = tid; e < P * P; e += kThreads) cd.AAt[(size_t)m * P * P + e] = saat[e];
   const double aref = (double)(1.f / (float)P);
   for (int e = tid; e < nl * P; e += kThreads) {
-    const int l = l0 + e / P, j = e - (e / P) * P;
-    double s = aref * cd.sx[l];  // shifted accumulation: add back (1/p) sum_i x_i
-    s += sum_partials(cd.part + (size_t)l * Mp + m * P + j, (size_t)(L + 1) * Mp, Pg, nullptr, 0);
-    cd.XAt[(size_t)l * Mp + m * P + j] = s;
-    sx[e] = s;
-  }
-  __syncthreads();
-  for (int e = tid; e < nl * P; e += kThreads) {
-    const int l = l0 + e / P, j = e - (e / P) * P;
-    double r = -sx[e];
-    for (int k = 0; k < P; ++k) r += cd.Ed[(size_t)l * Mp + m * P + k] * saat[k * P + j];
-    cd.Rf[(size_t)l * Mp + m * P + j] = (float)r;
-    if (cd.tc) store_panel(cd, cd.panelR, m * P + j, l, r);
-    sprod[e] = cd.Ed[(size_t)l * Mp + m * P + j] * r;
+    const int li = e / P, l = l0 + li, j = e - li * P;
+    const double xat = sxa[e] + aref * ssx[li];  // shifted accumulation: add back (1/p) sum_i x_i
+    cd.XAt[(size_t)l * Mp + c0 + j] = xat;
+    double r = -xat;
+    for (int k = 0; k < P; ++k) r += sE[li * P + k] * saat[k * P + j];
+    cd.Rf[(size_t)l * Mp + c0 + j] = (float)r;
+    if (cd.tc) store_panel(cd, cd.panelR, c0 + j, l, r);
+    sprod[e] = sE[e] * r;
   }
   __syncthreads();
   chunk_rho(cd, m, lc, nl, sprod);
 }
 
-__device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool init) {
+// B-merge of run m over band chunk lc: the online softmax over all pixels of
+// each column of B, merged across CTAs.  CTA g kept its weights as
+// e^u 2^-e_g; in the common frame mx = max_g e_g they scale by 2^(e_g - mx)
+// (exact).  The ones band (row L) gives the denominator S, so
+// E = X B = (sum_g 2^(e_g-mx) part_g + 2^(k-mx) sum_i x_i) / S, and the
+// stored lse is mx ln 2 + log S - log N (logits live in the frame log(N b)).
+// Then G = E^T E (chunk sums) and R = E A A^T - X A^T for the next pass.
+__device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int P = cd.p, L = cd.L, Mp = cd.Mp, Pg = cd.Pg;
-  double* sS = reinterpret_cast<double*>(smem);  // kMaxP: softmax denominators
-  double* sW = sS + kMaxP;                        // kMaxP: w_ref / S
-  double* sE = sW + kMaxP;                        // lchunk * P
-  double* sprod = sE + cd.lchunk * P;             // lchunk * P: E R products
-  double* sscale = sprod + cd.lchunk * P;         // Pg * P
-  (void)init;
-  const double logN = log((double)cd.N);
-  if (warp < P) {
-    // pmax holds each CTA's power-of-two exponent e_g: its weights are e^u 2^-e_g
-    const int j = warp, c = m * P + j;
+  const int P = cd.p, L = cd.L, Mp = cd.Mp, Pg = cd.Pg, c0 = m * P;
+  const MergeSmem ms = merge_smem(cd.lchunk, P, Pg);
+  double* sd = reinterpret_cast<double*>(smem);
+  double *saat = sd + ms.saat, *sw = sd + ms.sw, *ssx = sd + ms.ssx, *sxa = sd + ms.sxa, *sE = sd + ms.sE;
+  double *sraw = sd + ms.sraw, *sprod = sd + ms.sprod;
+  float* sscale = reinterpret_cast<float*>(sd + ms.sscale);  // Pg x P
+  const int l0 = lc * cd.lchunk, nl = min(cd.lchunk, L - l0);
+  // round 1: everything that does not depend on the partial sums
+  for (int e = tid; e < Pg * P; e += kThreads) sscale[e] = cd.pmax[(size_t)(e / P) * Mp + c0 + e % P];
+  for (int e = tid; e < nl * P; e += kThreads) sxa[e] = cd.XAt[(size_t)(l0 + e / P) * Mp + c0 + e % P];
+  for (int e = tid; e < nl; e += kThreads) ssx[e] = cd.sx[l0 + e];
+  for (int e = tid; e < P * P; e += kThreads) saat[e] = cd.AAt[(size_t)m * P * P + e];
+  __syncthreads();
+  if (warp < P) {  // the common frame of column j and the per-CTA scale factors
+    const int j = warp;
     float mx = -EDAA_INF;
-    for (int g = lane; g < Pg; g += 32) mx = fmaxf(mx, cd.pmax[(size_t)g * Mp + c]);
+    for (int g = lane; g < Pg; g += 32) mx = fmaxf(mx, sscale[g * P + j]);
     mx = warp_max(mx);
-    double S = 0.0;
     for (int g = lane; g < Pg; g += 32) {
-      const float eg = cd.pmax[(size_t)g * Mp + c];
-      const double f = (eg == -EDAA_INF) ? 0.0 : ldexp(1.0, (int)(eg - mx));  // exact
-      sscale[g * P + j] = f;
-      S += f * (double)cd.part[((size_t)g * (L + 1) + L) * Mp + c];
+      const float eg = sscale[g * P + j];
+      sscale[g * P + j] = (eg == -EDAA_INF) ? 0.f : ldexpf(1.f, (int)(eg - mx));  // exact (0 below 2^-149)
     }
-    S = warp_sum_d(S);
-    if (lane == 0) {
-      // shifted accumulation: every pixel contributed w - 2^(k-e_g), i.e.
-      // 2^(k-mx) in the merged frame; add N * 2^(k-mx) back to the denominator
-      const double wref = ldexp(1.0, cd.bref[c] - (int)mx);
-      S += wref * (double)cd.N;
-      sS[j] = S;
-      sW[j] = wref / S;
-      // stored logits live in the frame log(N b): keep lse - log N (small near uniform B)
-      if (lc == 0) cd.lse[c] = (float)((double)mx * 0.69314718055994531 + log(S) - logN);
-    }
+    if (lane == 0) sw[j] = (double)mx;
   }
   __syncthreads();
-  for (int e = tid; e < Pg * P; e += kThreads) sscale[e] /= sS[e % P];
+  // round 2: scaled sums of the partials of the chunk's bands and of the ones band
+  team_sums(
+      (nl + 1) * P, Pg,
+      [&](int e) {
+        const int li = e / P, j = e - li * P;
+        const int l = li < nl ? l0 + li : L;
+        return PartialRow{cd.part + (size_t)l * Mp + c0 + j, (size_t)(L + 1) * Mp, sscale + j, P};
+      },
+      [&](int e, double v) { sraw[e] = v; });
   __syncthreads();
-  const int l0 = lc * cd.lchunk, nl = min(cd.lchunk, L - l0);
+  if (tid < P) {
+    const int j = tid, c = c0 + j;
+    const double mx = sw[j];
+    // shifted accumulation: every pixel contributed w - 2^(k-e_g), i.e.
+    // 2^(k-mx) in the merged frame; add N 2^(k-mx) back to the denominator
+    const double wref = ldexp(1.0, cd.bref[c] - (int)mx);
+    const double S = sraw[nl * P + j] + wref * (double)cd.N;
+    if (lc == 0) cd.lse[c] = (float)(mx * 0.69314718055994531 + log(S) - log((double)cd.N));
+    sw[j] = wref;
+    sw[kMaxP + j] = S;
+  }
+  __syncthreads();
   for (int e = tid; e < nl * P; e += kThreads) {
-    const int l = l0 + e / P, j = e - (e / P) * P;
-    double s = sW[j] * cd.sx[l];
-    s += sum_partials(cd.part + (size_t)l * Mp + m * P + j, (size_t)(L + 1) * Mp, Pg, sscale + j, P);
-    cd.Ed[(size_t)l * Mp + m * P + j] = s;
-    cd.Ef[(size_t)l * Mp + m * P + j] = (float)s;
-    if (cd.tc) store_panel(cd, cd.panelE, m * P + j, l, s);
+    const int li = e / P, l = l0 + li, j = e - li * P;
+    const double s = (sraw[e] + sw[j] * ssx[li]) / sw[kMaxP + j];
+    cd.Ed[(size_t)l * Mp + c0 + j] = s;
+    cd.Ef[(size_t)l * Mp + c0 + j] = (float)s;
+    if (cd.tc) store_panel(cd, cd.panelE, c0 + j, l, s);
     sE[e] = s;
   }
   __syncthreads();
@@ -186,10 +261,10 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool
   }
   for (int e = tid; e < nl * P; e += kThreads) {
     const int li = e / P, l = l0 + li, j = e - li * P;
-    double r = -cd.XAt[(size_t)l * Mp + m * P + j];
-    for (int k = 0; k < P; ++k) r += sE[li * P + k] * cd.AAt[(size_t)m * P * P + k * P + j];
-    cd.Rf[(size_t)l * Mp + m * P + j] = (float)r;
-    if (cd.tc) store_panel(cd, cd.panelR, m * P + j, l, r);
+    double r = -sxa[e];
+    for (int k = 0; k < P; ++k) r += sE[li * P + k] * saat[k * P + j];
+    cd.Rf[(size_t)l * Mp + c0 + j] = (float)r;
+    if (cd.tc) store_panel(cd, cd.panelR, c0 + j, l, r);
     sprod[e] = sE[e] * r;
   }
   __syncthreads();
@@ -204,7 +279,7 @@ __device__ void merge_phase(const Batch* __restrict__ bt, int ph, float* smem) {
     const int local = u - cd.unit0;
     const int m = local / cd.nlchunk, lc = local - m * cd.nlchunk;
     if (ph == PH_AM) merge_a_unit(cd, m, lc, smem);
-    else merge_b_unit(cd, m, lc, smem, ph == PH_BM0);
+    else merge_b_unit(cd, m, lc, smem);
   }
 }
 
@@ -214,100 +289,126 @@ __device__ void merge_phase(const Batch* __restrict__ bt, int ph, float* smem) {
 // Largest eigenvalue of a symmetric p x p matrix by the cyclic Jacobi method
 // (plane rotations that zero one off-diagonal entry at a time, Golub & Van
 // Loan, "Matrix Computations", Sec. 8.5).
-__device__ double jacobi_max_eig(double* a, int n) {
+template <typename F>
+__device__ F jacobi_max_eig(F* a, int n) {
+  const F tol = sizeof(F) == 4 ? (F)1e-14 : (F)1e-30;  // squared relative size of the off-diagonal part
   for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0, diag = 0.0;
+    F off = 0, diag = 0;
     for (int i = 0; i < n; ++i) {
       diag += a[i * n + i] * a[i * n + i];
       for (int j = i + 1; j < n; ++j) off += a[i * n + j] * a[i * n + j];
     }
-    if (off <= 1e-30 * diag || off == 0.0) break;
+    if (off <= tol * diag || off == (F)0) break;
     for (int p = 0; p < n; ++p) {
       for (int q = p + 1; q < n; ++q) {
-        const double apq = a[p * n + q];
-        if (apq == 0.0) continue;
-        const double theta = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
-        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        const F apq = a[p * n + q];
+        if (apq == (F)0) continue;
+        const F theta = (a[q * n + q] - a[p * n + p]) / ((F)2 * apq);
+        const F t = (theta >= (F)0 ? (F)1 : (F)-1) / (fabs(theta) + sqrt(theta * theta + (F)1));
+        const F c = (F)1 / sqrt(t * t + (F)1), s = t * c;
         for (int k = 0; k < n; ++k) {  // columns p, q
-          const double akp = a[k * n + p], akq = a[k * n + q];
+          const F akp = a[k * n + p], akq = a[k * n + q];
           a[k * n + p] = c * akp - s * akq;
           a[k * n + q] = s * akp + c * akq;
         }
         for (int k = 0; k < n; ++k) {  // rows p, q
-          const double apk = a[p * n + k], aqk = a[q * n + k];
+          const F apk = a[p * n + k], aqk = a[q * n + k];
           a[p * n + k] = c * apk - s * aqk;
           a[q * n + k] = s * apk + c * aqk;
         }
       }
     }
   }
-  double mx = a[0];
+  F mx = a[0];
   for (int i = 1; i < n; ++i) mx = fmax(mx, a[i * n + i]);
   return mx;
 }
 
-__device__ void eta_phase(const Batch* __restrict__ bt) {
-  for (int g = blockIdx.x * kThreads + threadIdx.x; g < bt->total_runs; g += gridDim.x * kThreads) {
+// G = E^T E of run m with the mean pixel added back (E = E_c + xbar 1^T), by
+// one warp: lanes stride over the bands, each entry is reduced in a fixed
+// butterfly and lands in Gw (P x P, shared memory).
+__device__ void warp_gram(const CubeDev& cd, int m, double* Gw, int lane) {
+  const int P = cd.p;
+  for (int e = 0; e < P * P; ++e) {
+    const int j = e / P, k = e - j * P;
+    double s = 0.0;
+    if (k >= j)
+      for (int l = lane; l < cd.L; l += 32) {
+        const double* r = cd.Ed + (size_t)l * cd.Mp + m * P;
+        const double xb = cd.xbar[l];
+        s += (r[j] + xb) * (r[k] + xb);
+      }
+    s = warp_sum_d(s);
+    if (lane == 0 && k >= j) Gw[j * P + k] = Gw[k * P + j] = s;
+  }
+  __syncwarp();
+}
+
+// Step sizes (eqs. eta0A, eta0B), one warp per run: sigma_max^2(X B^0) by
+// Jacobi on G = E^0T E^0, eta1 = gamma / sigma_max^2, eta2 = sqrt(p / N) eta1.
+__device__ void eta_phase(const Batch* __restrict__ bt, float* smem) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* Gw = reinterpret_cast<double*>(smem) + warp * kMaxP * kMaxP;
+  float* Gf = reinterpret_cast<float*>(reinterpret_cast<double*>(smem) + kWarps * kMaxP * kMaxP) + warp * kMaxP * kMaxP;
+  for (int g = blockIdx.x * kWarps + warp; g < bt->total_runs; g += gridDim.x * kWarps) {
     int ci = 0;
     while (ci + 1 < bt->n_cubes && g >= bt->c[ci + 1].run0) ++ci;
     const CubeDev& cd = bt->c[ci];
     const int m = g - cd.run0, P = cd.p;
-    double G[kMaxP * kMaxP];
-    for (int e = 0; e < P * P; ++e) G[e] = 0.0;
-    for (int l = 0; l < cd.L; ++l) {  // E^0 = X B^0 with the mean pixel added back
-      const double* e = cd.Ed + (size_t)l * cd.Mp + m * P;
-      const double xb = cd.xbar[l];
-      for (int j = 0; j < P; ++j)
-        for (int k = 0; k < P; ++k) G[j * P + k] += (e[j] + xb) * (e[k] + xb);
+    warp_gram(cd, m, Gw, lane);
+    if (lane == 0) {
+      // FP64 Gram matrix, FP32 rotations: the largest eigenvalue to ~1e-7 relative
+      for (int e = 0; e < P * P; ++e) Gf[e] = (float)Gw[e];
+      const double s2 = (double)jacobi_max_eig(Gf, P);
+      const double e1 = cd.gammas[m] / s2;
+      const double e2 = sqrt((double)P / (double)cd.N) * e1;
+      cd.sig2[m] = s2;
+      cd.eta1d[m] = e1;
+      cd.eta2d[m] = e2;
+      cd.eta1[m] = (float)e1;
+      cd.eta2[m] = (float)e2;
     }
-    const double s2 = jacobi_max_eig(G, P);
-    const double e1 = cd.gammas[m] / s2;
-    const double e2 = sqrt((double)P / (double)cd.N) * e1;
-    cd.sig2[m] = s2;
-    cd.eta1d[m] = e1;
-    cd.eta2d[m] = e2;
-    cd.eta1[m] = (float)e1;
-    cd.eta2[m] = (float)e2;
+    __syncwarp();
   }
 }
 
-__device__ void fitm_phase(const Batch* __restrict__ bt) {
-  for (int g = blockIdx.x * kThreads + threadIdx.x; g < bt->total_runs; g += gridDim.x * kThreads) {
+// Fit merge and coherence (Algorithm 2, eq. coherence), one warp per run.
+__device__ void fitm_phase(const Batch* __restrict__ bt, float* smem) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* Gw = reinterpret_cast<double*>(smem) + warp * kMaxP * kMaxP;
+  for (int g = blockIdx.x * kWarps + warp; g < bt->total_runs; g += gridDim.x * kWarps) {
     int ci = 0;
     while (ci + 1 < bt->n_cubes && g >= bt->c[ci + 1].run0) ++ci;
     const CubeDev& cd = bt->c[ci];
     const int m = g - cd.run0, P = cd.p;
     double a1 = 0.0, am = 0.0, a2 = 0.0;
-    for (int q = 0; q < cd.Pg; ++q) {
+    for (int q = lane; q < cd.Pg; q += 32) {
       const double* s = cd.pfit + ((size_t)q * cd.M + m) * 3;
       a1 += s[0];
       am = fmax(am, s[1]);
       a2 += s[2];
     }
-    cd.fit[m] = a1;
-    cd.fitmax[m] = am;
-    cd.loss2[m] = a2;
-    // coherence (eq. coherence) from the FP64 copy of E
-    double G[kMaxP * kMaxP];
-    for (int e = 0; e < P * P; ++e) G[e] = 0.0;
-    for (int l = 0; l < cd.L; ++l) {  // uncentred E = E_c + xbar 1^T
-      const double* e = cd.Ed + (size_t)l * cd.Mp + m * P;
-      const double xb = cd.xbar[l];
+    a1 = warp_sum_d(a1);
+    am = warp_max_d(am);
+    a2 = warp_sum_d(a2);
+    warp_gram(cd, m, Gw, lane);  // coherence from the FP64 copy of E, uncentred
+    if (lane == 0) {
+      cd.fit[m] = a1;
+      cd.fitmax[m] = am;
+      cd.loss2[m] = a2;
+      double mu = -INFINITY;
       for (int j = 0; j < P; ++j)
-        for (int k = j; k < P; ++k) G[j * P + k] += (e[j] + xb) * (e[k] + xb);
-    }
-    double mu = -INFINITY;
-    for (int j = 0; j < P; ++j)
-      for (int k = j + 1; k < P; ++k) {
-        double v = G[j * P + k];
-        if (bt->coh_mode == 0) {
-          const double d = sqrt(G[j * P + j]) * sqrt(G[k * P + k]);
-          v = d > 0.0 ? v / d : 0.0;
+        for (int k = j + 1; k < P; ++k) {
+          double v = Gw[j * P + k];
+          if (bt->coh_mode == 0) {
+            const double d = sqrt(Gw[j * P + j]) * sqrt(Gw[k * P + k]);
+            v = d > 0.0 ? v / d : 0.0;
+          }
+          mu = fmax(mu, v);
         }
-        mu = fmax(mu, v);
-      }
-    cd.mu[m] = mu;
+      cd.mu[m] = mu;
+    }
+    __syncwarp();
   }
 }
 
@@ -327,6 +428,8 @@ __host__ __device__ inline int phase_of(int mode, int s, int K2) {
   return (k & 1) ? PH_BM : PH_B;
 }
 
+int program_phase_id(int mode, int s, int K2) { return phase_of(mode, s, K2); }
+
 int program_phase_count(int mode, int n_outer, int K2) {
   if (mode == MODE_INIT) return 5;
   if (mode == MODE_FIT) return 2;
@@ -338,10 +441,13 @@ k_edaa(const Batch* __restrict__ bt, int mode, int n_outer, int ph_lo, int ph_hi
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   (void)n_outer;
+  const bool tr = bt->trace_start != nullptr;
   for (int s = ph_lo; s < ph_hi; ++s) {
     if (s > ph_lo) {
       if (!grid_barrier(bt->bar, gridDim.x, bt->status, bt->timeout_ns)) return;
     }
+    const size_t ti = (size_t)mode * kTraceCap + s;
+    if (tr && threadIdx.x == 0 && s < kTraceCap) atomicMin(bt->trace_start + ti, (unsigned long long)global_ns());
     const int ph = phase_of(mode, s, bt->K2);
     switch (ph) {
       case PH_A:
@@ -352,9 +458,13 @@ k_edaa(const Batch* __restrict__ bt, int mode, int n_outer, int ph_lo, int ph_hi
       case PH_AM:
       case PH_BM:
       case PH_BM0: merge_phase(bt, ph, smem); break;
-      case PH_ETA: eta_phase(bt); break;
-      case PH_FITM: fitm_phase(bt); break;
+      case PH_ETA: eta_phase(bt, smem); break;
+      case PH_FITM: fitm_phase(bt, smem); break;
       default: break;
+    }
+    if (tr) {
+      __syncthreads();
+      if (threadIdx.x == 0 && s < kTraceCap) atomicMax(bt->trace_end + ti, (unsigned long long)global_ns());
     }
   }
 }

@@ -27,14 +27,14 @@ EXPORTS = ["edaa_config_default", "edaa_init", "edaa_reset", "edaa_step", "edaa_
            "edaa_select_rule", "edaa_get", "edaa_grad", "edaa_loss", "edaa_step_sizes", "edaa_sync",
            "edaa_outer_done", "edaa_describe", "edaa_destroy", "edaa_last_error", "edaa_selftest_barrier",
            "edaa_fit_eval_static", "edaa_unrolled_create", "edaa_unrolled_forward", "edaa_unrolled_backward",
-           "edaa_unrolled_destroy"]
+           "edaa_unrolled_destroy", "edaa_trace_read"]
 
 
 class Config(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int), ("K1", ctypes.c_int), ("K2", ctypes.c_int), ("normalize", ctypes.c_int),
                 ("precision", ctypes.c_int), ("fit_norm", ctypes.c_int), ("coherence", ctypes.c_int),
                 ("fit_ratio", ctypes.c_double), ("persistent", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("barrier_timeout_ms", ctypes.c_double), ("center", ctypes.c_int)]
+                ("barrier_timeout_ms", ctypes.c_double), ("center", ctypes.c_int), ("trace", ctypes.c_int)]
 
 
 class CubeDesc(ctypes.Structure):
@@ -87,6 +87,7 @@ def load_library():
         "edaa_unrolled_forward": (ctypes.c_int, [vp, vp, ctypes.c_uint64, dp, dp, vp, vp]),
         "edaa_unrolled_backward": (ctypes.c_int, [vp, vp, vp, vp, dp, dp]),
         "edaa_unrolled_destroy": (None, [vp]),
+        "edaa_trace_read": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip, ip, dp, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -249,6 +250,22 @@ class Context:
         _check(self.lib.edaa_step_sizes(self.h, cube, e1.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                         e2.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "edaa_step_sizes")
         return e1, e2
+
+    PHASE_NAMES = ["A-pass", "A-merge", "B-pass", "B-merge", "initial B-pass", "initial A-pass", "step sizes",
+                   "fit pass", "fit merge", "first B-merge"]
+
+    def trace(self, which: int = 0):
+        """Phase trace of the last launch sequence (needs trace=1): which 0 =
+        outer iterations, 1 = initialisation, 2 = fit.  Returns (phase ids,
+        start us, duration us) as numpy arrays."""
+        cap = 4096
+        ph, t0, dt, n = np.zeros(cap, np.int32), np.zeros(cap), np.zeros(cap), ctypes.c_int()
+        _check(self.lib.edaa_trace_read(self.h, which, cap, ctypes.byref(n),
+                                        ph.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                        t0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        dt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "edaa_trace_read")
+        k = min(n.value, cap)
+        return ph[:k], t0[:k], dt[:k]
 
     def describe(self, cube: int = 0) -> Dict[str, int]:
         vals = [ctypes.c_int() for _ in range(5)]
