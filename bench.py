@@ -287,7 +287,7 @@ def main():
     ap.add_argument("--outer", type=int, default=100, help="outer iterations T (100: the paper's)")
     ap.add_argument("--workload", default="jasper", choices=sorted(WORKLOADS))
     ap.add_argument("--autotune", type=int, default=1)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "tf32x3"])
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -313,7 +313,7 @@ def main():
     cubes = make_workload_cubes(args.workload, rank)
     stream = torch.cuda.Stream()
     Xds = [torch.from_numpy(c.pixel_major()).cuda() for c in cubes]
-    prec = {"fp32": edaa.FP32, "tf32": edaa.TF32, "bf16": edaa.BF16}[args.precision]
+    prec = {"fp32": edaa.FP32, "tf32": edaa.TF32, "bf16": edaa.BF16, "tf32x3": edaa.TF32X3}[args.precision]
     ctx = edaa.Context([dict(X=Xd, p=c.p, seeds=c.seeds, gammas=c.gammas) for Xd, c in zip(Xds, cubes)],
                        stream=stream, T=T, K1=K1, K2=K2, persistent=args.persistent, autotune=args.autotune,
                        precision=prec)
@@ -368,9 +368,11 @@ def main():
     if tensor:
         # the solve is one long launch: sustained bf16 peak; TF32 at the nominal TF32/BF16 ratio 1.1/2.25
         bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
-        peak = bf16 if args.precision == "bf16" else bf16 * 1.1 / 2.25
+        # split TF32 issues three MMAs per product: its peak in algorithmic FLOPs is a third of TF32's
+        peak = bf16 if args.precision == "bf16" else bf16 * 1.1 / 2.25 / (3 if args.precision == "tf32x3" else 1)
         peak_source = (f"{peak_kind} sustained dense bf16 {bf16} TFLOP/s" +
-                       ("" if args.precision == "bf16" else " x nominal TF32/BF16 ratio 1.1/2.25"))
+                       ("" if args.precision == "bf16" else " x nominal TF32/BF16 ratio 1.1/2.25") +
+                       (" / 3 MMAs per product" if args.precision == "tf32x3" else ""))
     else:
         peak = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
         peak_source = (f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 x "
@@ -431,7 +433,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "tf32": "tf32 (fp32 accumulate)", "bf16": "bf16 (fp32 accumulate)"}[args.precision],
+            "dtype": {"fp32": "f32", "tf32": "tf32 (fp32 accumulate)", "bf16": "bf16 (fp32 accumulate)",
+                      "tf32x3": "f32 via split tf32 (hi*hi + hi*lo + lo*hi, fp32 accumulate)"}[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload] if args.outer == 100 else
                        WORKLOADS[args.workload] + f" (T={T})", "global_batch_runs": sum(c.M for c in cubes) * world,

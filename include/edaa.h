@@ -47,7 +47,15 @@ typedef enum {
   EDAA_ERR_UNSUPPORTED = 7  /* shape outside the compiled kernels' range       */
 } edaa_status;
 
-typedef enum { EDAA_FP32 = 0, EDAA_TF32 = 1, EDAA_BF16 = 2 } edaa_precision;
+/* Contraction types of the X-streaming passes.  EDAA_FP32: CUDA cores.
+ * EDAA_TF32, EDAA_BF16: tensor cores with TF32 or BF16 operands and FP32
+ * accumulation.  EDAA_TF32X3: tensor cores at FP32 accuracy; every operand is
+ * split into two TF32 parts (x = hi + lo, lo = tf32(x - hi)) and each product
+ * is formed as hi*hi + hi*lo + lo*hi (the dropped lo*lo term is about 2^-22
+ * relative), with the element-wise steps in full FP32.  The tensor-core modes
+ * apply to cubes whose ensembles make the contractions dense (M p >= 64);
+ * other cubes use the CUDA-core FP32 pass. */
+typedef enum { EDAA_FP32 = 0, EDAA_TF32 = 1, EDAA_BF16 = 2, EDAA_TF32X3 = 3 } edaa_precision;
 
 typedef struct {
   int T;              /* outer iterations (Algorithm 1; paper: 100)                 */

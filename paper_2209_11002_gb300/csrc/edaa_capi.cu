@@ -170,7 +170,7 @@ static edaa_status check_status(edaa_ctx* c) {
 // column count Rgp fits TMEM next to one accumulator per 128-band tile
 // (Rgp * (1 + band tiles) <= 512 columns, Rgp <= 256), balanced over groups.
 static void tc_tile(CubeHost& h) {
-  const int rgp_max = tc_rgp_max(h.L, h.esz);
+  const int rgp_max = tc_rgp_max(h.L, h.esz, h.tc == 3);
   const int rm_max = std::max(1, std::min({128, rgp_max / h.p, 2048 / (h.p * h.p)}));
   const int RG = (h.M + rm_max - 1) / rm_max;
   h.tile.Rm = (h.M + RG - 1) / RG;
@@ -236,7 +236,7 @@ static size_t pass_item_smem(const CubeHost& h) {
   if (h.tc) {
     const int rb = std::min(h.tile.Rm, (8 / h.tile.WP1) * rq1_max(h.p));
     s = (size_t)pass_smem(h.L, h.Ls, h.Lr, h.p, rb, 128).total * 4;  // fit pass in run blocks
-    s = std::max(s, (size_t)tc_smem(round_up(h.tile.Rm * h.p, 16), h.esz).total);
+    s = std::max(s, (size_t)tc_smem(round_up(h.tile.Rm * h.p, 16), h.esz, h.tc == 3).total);
   }
   return s;
 }
@@ -267,9 +267,10 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
   size_t oseeds = take(M * 8), ogam = take(M * 8);
   size_t orho = take(L * Mp * 8), obref = take(Mp * 4);  // nlchunk <= L band chunks
   size_t ogpart = take(L * M * p * p * 8);
-  const size_t tcb = h.tc ? 1 : 0;
-  size_t oXk = take(tcb * N * h.kp * h.esz), oXT = take(tcb * (L + 1) * h.Npad * h.esz);
-  size_t opE = take(tcb * Mp * h.kp * h.esz), opR = take(tcb * Mp * h.kp * h.esz), otm = take(tcb * 4 * 128);
+  const size_t tcb = h.tc ? 1 : 0, parts = h.tc == 3 ? 2 : 1;  // split operands: high and low copies
+  size_t oXk = take(tcb * parts * N * h.kp * h.esz), oXT = take(tcb * parts * (L + 1) * h.Npad * h.esz);
+  size_t opE = take(tcb * parts * Mp * h.kp * h.esz), opR = take(tcb * parts * Mp * h.kp * h.esz);
+  size_t otm = take(tcb * 8 * 128);
   size_t oscale = take(N * 8), oxbar = take(L * 8), osx = take((L + 1) * 8), obsum = take((size_t)normalize_blocks(h.N) * L * 8);
   if (assign) {
     char* b = (char*)h.arena;
@@ -348,13 +349,23 @@ static edaa_status make_tmaps(edaa_ctx* c, CubeHost& h) {
   const CUtensorMapDataType dt = h.esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const cuuint32_t kch = 128 / h.esz, es[2] = {1, 1};
   const int rgp = round_up(h.tile.Rm * h.p, 16);
-  CUtensorMap m[4];
-  struct Spec { void* ptr; cuuint64_t inner, outer; cuuint32_t box_outer; } spec[4] = {
+  // [X pixel-major, X band-major, panel E, panel R], then with split operands
+  // the same four for the low parts, which follow the high parts in memory
+  CUtensorMap m[8];
+  const size_t nXk = (size_t)h.N * h.kp * h.esz, nXT = (size_t)(h.L + 1) * h.Npad * h.esz;
+  const size_t nP = (size_t)h.Mp * h.kp * h.esz;
+  char* lo[4] = {(char*)h.Xk + nXk, (char*)h.XT + nXT, (char*)h.dev.panelE + nP, (char*)h.dev.panelR + nP};
+  struct Spec { void* ptr; cuuint64_t inner, outer; cuuint32_t box_outer; } spec[8] = {
       {h.Xk, (cuuint64_t)h.kp, (cuuint64_t)h.N, 128},
       {h.XT, (cuuint64_t)h.Npad, (cuuint64_t)(h.L + 1), 128},
       {h.dev.panelE, (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp},
-      {h.dev.panelR, (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp}};
-  for (int i = 0; i < 4; ++i) {
+      {h.dev.panelR, (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp},
+      {lo[0], (cuuint64_t)h.kp, (cuuint64_t)h.N, 128},
+      {lo[1], (cuuint64_t)h.Npad, (cuuint64_t)(h.L + 1), 128},
+      {lo[2], (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp},
+      {lo[3], (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp}};
+  const int nmaps = h.tc == 3 ? 8 : 4;
+  for (int i = 0; i < nmaps; ++i) {
     const cuuint64_t dims[2] = {spec[i].inner, spec[i].outer};
     const cuuint64_t strides[1] = {spec[i].inner * (cuuint64_t)h.esz};
     const cuuint32_t box[2] = {kch, spec[i].box_outer};
@@ -362,7 +373,8 @@ static edaa_status make_tmaps(edaa_ctx* c, CubeHost& h) {
                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(EDAA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   }
-  CK(cudaMemcpyAsync(h.tmaps, m, sizeof(m), cudaMemcpyHostToDevice, c->stream), "upload tensor maps");
+  CK(cudaMemcpyAsync(h.tmaps, m, nmaps * sizeof(CUtensorMap), cudaMemcpyHostToDevice, c->stream),
+     "upload tensor maps");
   return EDAA_OK;
 }
 
@@ -518,7 +530,7 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
   if (cfg) conf = *cfg;
   if (conf.T < 0 || conf.K1 < 0 || conf.K2 < 0) return fail(EDAA_ERR_ARG, "T, K1, K2 must be >= 0");
   if (!(conf.fit_ratio >= 1.0)) return fail(EDAA_ERR_ARG, "fit_ratio must be >= 1");
-  if (conf.precision < EDAA_FP32 || conf.precision > EDAA_BF16) return fail(EDAA_ERR_ARG, "unknown precision");
+  if (conf.precision < EDAA_FP32 || conf.precision > EDAA_TF32X3) return fail(EDAA_ERR_ARG, "unknown precision");
   for (int i = 0; i < n_cubes; ++i) {
     const edaa_cube& q = cubes[i];
     if (!q.X) return fail(EDAA_ERR_ARG, "cube X is NULL");
@@ -569,7 +581,7 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
     h.tile = default_tile(q.L, q.p, q.M);
     // tensor cores only where the ensemble makes the contractions dense (M p >= 64)
     if (conf.precision != EDAA_FP32 && h.Mp >= 64) {
-      h.tc = conf.precision == EDAA_BF16 ? 2 : 1;
+      h.tc = conf.precision == EDAA_BF16 ? 2 : (conf.precision == EDAA_TF32X3 ? 3 : 1);
       h.esz = h.tc == 2 ? 2 : 4;
       h.kp = round_up(q.L + 1, 128 / h.esz);
       h.Npad = round_up(q.N, 8);

@@ -49,14 +49,21 @@ __device__ void pass_phase(const Batch* __restrict__ bt, int ph, float* smem) {
 // ---------------------------------------------------------------------------
 // K-major copy of a panel for the tensor-core passes: row c (column of E or R),
 // band l, in the compute type (TF32 rounded to nearest, or BF16)
+// (split operands: the high part here and the low part tf32(v - high) one
+// panel further on)
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
 __device__ __forceinline__ void store_panel(const CubeDev& cd, void* panel, int c, int l, double v) {
   const size_t o = (size_t)c * cd.tc_kp + l;
   if (cd.tc == 2) {
     reinterpret_cast<__nv_bfloat16*>(panel)[o] = __float2bfloat16_rn((float)v);
   } else {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)v));
-    reinterpret_cast<float*>(panel)[o] = __uint_as_float(r);
+    const float f = (float)v, hi = tf32_rna(f);
+    reinterpret_cast<float*>(panel)[o] = hi;
+    if (cd.tc == 3) reinterpret_cast<float*>(panel)[(size_t)cd.Mp * cd.tc_kp + o] = tf32_rna(f - hi);
   }
 }
 
@@ -695,27 +702,34 @@ cudaError_t launch_gather(const CubeDev& hc, int run, float* E, float* A, float*
 // Compute-type copies of the centred X for the tensor-core passes:
 // Xk: N x kp pixel-major (bands >= L+1 zero), XT: (L+1) x Npad band-major
 // (row L is the ones band), TF32 rounded to nearest or BF16.
-__global__ void k_tc_prepare(const float* __restrict__ X, int L, int Ls, int N, int kp, int Npad, int bf16,
+// mode 1: TF32, 2: BF16, 3: split TF32 (high part, then the low part
+// tf32(x - high) in a second copy of each array right after the first)
+__global__ void k_tc_prepare(const float* __restrict__ X, int L, int Ls, int N, int kp, int Npad, int mode,
                              void* __restrict__ Xk, void* __restrict__ XT) {
-  const size_t n = (size_t)N * kp;
+  const size_t n = (size_t)N * kp, nT = (size_t)(L + 1) * Npad;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / kp), l = (int)(e - (size_t)i * kp);
     const float v = (l < Ls) ? X[(size_t)i * Ls + l] : 0.f;
-    if (bf16) {
+    const size_t t = (size_t)l * Npad + i;
+    if (mode == 2) {
       const __nv_bfloat16 h = __float2bfloat16_rn(v);
       reinterpret_cast<__nv_bfloat16*>(Xk)[e] = h;
-      if (l <= L) reinterpret_cast<__nv_bfloat16*>(XT)[(size_t)l * Npad + i] = h;
+      if (l <= L) reinterpret_cast<__nv_bfloat16*>(XT)[t] = h;
     } else {
-      uint32_t r;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-      reinterpret_cast<float*>(Xk)[e] = __uint_as_float(r);
-      if (l <= L) reinterpret_cast<float*>(XT)[(size_t)l * Npad + i] = __uint_as_float(r);
+      const float hi = tf32_rna(v);
+      reinterpret_cast<float*>(Xk)[e] = hi;
+      if (l <= L) reinterpret_cast<float*>(XT)[t] = hi;
+      if (mode == 3) {
+        const float lo = tf32_rna(v - hi);
+        reinterpret_cast<float*>(Xk)[n + e] = lo;
+        if (l <= L) reinterpret_cast<float*>(XT)[nT + t] = lo;
+      }
     }
   }
 }
 
 cudaError_t launch_tc_prepare(const CubeDev& hc, void* Xk, void* XT, int Npad, cudaStream_t s) {
-  k_tc_prepare<<<1024, 256, 0, s>>>(hc.X, hc.L, hc.Ls, hc.N, hc.tc_kp, Npad, hc.tc == 2 ? 1 : 0, Xk, XT);
+  k_tc_prepare<<<1024, 256, 0, s>>>(hc.X, hc.L, hc.Ls, hc.N, hc.tc_kp, Npad, hc.tc, Xk, XT);
   return cudaGetLastError();
 }
 

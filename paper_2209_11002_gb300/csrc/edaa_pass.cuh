@@ -734,7 +734,7 @@ __device__ __noinline__ void fit_item(const CubeDev& cd, int rg, int pg, float* 
   __syncthreads();
 }
 
-template <int P, bool IS_A, bool BF>
+template <int P, bool IS_A, int PREC>
 __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const CubeDev& cd, int rg, int pg,
                                           unsigned char* smem_raw, int K1, bool init);
 
@@ -752,11 +752,14 @@ __device__ __forceinline__ void pass_dispatch_impl(const Batch* bt, const CubeDe
   if (cd.tc) {
     unsigned char* sb = reinterpret_cast<unsigned char*>(smem);
     if (cd.tc == 2) {
-      if (is_a) tc_pass_item<P, true, true>(bt, cd, rg, pg, sb, k1, init);
-      else tc_pass_item<P, false, true>(bt, cd, rg, pg, sb, k1, init);
+      if (is_a) tc_pass_item<P, true, 1>(bt, cd, rg, pg, sb, k1, init);
+      else tc_pass_item<P, false, 1>(bt, cd, rg, pg, sb, k1, init);
+    } else if (cd.tc == 3) {
+      if (is_a) tc_pass_item<P, true, 2>(bt, cd, rg, pg, sb, k1, init);
+      else tc_pass_item<P, false, 2>(bt, cd, rg, pg, sb, k1, init);
     } else {
-      if (is_a) tc_pass_item<P, true, false>(bt, cd, rg, pg, sb, k1, init);
-      else tc_pass_item<P, false, false>(bt, cd, rg, pg, sb, k1, init);
+      if (is_a) tc_pass_item<P, true, 0>(bt, cd, rg, pg, sb, k1, init);
+      else tc_pass_item<P, false, 0>(bt, cd, rg, pg, sb, k1, init);
     }
     return;
   }

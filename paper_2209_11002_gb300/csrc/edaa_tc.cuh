@@ -149,29 +149,36 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-// Largest padded run-group width: TMEM holds C (Rgp columns) and one Acc
-// per 128-band tile; 8 spare columns keep the 8-wide TMEM reads of the last
-// run inside the 512 allocated; shared memory (3 stages + W + 32 KB) <= 227 KB.
-__host__ __device__ inline int tc_rgp_max(int L, int esz) {
-  const int nbt = (L + 1 + 127) / 128;
-  const int tmem = ((512 - 8) / (1 + nbt)) & ~15;
-  const int smem = esz == 2 ? 224 : 160;
-  return tmem < smem ? tmem : smem;
-}
-
 struct TcSmem {
   uint32_t stage_bytes, w_off, misc_off, total;
 };
-// stages: [X chunk 128 x 128 B | panel chunk Rgp x 128 B]; W: npc chunks of Rgp x 128 B
-__host__ __device__ inline TcSmem tc_smem(int Rgp, int esz) {
+// Shared memory of a tensor-core pass.  A ring stage holds one 128 x 128-byte
+// chunk of X and the panel chunk (Rgp x 128 B; with split operands both the
+// high and the low part); W holds the weights of one 128-pixel tile in
+// 128-byte pixel chunks (split: high and low part); 32 KB for barriers,
+// column statistics, G, step sizes and A A^T sums; 1 KB alignment slack.
+__host__ __device__ inline TcSmem tc_smem(int Rgp, int esz, bool split) {
   TcSmem s;
-  const uint32_t pnl = (uint32_t)Rgp * 128u;
-  s.stage_bytes = 128u * 128u + ((pnl + 1023u) & ~1023u);
+  const uint32_t pnl = ((uint32_t)Rgp * 128u + 1023u) & ~1023u;
+  const uint32_t parts = split ? 2u : 1u;
+  s.stage_bytes = 128u * 128u + parts * pnl;
   const uint32_t npc = 128u / (128u / (uint32_t)esz);  // pixel chunks of 128 bytes per 128-pixel tile
-  s.w_off = 1024u + kTcStages * s.stage_bytes;       // 1024: alignment slack
-  s.misc_off = s.w_off + npc * ((pnl + 1023u) & ~1023u);
-  s.total = s.misc_off + 32768u;                     // barriers, column stats, G, eta, A A^T sums
+  s.w_off = 1024u + kTcStages * s.stage_bytes;
+  s.misc_off = s.w_off + parts * npc * pnl;
+  s.total = s.misc_off + 32768u;
   return s;
+}
+
+// Largest padded run-group width (a multiple of 16): TMEM holds C (Rgp
+// columns) and one Acc per 128-band tile (split operands: a per-tile Acc and
+// a running sum per band tile), with 8 spare columns so that the 8-wide TMEM
+// reads of the last run stay inside the 512 allocated; the shared memory
+// above stays within 227 KB.
+__host__ __device__ inline int tc_rgp_max(int L, int esz, bool split) {
+  const int nbt = (L + 1 + 127) / 128;
+  int r = ((512 - 8) / (1 + (split ? 2 : 1) * nbt)) & ~15;
+  while (r > 16 && tc_smem(r, esz, split).total > 232448u) r -= 16;
+  return r;
 }
 
 }  // namespace edaa

@@ -5,9 +5,13 @@
 
 namespace edaa {
 
-template <int P, bool IS_A, bool BF>
+// PREC: 0 TF32, 1 BF16, 2 split TF32 (x = hi + lo; products hi*hi + hi*lo + lo*hi,
+// and the element-wise steps in full FP32 as in the CUDA-core pass).
+template <int P, bool IS_A, int PREC>
 __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const CubeDev& cd, int rg, int pg,
                                           unsigned char* smem_raw, int K1, bool init) {
+  constexpr bool BF = PREC == 1, SPLIT = PREC == 2;
+  constexpr int SUB = SPLIT ? 2 : 1;  // stream chunks per 128-byte K chunk (split: high part, then low part)
   constexpr int PP = P * (P + 1) / 2;
   constexpr int ESZ = BF ? 2 : 4;
   constexpr int KCH = 128 / ESZ;   // elements per 128-byte row (32 tf32, 64 bf16)
@@ -23,10 +27,14 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   const CUtensorMap* tmX = cd.tmaps + 0;
   const CUtensorMap* tmXT = cd.tmaps + 1;
   const CUtensorMap* tmPan = cd.tmaps + (IS_A ? 2 : 3);
-  const TcSmem S = tc_smem(Rgp, ESZ);
+  const CUtensorMap* tmXlo = cd.tmaps + 4;  // split operands: the low parts
+  const CUtensorMap* tmXTlo = cd.tmaps + 5;
+  const CUtensorMap* tmPanLo = cd.tmaps + (IS_A ? 6 : 7);
+  const TcSmem S = tc_smem(Rgp, ESZ, SPLIT);
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* Wsm = sm + (S.w_off - 1024u);
   const uint32_t wchunk = ((uint32_t)Rgp * 128u + 1023u) & ~1023u;
+  const uint32_t pnl = wchunk;  // a panel chunk (Rgp rows of 128 B), 1024-byte aligned in its stage
   unsigned char* misc = sm + (S.misc_off - 1024u);
   uint64_t* full = reinterpret_cast<uint64_t*>(misc);      // kTcStages
   uint64_t* empty = full + kTcStages;                      // kTcStages
@@ -89,7 +97,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     }
   }
   // W: zero once (padding rows and invalid pixels must stay 0)
-  for (uint32_t e = tid; e < (uint32_t)NPC * wchunk / 4; e += kThreads) reinterpret_cast<float*>(Wsm)[e] = 0.f;
+  for (uint32_t e = tid; e < (uint32_t)SUB * NPC * wchunk / 4; e += kThreads) reinterpret_cast<float*>(Wsm)[e] = 0.f;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -103,8 +111,9 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   // run up to kTcStages chunks ahead of the MMAs, so contraction 2's X streams
   // in during the epilogue and the next tile's contraction 1 during
   // contraction 2.
-  const int nc2 = nbt * NPC;
-  const int per_tile = (do_c1 ? nkc : 0) + nc2;
+  const int nc1 = do_c1 ? nkc * SUB : 0;
+  const int nc2 = nbt * NPC * SUB;
+  const int per_tile = nc1 + nc2;
   const int ntl = pg < cd.ntiles ? (cd.ntiles - pg + cd.Pg - 1) / cd.Pg : 0;
   const uint32_t total = (uint32_t)(ntl * per_tile);
   uint32_t loaded = 0, issued = 0;
@@ -114,14 +123,17 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     const int q = (int)(k / (uint32_t)per_tile), j = (int)(k - (uint32_t)(q * per_tile));
     const int ti0 = (pg + q * cd.Pg) * kTcTile;
     unsigned char* dst = sm + s * S.stage_bytes;
-    if (do_c1 && j < nkc) {
-      mbar_expect(full + s, 128u * 128u + (uint32_t)Rgp * 128u);
-      tma2d(dst, tmX, j * KCH, ti0, full + s);
-      tma2d(dst + 128 * 128, tmPan, j * KCH, c0, full + s);
-    } else {
-      const int jj = j - (do_c1 ? nkc : 0), bti = jj / NPC, pc = jj - bti * NPC;
+    if (j < nc1) {  // X chunk + panel chunk (split: [X hi | P hi | P lo], then [X lo | P hi])
+      const int kc = j / SUB, part = j - kc * SUB;
+      const bool two = SPLIT && part == 0;
+      mbar_expect(full + s, 128u * 128u + (two ? 2u : 1u) * (uint32_t)Rgp * 128u);
+      tma2d(dst, part ? tmXlo : tmX, kc * KCH, ti0, full + s);
+      tma2d(dst + 128 * 128, tmPan, kc * KCH, c0, full + s);
+      if (two) tma2d(dst + 128 * 128 + pnl, tmPanLo, kc * KCH, c0, full + s);
+    } else {  // band-major X chunk (split: high part, then low part)
+      const int jj = j - nc1, kc = jj / SUB, part = jj - kc * SUB, bti = kc / NPC, pc = kc - bti * NPC;
       mbar_expect(full + s, 128u * 128u);
-      tma2d(dst, tmXT, ti0 + pc * KCH, bti * 128, full + s);
+      tma2d(dst, part ? tmXTlo : tmXT, ti0 + pc * KCH, bti * 128, full + s);
     }
     return true;
   };
@@ -144,6 +156,33 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   };
   if (tid == 0 && !fill()) flags[0] = 1;
 
+  // Split operands: contraction 2 of each tile restarts a tile accumulator T
+  // (TMEM columns Rgp (1 + b)), and the threads add it into the running sums
+  // S (columns Rgp (1 + nbt + b)) in FP32, S = S * scale + T, with the B-pass
+  // frame change as the exact power-of-two scale.  The tensor core's FP32
+  // accumulation then never runs over more than one tile: over long chains
+  // (many tiles per CTA) it drifts by more than the FP32 path allows.
+  const uint32_t tl0 = (uint32_t)((warp & 3) * 32) << 16;
+  auto fold_tile = [&](bool first) {
+    for (int b = 0; b < nbt; ++b)
+      for (int cc = (warp >> 2) * 8; cc < Rgp; cc += 16) {
+        const uint32_t tT = tbase + tl0 + (uint32_t)(Rgp * (1 + b) + cc);
+        const uint32_t tS = tbase + tl0 + (uint32_t)(Rgp * (1 + nbt + b) + cc);
+        float vt[8], vs[8];
+        tmem_ld8(tT, vt);
+        if (first) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) vs[j] = vt[j];
+        } else {
+          tmem_ld8(tS, vs);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) vs[j] = fmaf(vs[j], IS_A ? 1.f : colScale[cc + j], vt[j]);
+        }
+        tmem_st8(tS, vs);
+      }
+  };
+  bool folded = false;
+
   uint32_t c1_phase = 0, c2_phase = 0;
   bool c2_pending = false, d2_started = false;
   int bail = 0;
@@ -158,15 +197,19 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     if (do_c1) {
       if (tid == 0 && !flags[0]) {
         bool ok = true;
-        for (int j = 0; j < nkc && ok; ++j)
+        for (int j = 0; j < nc1 && ok; ++j) {
+          const int kc = j / SUB, part = j - kc * SUB;
           ok = consume([&](unsigned char* st) {
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
               const uint64_t da = desc_sw128(su32(st + ks * 32));
               const uint64_t db = desc_sw128(su32(st + 128 * 128 + ks * 32));
-              tc_mma<BF>(tbase, da, db, id, (j | ks) ? 1u : 0u);
+              tc_mma<BF>(tbase, da, db, id, (kc | ks | part) ? 1u : 0u);
+              if (SPLIT && part == 0)  // X hi * P lo
+                tc_mma<BF>(tbase, da, desc_sw128(su32(st + 128 * 128 + pnl + ks * 32)), id, 1u);
             }
           });
+        }
         if (ok) tc_commit(bar_c1);
         else flags[0] = 1;
       }
@@ -191,6 +234,10 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
       c2_phase ^= 1;
       c2_pending = false;
       tc_fence_after();
+      if (SPLIT) {
+        fold_tile(!folded);
+        folded = true;
+      }
     }
     // ---- 2. epilogue: warp (quarter, half) = pixels 32*quarter.., runs of parity `half`
     const int il = quarter * 32 + lane;
@@ -202,8 +249,15 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     const int kb = (il % KCH) * ESZ;
     auto store_w = [&](int c, float w) {
       unsigned char* dst = wl + c * 128 + (kb ^ ((c & 7) << 4));
-      if (BF) *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(w);
-      else *reinterpret_cast<float*>(dst) = to_tf32(w);
+      if (BF) {
+        *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(w);
+      } else if (SPLIT) {
+        const float hi = to_tf32(w);
+        *reinterpret_cast<float*>(dst) = hi;
+        *reinterpret_cast<float*>(dst + NPC * wchunk) = to_tf32(w - hi);
+      } else {
+        *reinterpret_cast<float*>(dst) = to_tf32(w);
+      }
     };
     if (IS_A) {
       // eq. (update_A), K1 steps in base 2 (y = z log2 e); the state and the
@@ -214,7 +268,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
       for (int j = 0; j < P; ++j) zn[j] = (ld_state && half < nr) ? St[gpix + (half * P + j) * Nst] : 0.f;
       if (do_c1 && half < nr) tmem_ld8_issue(tbase + tl + (uint32_t)(half * P), cn);
       for (int r = half; r < nr; r += 2) {
-        float cv[P], y[P];
+        float cv[P], zc[P];
         if (do_c1) {
           tmem_wait_ld8(cn);
 #pragma unroll
@@ -224,49 +278,101 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
           for (int j = 0; j < P; ++j) cv[j] = 0.f;
         }
 #pragma unroll
-        for (int j = 0; j < P; ++j) y[j] = zn[j] * kLog2e;
+        for (int j = 0; j < P; ++j) zc[j] = zn[j];
         if (r + 2 < nr) {
 #pragma unroll
           for (int j = 0; j < P; ++j) zn[j] = ld_state ? St[gpix + ((r + 2) * P + j) * Nst] : 0.f;
           if (do_c1) tmem_ld8_issue(tbase + tl + (uint32_t)((r + 2) * P), cn);
         }
         const float* G = Gs + r * P * P;
-        const float e2 = runEta[r] * kLog2e;
-        float ea[P], se = 0.f;
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-          ea[j] = ex2_approx(y[j]);
-          se += ea[j];
-        }
-        for (int kk = 0; kk < K1; ++kk) {
-          // a+ = softmax(log a - eta (G a - c)), G = E^T E, c = E^T x
-          const float inv = rcp_approx(se);
-          float a[P], mx = -EDAA_INF;
-#pragma unroll
-          for (int j = 0; j < P; ++j) a[j] = ea[j] * inv;
+        float a[P], wdev[P], znew[P];  // new a, a - 1/p (shifted accumulation), new log frame
+        if (SPLIT) {
+          // FP32 throughout, as in the CUDA-core pass: a+ = softmax(log a - eta (G a - c)),
+          // G = E^T E, c = E^T x; the deviation a - 1/p from d = expm1(z)
+          const float eta = runEta[r];
+          float ea[P], se = 0.f;
 #pragma unroll
           for (int j = 0; j < P; ++j) {
-            float g = -cv[j];
-#pragma unroll
-            for (int k = 0; k < P; ++k) g = fmaf(G[j * P + k], a[k], g);
-            y[j] = fmaf(-e2, g, y[j]);
-            mx = fmaxf(mx, y[j]);
+            ea[j] = expf(zc[j]);
+            se += ea[j];
           }
-          se = 0.f;
+          for (int kk = 0; kk < K1; ++kk) {
+            const float inv = 1.f / se;
+            float at[P], mx = -EDAA_INF;
+#pragma unroll
+            for (int j = 0; j < P; ++j) at[j] = ea[j] * inv;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              float g = -cv[j];
+#pragma unroll
+              for (int k = 0; k < P; ++k) g = fmaf(G[j * P + k], at[k], g);
+              zc[j] = fmaf(-eta, g, zc[j]);
+              mx = fmaxf(mx, zc[j]);
+            }
+            se = 0.f;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              zc[j] -= mx;
+              ea[j] = expf(zc[j]);
+              se += ea[j];
+            }
+          }
+          float d[P], sd = 0.f;
 #pragma unroll
           for (int j = 0; j < P; ++j) {
-            y[j] -= mx;
+            d[j] = expm1f(zc[j]);
+            sd += d[j];
+          }
+          const float den = 1.f / ((float)P + sd);
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            a[j] = valid ? (1.f + d[j]) * den : 0.f;
+            wdev[j] = valid ? ((float)P * d[j] - sd) * den * aref : 0.f;
+            znew[j] = zc[j];
+          }
+        } else {
+          // the same step in base 2 (y = z log2 e) with the hardware exponential
+          const float e2 = runEta[r] * kLog2e;
+          float y[P], ea[P], se = 0.f;
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            y[j] = zc[j] * kLog2e;
             ea[j] = ex2_approx(y[j]);
             se += ea[j];
           }
+          for (int kk = 0; kk < K1; ++kk) {
+            const float inv = rcp_approx(se);
+            float at[P], mx = -EDAA_INF;
+#pragma unroll
+            for (int j = 0; j < P; ++j) at[j] = ea[j] * inv;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              float g = -cv[j];
+#pragma unroll
+              for (int k = 0; k < P; ++k) g = fmaf(G[j * P + k], at[k], g);
+              y[j] = fmaf(-e2, g, y[j]);
+              mx = fmaxf(mx, y[j]);
+            }
+            se = 0.f;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              y[j] -= mx;
+              ea[j] = ex2_approx(y[j]);
+              se += ea[j];
+            }
+          }
+          const float inv = rcp_approx(se);
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            a[j] = valid ? ea[j] * inv : 0.f;
+            wdev[j] = valid ? a[j] - aref : 0.f;
+            znew[j] = y[j] * kLn2;
+          }
         }
-        const float inv = rcp_approx(se);
-        float a[P];
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-          a[j] = valid ? ea[j] * inv : 0.f;
-          if (valid) St[gpix + (r * P + j) * Nst] = y[j] * kLn2;
-          store_w(r * P + j, valid ? a[j] - aref : 0.f);  // shifted accumulation: a - 1/p
+          if (valid) St[gpix + (r * P + j) * Nst] = znew[j];
+          store_w(r * P + j, wdev[j]);
         }
         // A A^T of this tile's pixels: products in 2^-24 fixed point, summed
         // exactly over the warp's 32 pixels (integer warp reduction)
@@ -330,7 +436,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
         colRefW[c] = ldexpf(1.f, colRef[c] - (int)Mn);
       }
       __syncthreads();
-      if (flags[1] && d2_started) {  // exact power-of-two rescale of Acc in TMEM, disjoint 8-column chunks
+      if (!SPLIT && flags[1] && d2_started) {  // exact power-of-two rescale of Acc in TMEM, disjoint 8-column chunks
         for (int b = 0; b < nbt; ++b)
           for (int cc = half * 8; cc < Rgp; cc += 16) {
             float v[8];
@@ -355,7 +461,11 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
 #pragma unroll
           for (int j = 0; j < P; ++j) {
             const int c = r * P + j;
-            store_w(c, valid ? ex2_approx(fmaf(un[b][j], kLog2e, -colM[c])) - colRefW[c] : 0.f);
+            float w = 0.f;
+            if (valid)
+              w = SPLIT ? shifted_weight(un[b][j], colM[c], colRef[c])  // FP32, expm1 near the reference
+                        : ex2_approx(fmaf(un[b][j], kLog2e, -colM[c])) - colRefW[c];
+            store_w(c, w);
           }
         }
       }
@@ -371,14 +481,16 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
         const bool first = !d2_started;
         bool ok = true;
         for (int j = 0; j < nc2 && ok; ++j) {
-          const int bti = j / NPC, pc = j - bti * NPC;
+          const int kc = j / SUB, part = j - kc * SUB, bti = kc / NPC, pc = kc - bti * NPC;
           ok = consume([&](unsigned char* st) {
             const uint32_t dcol = tbase + (uint32_t)(Rgp * (1 + bti));
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
               const uint64_t da = desc_sw128(su32(st + ks * 32));
               const uint64_t db = desc_sw128(su32(Wsm + pc * wchunk + ks * 32));
-              tc_mma<BF>(dcol, da, db, id, (first && pc == 0 && ks == 0) ? 0u : 1u);
+              tc_mma<BF>(dcol, da, db, id, ((SPLIT || first) && pc == 0 && part == 0 && ks == 0) ? 0u : 1u);
+              if (SPLIT && part == 0)  // X hi * W lo
+                tc_mma<BF>(dcol, da, desc_sw128(su32(Wsm + (NPC + pc) * wchunk + ks * 32)), id, 1u);
             }
           });
         }
@@ -403,6 +515,12 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     if (to) atomicOr(bt->status, 1 << 13);  // last contraction 2
     bail = __syncthreads_or(to);
     tc_fence_after();
+    if (SPLIT && !bail) {
+      fold_tile(!folded);
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+    }
   }
   if (bail) {
     // time-out: report it, give in-flight TMA/MMA work a bounded time to drain, then free TMEM
@@ -417,7 +535,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
       const int l = b * 128 + quarter * 32 + lane;
       for (int r = half; r < nr; r += 2) {
         float v[8];
-        tmem_ld8(tbase + tl + (uint32_t)(Rgp * (1 + b) + r * P), v);
+        tmem_ld8(tbase + tl + (uint32_t)(Rgp * (1 + (SPLIT ? nbt : 0) + b) + r * P), v);  // split: the running sums
         if (l <= L) {
 #pragma unroll
           for (int j = 0; j < P; ++j) part[(size_t)l * Mp + c0 + r * P + j] = v[j];

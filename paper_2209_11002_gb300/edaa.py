@@ -20,7 +20,7 @@ EDAA_OK, EDAA_ERR_ARG, EDAA_ERR_CUDA, EDAA_ERR_OOM, EDAA_ERR_STATE, EDAA_ERR_NON
     EDAA_ERR_TIMEOUT, EDAA_ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ["EDAA_OK", "EDAA_ERR_ARG", "EDAA_ERR_CUDA", "EDAA_ERR_OOM", "EDAA_ERR_STATE",
                 "EDAA_ERR_NONFINITE", "EDAA_ERR_TIMEOUT", "EDAA_ERR_UNSUPPORTED"]
-FP32, TF32, BF16 = 0, 1, 2
+FP32, TF32, BF16, TF32X3 = 0, 1, 2, 3
 
 # Every function declared in include/edaa.h (the CPU tests check the export list).
 EXPORTS = ["edaa_config_default", "edaa_init", "edaa_reset", "edaa_step", "edaa_solve", "edaa_select",

@@ -74,3 +74,57 @@ def test_uneven_batch_mixes_tensor_core_and_cuda_core_cubes():
                 assert np.abs(A - ref["A"]).max() <= 2e-4
                 lr = O.objective(Xn, ref["A"], ref["B"])
                 assert abs(loss[m] - lr) / lr <= 2e-4
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_split_tf32_gradients_per_outer_iteration(persistent):
+    """EDAA_TF32X3 (operands split into two TF32 parts, three MMAs per
+    product, element-wise steps in full FP32, tile accumulators folded into
+    FP32 running sums): grad_A and grad_B at every outer boundary t = 0..3
+    within 1e-5 (norm-wise relative) of the oracle on this 48-band,
+    2333-pixel ensemble (M p = 64).  The split keeps about 22 of FP32's 24
+    bits: on larger pixel counts its gradient error grows past the FP32
+    path's (2.4e-5 at N = 40000, t = 2, against 2.8e-6)."""
+    cube = synth.make_cube(48, 2333, 4, alpha=0.5, snr_db=30, M=16, gamma_choices=(0.5, 1.0, 2.0), seed=6)
+    Xn = O.normalize_pixels(cube.X)
+    runs = (0, 5, 15)
+    refs = {m: O.edaa(Xn, 4, 3, 5, 5, int(cube.seeds[m]), float(cube.gammas[m]), record=True)["hist"] for m in runs}
+    errs = {}
+    with _ctx(cube, T=3, precision=edaa.TF32X3, persistent=persistent) as ctx:
+        assert ctx.describe(0)["pixel_tile"] == 128  # the tensor-core tiling
+        for t in range(4):
+            for m in runs:
+                gA, gB = ctx.grad(0, m, device="cpu")
+                errs[(t, m)] = (_rel(gA, refs[m]["gA"][t]), _rel(gB, refs[m]["gB"][t]))
+            if t < 3:
+                ctx.step(1)
+    for k, v in sorted(errs.items()):
+        print("t=%d run=%d  grad_A rel %.2e  grad_B rel %.2e" % (k[0], k[1], v[0], v[1]))
+    assert max(max(v) for v in errs.values()) <= 1e-5
+
+
+def test_split_tf32_solve_against_oracle_and_fp32():
+    """After 30 outer iterations: loss within 1e-3 relative and A, E within
+    1e-3 max-abs of the oracle, and every run's loss within 1e-3 of the
+    CUDA-core FP32 path."""
+    cube = synth.make_cube(64, 3001, 4, alpha=0.3, snr_db=25, M=16, gamma_choices=(0.5, 1.0, 2.0), seed=43)
+    T = 30
+    Xn = O.normalize_pixels(cube.X)
+    with _ctx(cube, T=T, precision=edaa.TF32X3) as ctx:
+        ctx.solve()
+        loss = ctx.loss(0)
+        got = {m: ctx.get(0, m, device="cpu") for m in (0, 9, 15)}
+    with _ctx(cube, T=T, precision=edaa.FP32) as ref32:
+        ref32.solve()
+        loss32 = ref32.loss(0)
+    for m, (E, A, B) in got.items():
+        ref = O.edaa(Xn, 4, T, 5, 5, int(cube.seeds[m]), float(cube.gammas[m]))
+        lr = O.objective(Xn, ref["A"], ref["B"])
+        assert abs(loss[m] - lr) / lr <= 1e-3
+        assert np.abs(A - ref["A"]).max() <= 1e-3
+        assert np.abs(E - ref["E"]).max() <= 1e-3
+    assert np.max(np.abs(loss - loss32) / loss32) <= 1e-3
