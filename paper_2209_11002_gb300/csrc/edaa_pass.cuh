@@ -73,6 +73,13 @@ __device__ __forceinline__ int ref_exponent(const CubeDev& cd, int m, int c) {
   return (int)rint(t);
 }
 
+// The same with 2^-Mn precomputed (p2) for the common case k = 0.
+__device__ __forceinline__ float shifted_weight(float u, float Mn, int k);
+__device__ __forceinline__ float shifted_weight_p2(float u, float Mn, float p2, int k) {
+  if (k != 0) return shifted_weight(u, Mn, k);
+  return (fabsf(u) < 1.f) ? expm1f(u) * p2 : exp2f(fmaf(u, kLog2e, -Mn)) - p2;
+}
+
 // Shifted weight of logit u in the power-of-two frame Mn with reference 2^k:
 // e^u 2^-Mn - 2^(k-Mn).  Near the reference the difference is formed by
 // expm1 and is exact to rounding.
@@ -206,6 +213,8 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
   float* colM = colLse + sm.RgS4;
   int* colKey = reinterpret_cast<int*>(colM + sm.RgS4);
   int* colRef = colKey + sm.RgS4;  // B: reference exponent k of the shifted weights
+  float* colP2 = reinterpret_cast<float*>(colRef + sm.RgS4);  // B: 2^-Mn of the current tile's frame
+  float* colMn = colP2 + sm.RgS4;                              // B: the current tile's frame Mn
   float* runEta = smem + sm.off_run;
   const int RgS4 = sm.RgS4, RgSo = sm.RgSo, RgW = sm.RgW;
 
@@ -290,6 +299,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
 #pragma unroll
         for (int j = 0; j < P; ++j) cr[s][q][j] = 0.f;
     if (need_panel && (!IS_A || K1 > 0)) {
+#pragma unroll 2
       for (int l = 0; l < Lr; l += 4) {
         float4 xv[SPTM];
 #pragma unroll
@@ -322,6 +332,60 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
     }
 
     if (IS_A) {
+      // eq. (update_A) in softmax form, a+ = softmax(log a - eta (G a - c)),
+      // for every (pixel, run) slot of this thread.  The K1 loop is outermost
+      // so that the slots' independent chains interleave.  Inactive slots
+      // (beyond SPT, RQ1 or the group's runs) compute on zeros with clamped
+      // indices and store nothing.
+      float z[SPTM][RQ1M][P], ea[SPTM][RQ1M][P], se[SPTM][RQ1M];
+#pragma unroll
+      for (int s = 0; s < SPTM; ++s) {
+        const int il = lane + 32 * (wp + WP1 * s);
+        const bool valid = s < SPT && il < ni;
+#pragma unroll
+        for (int q = 0; q < RQ1M; ++q) {
+          const int r = wr + WR1 * q;
+          const bool act = valid && q < RQ1 && r < nr;
+          // z = log a - max_j log a (max-normalised log abundances; 0 for uniform a)
+          se[s][q] = 0.f;
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            z[s][q][j] = (init || !act) ? 0.f : Ss[il * RgSo + r * P + j];
+            ea[s][q][j] = expf(z[s][q][j]);
+            se[s][q] += ea[s][q][j];
+          }
+        }
+      }
+      for (int kk = 0; kk < K1; ++kk) {
+#pragma unroll
+        for (int s = 0; s < SPTM; ++s)
+#pragma unroll
+          for (int q = 0; q < RQ1M; ++q) {
+            const int r = wr + WR1 * q;
+            const int rr = (q < RQ1 && r < nr) ? r : 0;
+            const float* G = Gs + rr * P * P;
+            const float eta = runEta[rr];
+            const float inv = 1.f / se[s][q];
+            float a[P], mx = -EDAA_INF;
+#pragma unroll
+            for (int j = 0; j < P; ++j) a[j] = ea[s][q][j] * inv;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              float g = -cr[s][q][j];
+#pragma unroll
+              for (int k = 0; k < P; ++k) g = fmaf(G[j * P + k], a[k], g);
+              z[s][q][j] = fmaf(-eta, g, z[s][q][j]);
+              mx = fmaxf(mx, z[s][q][j]);
+            }
+            se[s][q] = 0.f;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              z[s][q][j] -= mx;
+              ea[s][q][j] = expf(z[s][q][j]);
+              se[s][q] += ea[s][q][j];
+            }
+          }
+      }
 #pragma unroll
       for (int s = 0; s < SPTM; ++s) {
         if (s >= SPT) continue;
@@ -331,42 +395,6 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
         for (int q = 0; q < RQ1M; ++q) {
           const int r = wr + WR1 * q;
           if (!(q < RQ1 && r < nr)) continue;
-          // z = log a - max_j log a (max-normalised log abundances; 0 for uniform a)
-          float z[P];
-#pragma unroll
-          for (int j = 0; j < P; ++j) z[j] = init ? 0.f : (valid ? Ss[il * RgSo + r * P + j] : 0.f);
-          const float* G = Gs + r * P * P;
-          const float eta = runEta[r];
-          float ea[P];
-          float se = 0.f;
-#pragma unroll
-          for (int j = 0; j < P; ++j) {
-            ea[j] = expf(z[j]);
-            se += ea[j];
-          }
-          for (int kk = 0; kk < K1; ++kk) {
-            // eq. (update_A) in softmax form: a+ = softmax(log a - eta (G a - c))
-            const float inv = 1.f / se;
-            float a[P];
-#pragma unroll
-            for (int j = 0; j < P; ++j) a[j] = ea[j] * inv;
-            float mx = -EDAA_INF;
-#pragma unroll
-            for (int j = 0; j < P; ++j) {
-              float g = -cr[s][q][j];
-#pragma unroll
-              for (int k = 0; k < P; ++k) g = fmaf(G[j * P + k], a[k], g);
-              z[j] = fmaf(-eta, g, z[j]);
-              mx = fmaxf(mx, z[j]);
-            }
-            se = 0.f;
-#pragma unroll
-            for (int j = 0; j < P; ++j) {
-              z[j] -= mx;
-              ea[j] = expf(z[j]);
-              se += ea[j];
-            }
-          }
           // a_j = e^{z_j} / sum_k e^{z_k}.  The accumulated deviation a_j - 1/p is
           // formed from d = expm1(z), exact to float rounding near uniform a
           // (where a_j - 1/p itself is small): a_j - 1/p = (p d_j - sd) / (p (p + sd)).
@@ -374,7 +402,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
           float sd = 0.f;
 #pragma unroll
           for (int j = 0; j < P; ++j) {
-            d[j] = expm1f(z[j]);
+            d[j] = expm1f(z[s][q][j]);
             sd += d[j];
           }
           const float den = 1.f / ((float)P + sd);
@@ -387,7 +415,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
           }
           if (valid) {
 #pragma unroll
-            for (int j = 0; j < P; ++j) Ss[il * RgSo + r * P + j] = z[j];
+            for (int j = 0; j < P; ++j) Ss[il * RgSo + r * P + j] = z[s][q][j];
           }
 #pragma unroll
           for (int h = 0; h < P4 / 4; ++h)
@@ -438,6 +466,12 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
         }
       }
       __syncthreads();
+      for (int c = tid; c < RgS4; c += kThreads) {  // the tile's power-of-two frame of each column
+        const float Mn = fmaxf(colM[c], tile_exp(colKey[c]));
+        colMn[c] = Mn;
+        colP2[c] = Mn == -EDAA_INF ? 0.f : ldexpf(1.f, -(int)Mn);
+      }
+      __syncthreads();
 #pragma unroll
       for (int s = 0; s < SPTM; ++s) {
         if (s >= SPT) continue;
@@ -453,9 +487,8 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
             w[j] = 0.f;
             if (j < P && valid) {
               const int c = r * P4 + j;
-              const float Mn = fmaxf(colM[c], tile_exp(colKey[c]));  // power-of-two frame
               // w = e^u 2^-Mn minus the reference weight 2^(k-Mn) (k = 0: uniform b)
-              w[j] = shifted_weight(ur[s][q][j], Mn, colRef[c]);
+              w[j] = shifted_weight_p2(ur[s][q][j], colMn[c], colP2[c], colRef[c]);
             }
           }
           if (valid) {
@@ -495,17 +528,21 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
         }
       }
     }
+    bool act2[RQ2M];
+#pragma unroll
+    for (int q = 0; q < RQ2M; ++q) act2[q] = q < RQ2 && wr2 + WR2 * q < nr;
+    const bool last_in = lane + 32 * (LT - 1) <= L;  // bands of the earlier groups are all <= L
+#pragma unroll 2
     for (int i = wp2; i < ni; i += WP2) {
+      const float* xr = Xs + i * Ls + lane;
       float xv[LT];
 #pragma unroll
-      for (int k = 0; k < LT; ++k) {
-        const int l = lane + 32 * k;
-        xv[k] = (l <= L) ? Xs[i * Ls + l] : 0.f;
-      }
+      for (int k = 0; k < LT - 1; ++k) xv[k] = xr[32 * k];
+      xv[LT - 1] = last_in ? xr[32 * (LT - 1)] : 0.f;
 #pragma unroll
       for (int q = 0; q < RQ2M; ++q) {
+        if (!act2[q]) continue;
         const int r = wr2 + WR2 * q;
-        if (!(q < RQ2 && r < nr)) continue;
         float w[P4];
         load_p4<P>(Ws + i * RgW + r * P4, w);
 #pragma unroll
