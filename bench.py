@@ -104,6 +104,7 @@ def unrolled_workload(args, rank, world):
         step()
     torch.cuda.synchronize()
     ms = []
+    torch.cuda.nvtx.range_push("timed")  # lets ncu --nvtx-include "timed/" pick the timed launches
     for _ in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -111,6 +112,7 @@ def unrolled_workload(args, rank, world):
         e1.record()
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
+    torch.cuda.nvtx.range_pop()
     t = max_over_ranks(sum(ms), world, "cuda")
     run_steps = T * (K1 + K2)
     line = {"metric": "unrolled EDAA forward+backward run-steps/s", "value": whole_job_rate(run_steps * args.steps,

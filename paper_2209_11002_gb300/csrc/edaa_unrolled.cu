@@ -103,7 +103,11 @@ __global__ void __launch_bounds__(kT) k_xw(const float* __restrict__ X, int L, i
 // ---- out[i*P + j] = scale * sum_l x_i[l] panel[l*P + j]  (warp per pixel)
 template <int P>
 __global__ void __launch_bounds__(kT) k_xdot(const float* __restrict__ X, int L, int N,
-                                           const float* __restrict__ panel, float scale, float* __restrict__ out) {
+                                           const float* __restrict__ panel, float scale0,
+                                           const float* __restrict__ smul, float* __restrict__ out) {
+  // scale = scale0 times the step size at smul when given (read on the device, so that a
+  // captured graph serves every call)
+  const float scale = smul ? scale0 * *smul : scale0;
   extern __shared__ float sp[];  // L * P
   for (int e = threadIdx.x; e < L * P; e += kT) sp[e] = panel[e];
   __syncthreads();
@@ -133,8 +137,9 @@ __global__ void __launch_bounds__(kT) k_xdot(const float* __restrict__ X, int L,
 // ---- Xbar_i[l] += s1 sum_j L1[l,j] R1[i,j] + s2 sum_j L2[l,j] R2[i,j]  (rank-p updates of dX)
 template <int P>
 __global__ void __launch_bounds__(kT) k_rank(float* __restrict__ Xbar, int L, int N, const float* __restrict__ L1,
-                                           const float* __restrict__ R1, float s1, const float* __restrict__ L2,
-                                           const float* __restrict__ R2, float s2) {
+                                           const float* __restrict__ R1, float s1m, const float* __restrict__ L2,
+                                           const float* __restrict__ R2, float s2m, const float* __restrict__ smul) {
+  const float s1 = smul ? s1m * *smul : s1m, s2 = smul ? s2m * *smul : s2m;
   extern __shared__ float sp[];  // 2 * L * P
   float* l1 = sp;
   float* l2 = sp + L * P;
@@ -194,15 +199,42 @@ __global__ void __launch_bounds__(kT) k_pred(const float* __restrict__ w1, const
 }
 
 // fixed-order merge of per-block partials (FP64), optional scale and float copy
-__global__ void k_merge(const float* __restrict__ part, int nb, int n, double scale, double* outd, float* outf) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += (double)part[(size_t)b * n + e];
-  s *= scale;
-  if (outd) outd[e] = s;
-  if (outf) outf[e] = (float)s;
+// Float-float accumulation (Knuth's TwoSum: s + e == hi + x exactly).  This
+// GPU's FP64 rate is a small fraction of its FP32 rate; two-float sums keep
+// about 44 bits at FP32 speed.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += e;
 }
+// butterfly over the warp in a fixed order (lane 0 ends with the total)
+__device__ __forceinline__ double ff_warp_total(float hi, float lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    ff_add(hi, lo, h2);
+    lo += l2;
+  }
+  return (double)hi + (double)lo;
+}
+
+// out[e] = scale * sum_b part[b][e]: one warp per output, lanes over the
+// partials (fixed order, float-float)
+__global__ void k_merge(const float* __restrict__ part, int nb, int n, double scale, double* outd, float* outf) {
+  const int lane = threadIdx.x & 31;
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (e >= n) return;  // whole warps leave together
+  float hi = 0.f, lo = 0.f;
+  for (int b = lane; b < nb; b += 32) ff_add(hi, lo, part[(size_t)b * n + e]);
+  const double s = ff_warp_total(hi, lo) * scale;
+  if (lane == 0) {
+    if (outd) outd[e] = s;
+    if (outf) outf[e] = (float)s;
+  }
+}
+inline int merge_blocks(int n) { return (n + 7) / 8; }  // 8 warps (outputs) per 256-thread block
 
 // ---- column log-sum-exp over pixels (online per thread, fixed-order merges)
 __global__ void __launch_bounds__(kT) k_lse_part(const float* __restrict__ u, int N, int P, float* __restrict__ part) {
@@ -242,16 +274,20 @@ __global__ void __launch_bounds__(kT) k_lse_part(const float* __restrict__ u, in
 }
 
 __global__ void k_lse_merge(const float* __restrict__ part, int nb, int P, double* __restrict__ lse) {
-  const int j = threadIdx.x;
+  // one warp per column: m = max of the block maxima, then sum_b s_b e^(m_b - m)
+  const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
   if (j >= P) return;
-  double m = -INFINITY;
-  for (int b = 0; b < nb; ++b) m = fmax(m, (double)part[((size_t)b * P + j) * 2]);
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) {
-    const double mb = part[((size_t)b * P + j) * 2];
-    if (mb != -INFINITY) s += (double)part[((size_t)b * P + j) * 2 + 1] * exp(mb - m);
+  float m = -INFINITY;
+  for (int b = lane; b < nb; b += 32) m = fmaxf(m, part[((size_t)b * P + j) * 2]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  float hi = 0.f, lo = 0.f;
+  for (int b = lane; b < nb; b += 32) {
+    const float mb = part[((size_t)b * P + j) * 2];
+    if (mb != -INFINITY) ff_add(hi, lo, part[((size_t)b * P + j) * 2 + 1] * expf(mb - m));
   }
-  lse[j] = m + log(s);
+  const double sum = ff_warp_total(hi, lo);
+  if (lane == 0) lse[j] = (double)m + log(sum);
 }
 
 // l -= lse (per column); b = exp(l)
@@ -281,12 +317,15 @@ __global__ void k_fill(float* __restrict__ z, int n, float v) {
 
 // G = E^T E (P x P) from the FP64 E, one block
 __global__ void k_gram(const double* __restrict__ E, int L, int P, float* __restrict__ G) {
-  const int e = threadIdx.x;
+  // one warp per entry (j, k) of G = E^T E, lanes over the bands
+  const int lane = threadIdx.x & 31, e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (e >= P * P) return;
   const int j = e / P, k = e % P;
   double s = 0.0;
-  for (int l = 0; l < L; ++l) s += E[l * P + j] * E[l * P + k];
-  G[e] = (float)s;
+  for (int l = lane; l < L; l += 32) s += E[l * P + j] * E[l * P + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) G[e] = (float)s;
 }
 
 // one pixel's A-phase: K1 mirror steps; keeps the iterates when `rec` is set
@@ -312,8 +351,9 @@ __device__ __forceinline__ void a_steps(float* z, const float* c, const float* G
     for (int j = 0; j < P; ++j) zs[K1][j] = z[j];
 }
 
-__global__ void k_a_fwd(const float* __restrict__ C, const float* __restrict__ Gg, float eta, int K1, int N, int P,
-                        const float* __restrict__ zin, float* __restrict__ zout) {
+__global__ void k_a_fwd(const float* __restrict__ C, const float* __restrict__ Gg, const float* __restrict__ etap,
+                        int K1, int N, int P, const float* __restrict__ zin, float* __restrict__ zout) {
+  const float eta = *etap;
   __shared__ float G[kMaxP * kMaxP];
   if (threadIdx.x < P * P) G[threadIdx.x] = Gg[threadIdx.x];
   __syncthreads();
@@ -341,9 +381,10 @@ __global__ void k_dev(const float* __restrict__ b, const float* __restrict__ a, 
 }
 
 // l' = l - eta g (unnormalised)
-__global__ void k_axpy(const float* __restrict__ l, const float* __restrict__ g, float eta, int n, float* __restrict__ o) {
+__global__ void k_axpy(const float* __restrict__ l, const float* __restrict__ g, const float* __restrict__ etap, int n,
+                       float* __restrict__ o) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n) o[e] = fmaf(-eta, g[e], l[e]);
+  if (e < n) o[e] = fmaf(-*etap, g[e], l[e]);
 }
 
 // zeta = lbar - bp o s
@@ -381,10 +422,11 @@ __global__ void k_zbar(const float* __restrict__ a, const float* __restrict__ Ab
 
 // A-phase adjoint per pixel: recompute the K1 iterates from z_t, then reverse.
 // Writes zbar (adjoint of z_t), Cbar; block partials of Gbar (P*P) and d eta (1).
-__global__ void __launch_bounds__(kT) k_a_bwd(const float* __restrict__ C, const float* __restrict__ Gg, float eta,
-                                            int K1, int N, int P, const float* __restrict__ zt,
-                                            float* __restrict__ zbar, float* __restrict__ Cbar,
-                                            float* __restrict__ part) {
+__global__ void __launch_bounds__(kT) k_a_bwd(const float* __restrict__ C, const float* __restrict__ Gg,
+                                            const float* __restrict__ etap, int K1, int N, int P,
+                                            const float* __restrict__ zt, float* __restrict__ zbar,
+                                            float* __restrict__ Cbar, float* __restrict__ part) {
+  const float eta = *etap;
   __shared__ float G[kMaxP * kMaxP];
   __shared__ float red[kT];
   if (threadIdx.x < P * P) G[threadIdx.x] = Gg[threadIdx.x];
@@ -507,16 +549,20 @@ struct Buf {
 
 struct edaa_unrolled {
   int L, N, P, T, K1, K2;
-  cudaStream_t s;
+  cudaStream_t caller = nullptr;  // the stream the caller orders our work on
+  cudaStream_t s = nullptr;       // our own stream (a captured graph needs one that is not the legacy default)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t g_fwd = nullptr, g_bwd = nullptr;
   eu::Buf buf;
   float *X, *zck, *lck, *z, *l, *b, *a, *C, *g, *d, *part, *G, *W, *E32, *R32;
   double *Ed, *Wd, *Rd, *lse, *scr;
   float *ls, *gs;              // recompute storage: (K2+1) x N x P logits, K2 x N x P B-gradients
   float *Rs;                   // K2 x L x P
   double* deta;                // 2T: d eta_A, d eta_B
+  float* eta;                  // 2T on the device: eta_A[t], then eta_B[t]
+  float* dAin;                 // p x N: d(loss)/dA_hat for the backward (zeros when absent)
   float *lbar, *zbar, *Abar, *Xbar, *zeta, *Dbar, *bp, *tmp, *P32, *Eb32, *Wb32, *Gb32;
   double *sd, *XCd, *Gbd, *Pd, *Wbd, *eta_scr;
-  std::vector<double> etaA, etaB;
   bool have_forward = false;
 };
 
@@ -549,25 +595,26 @@ cudaError_t xw(edaa_unrolled* u, const float* w, double* outd, float* outf, doub
     return cudaGetLastError();
   });
   if (e != cudaSuccess) return e;
-  k_merge<<<g1(u->L * u->P), 256, 0, u->s>>>(u->part, nb, u->L * u->P, scale, outd, outf);
+  k_merge<<<merge_blocks(u->L * u->P), 256, 0, u->s>>>(u->part, nb, u->L * u->P, scale, outd, outf);
   return cudaGetLastError();
 }
 
-cudaError_t xdot(edaa_unrolled* u, const float* panel, float scale, float* out) {
+// out = scale * X panel, times the step size at smul when given
+cudaError_t xdot(edaa_unrolled* u, const float* panel, float scale, float* out, const float* smul = nullptr) {
   const int nb = nb_pix(u->N);
   return by_p(u->P, [&](auto pc) {
     constexpr int PP = decltype(pc)::value;
-    k_xdot<PP><<<nb, kT, u->L * PP * sizeof(float), u->s>>>(u->X, u->L, u->N, panel, scale, out);
+    k_xdot<PP><<<nb, kT, u->L * PP * sizeof(float), u->s>>>(u->X, u->L, u->N, panel, scale, smul, out);
     return cudaGetLastError();
   });
 }
 
 cudaError_t rank(edaa_unrolled* u, const float* L1, const float* R1, float s1, const float* L2, const float* R2,
-                 float s2) {
+                 float s2, const float* smul = nullptr) {
   const int nb = nb_pix(u->N);
   return by_p(u->P, [&](auto pc) {
     constexpr int PP = decltype(pc)::value;
-    k_rank<PP><<<nb, kT, 2 * u->L * PP * sizeof(float), u->s>>>(u->Xbar, u->L, u->N, L1, R1, s1, L2, R2, s2);
+    k_rank<PP><<<nb, kT, 2 * u->L * PP * sizeof(float), u->s>>>(u->Xbar, u->L, u->N, L1, R1, s1, L2, R2, s2, smul);
     return cudaGetLastError();
   });
 }
@@ -577,7 +624,7 @@ cudaError_t pred(edaa_unrolled* u, const float* w1, const float* w2, int mode, d
   const int nb = nb_thr(u->N);
   const int n_out = mode == 0 ? u->P * u->P : u->P;
   k_pred<<<nb, kT, 0, u->s>>>(w1, w2, u->N, u->P, mode, u->part);
-  k_merge<<<g1(n_out), 256, 0, u->s>>>(u->part, nb, n_out, scale, outd, outf);
+  k_merge<<<merge_blocks(n_out), 256, 0, u->s>>>(u->part, nb, n_out, scale, outd, outf);
   return cudaGetLastError();
 }
 
@@ -585,7 +632,7 @@ cudaError_t pred(edaa_unrolled* u, const float* w1, const float* w2, int mode, d
 cudaError_t normalise_logits(edaa_unrolled* u, float* l, float* b) {
   const int nb = nb_thr(u->N);
   k_lse_part<<<nb, kT, 0, u->s>>>(l, u->N, u->P, u->part);
-  k_lse_merge<<<1, 32, 0, u->s>>>(u->part, nb, u->P, u->lse);
+  k_lse_merge<<<1, 32 * u->P, 0, u->s>>>(u->part, nb, u->P, u->lse);
   k_shift_exp<<<g1(u->N * u->P), 256, 0, u->s>>>(l, u->lse, u->N, u->P, b);
   return cudaGetLastError();
 }
@@ -608,9 +655,9 @@ cudaError_t outer_forward(edaa_unrolled* u, int t, bool rec) {
   cudaError_t e;
   const int n = u->N * u->P;
   if ((e = make_E(u, u->b)) != cudaSuccess) return e;
-  k_gram<<<1, 64, 0, u->s>>>(u->Ed, u->L, u->P, u->G);
+  k_gram<<<(u->P * u->P + 7) / 8, 256, 0, u->s>>>(u->Ed, u->L, u->P, u->G);
   if ((e = xdot(u, u->E32, 1.f, u->C)) != cudaSuccess) return e;
-  k_a_fwd<<<g1(u->N), 256, 0, u->s>>>(u->C, u->G, (float)u->etaA[t], u->K1, u->N, u->P, u->z, u->z);
+  k_a_fwd<<<g1(u->N), 256, 0, u->s>>>(u->C, u->G, u->eta + t, u->K1, u->N, u->P, u->z, u->z);
   k_exp<<<g1(n), 256, 0, u->s>>>(u->z, n, u->a);
   if ((e = make_W(u, u->a)) != cudaSuccess) return e;
   if (rec) cudaMemcpyAsync(u->ls, u->l, n * 4, cudaMemcpyDeviceToDevice, u->s);
@@ -621,11 +668,134 @@ cudaError_t outer_forward(edaa_unrolled* u, int t, bool rec) {
       cudaMemcpyAsync(u->Rs + (size_t)k * u->L * u->P, u->R32, u->L * u->P * 4, cudaMemcpyDeviceToDevice, u->s);
       cudaMemcpyAsync(u->gs + (size_t)k * n, u->g, n * 4, cudaMemcpyDeviceToDevice, u->s);
     }
-    k_axpy<<<g1(n), 256, 0, u->s>>>(u->l, u->g, (float)u->etaB[t], n, u->l);
+    k_axpy<<<g1(n), 256, 0, u->s>>>(u->l, u->g, u->eta + u->T + t, n, u->l);
     if ((e = normalise_logits(u, u->l, u->b)) != cudaSuccess) return e;
     if (rec) cudaMemcpyAsync(u->ls + (size_t)(k + 1) * n, u->l, n * 4, cudaMemcpyDeviceToDevice, u->s);
   }
   return cudaGetLastError();
+}
+
+// The T outer iterations with their checkpoints, then E_hat (E32) and A_hat
+// (tmp, p x N).  Every input lives in the engine's buffers, so the sequence
+// is captured once and replayed.
+cudaError_t forward_body(edaa_unrolled* u) {
+  const int N = u->N, P = u->P, n = N * P;
+  cudaError_t e;
+  for (int t = 0; t < u->T; ++t) {
+    cudaMemcpyAsync(u->zck + (size_t)t * n, u->z, n * 4, cudaMemcpyDeviceToDevice, u->s);
+    cudaMemcpyAsync(u->lck + (size_t)t * n, u->l, n * 4, cudaMemcpyDeviceToDevice, u->s);
+    if ((e = outer_forward(u, t, false)) != cudaSuccess) return e;
+  }
+  cudaMemcpyAsync(u->zck + (size_t)u->T * n, u->z, n * 4, cudaMemcpyDeviceToDevice, u->s);
+  cudaMemcpyAsync(u->lck + (size_t)u->T * n, u->l, n * 4, cudaMemcpyDeviceToDevice, u->s);
+  if ((e = make_E(u, u->b)) != cudaSuccess) return e;
+  k_exp<<<g1(n), 256, 0, u->s>>>(u->z, n, u->a);
+  k_transpose_pn<<<g1(n), 256, 0, u->s>>>(u->a, N, P, u->tmp);
+  return cudaGetLastError();
+}
+
+// The reverse sweep: from d(loss)/dE_hat (Eb32) and d(loss)/dA_hat (dAin),
+// accumulates Xbar (dX) and deta (d eta_A, d eta_B).
+cudaError_t backward_body(edaa_unrolled* u) {
+  const int N = u->N, P = u->P, L = u->L, n = N * P, lp = L * P;
+  cudaError_t e;
+  cudaMemsetAsync(u->Xbar, 0, (size_t)N * L * 4, u->s);
+  cudaMemsetAsync(u->zbar, 0, n * 4, u->s);
+  // final state: b_T, a_T
+  cudaMemcpyAsync(u->l, u->lck + (size_t)u->T * n, n * 4, cudaMemcpyDeviceToDevice, u->s);
+  k_exp<<<g1(n), 256, 0, u->s>>>(u->l, n, u->b);
+  // E_hat = X B_T: Xbar += dE B^T; lbar = B o (X^T dE)
+  if ((e = rank(u, u->Eb32, u->b, 1.f, nullptr, nullptr, 0.f)) != cudaSuccess) return e;
+  if ((e = xdot(u, u->Eb32, 1.f, u->tmp)) != cudaSuccess) return e;
+  cudaMemsetAsync(u->lbar, 0, n * 4, u->s);
+  k_fma_inplace<<<g1(n), 256, 0, u->s>>>(u->lbar, u->b, u->tmp, n);
+  // A_hat = exp(z_T): the A-adjoint accumulator (pixel-major) starts at dA (p x N)
+  k_transpose_np<<<g1(n), 256, 0, u->s>>>(u->dAin, N, P, u->Abar);
+  cudaMemsetAsync(u->deta, 0, 2 * u->T * sizeof(double), u->s);
+  for (int t = u->T - 1; t >= 0; --t) {
+    // ---- recompute outer iteration t from its checkpoint
+    cudaMemcpyAsync(u->z, u->zck + (size_t)t * n, n * 4, cudaMemcpyDeviceToDevice, u->s);
+    cudaMemcpyAsync(u->l, u->lck + (size_t)t * n, n * 4, cudaMemcpyDeviceToDevice, u->s);
+    k_exp<<<g1(n), 256, 0, u->s>>>(u->l, n, u->b);
+    if ((e = outer_forward(u, t, true)) != cudaSuccess) return e;
+    // after it: z = z_{t+1}, a = exp(z_{t+1}), W = A A^T; ls[k], gs[k], Rs[k]
+    const float* etaA = u->eta + t;
+    const float* etaB = u->eta + u->T + t;
+    cudaMemsetAsync(u->Wbd, 0, 64 * 8, u->s);
+    cudaMemsetAsync(u->Wb32, 0, 64 * 4, u->s);
+    // ---- reverse the B-steps
+    for (int k = u->K2 - 1; k >= 0; --k) {
+      const float* lk = u->ls + (size_t)k * n;
+      const float* lk1 = u->ls + (size_t)(k + 1) * n;
+      k_exp<<<g1(n), 256, 0, u->s>>>(lk1, n, u->bp);
+      k_exp<<<g1(n), 256, 0, u->s>>>(lk, n, u->b);
+      // s = column sums of lbar; zeta = lbar - B' diag(s)
+      if ((e = pred(u, u->lbar, nullptr, 1, u->sd, nullptr)) != cudaSuccess) return e;
+      k_zeta<<<g1(n), 256, 0, u->s>>>(u->lbar, u->bp, u->sd, N, P, u->zeta);
+      // d eta_B += -<zeta, g>
+      if ((e = pred(u, u->zeta, u->gs + (size_t)k * n, 2, u->eta_scr, nullptr)) != cudaSuccess) return e;
+      k_acc_sum<<<1, 1, 0, u->s>>>(u->deta + u->T + t, u->eta_scr, P, -1.0);
+      // P = X zeta; Dbar = -eta X^T P
+      if ((e = xw(u, u->zeta, u->Pd, u->P32)) != cudaSuccess) return e;
+      if ((e = xdot(u, u->P32, -1.f, u->Dbar, etaB)) != cudaSuccess) return e;
+      // D = B W - A^T (per pixel), Xbar += -eta (R zeta^T + P D^T)
+      k_dev<<<g1(N), 256, 0, u->s>>>(u->b, u->a, u->W, N, P, u->d);
+      if ((e = rank(u, u->Rs + (size_t)k * lp, u->zeta, -1.f, u->P32, u->d, -1.f, etaB)) != cudaSuccess) return e;
+      // Wbar += B^T Dbar
+      if ((e = pred(u, u->b, u->Dbar, 0, u->scr, nullptr)) != cudaSuccess) return e;
+      k_add_d<<<1, 64, 0, u->s>>>(u->Wbd, u->scr, P * P, u->Wb32);
+      // lbar = zeta + B o (Dbar W); Abar -= Dbar
+      k_bbwd<<<g1(N), 256, 0, u->s>>>(u->zeta, u->b, u->Dbar, u->W, N, P, u->lbar, u->Abar);
+    }
+    // ---- A-phase: zbar(z_{t+1}) += a o (Abar + (Wbar + Wbar^T) a)
+    k_zbar<<<g1(N), 256, 0, u->s>>>(u->a, u->Abar, u->Wb32, N, P, u->zbar);
+    cudaMemsetAsync(u->Abar, 0, n * 4, u->s);
+    // ---- reverse the A-steps from z_t with E_t = X B_t, its Gram, and c = E_t^T x
+    cudaMemcpyAsync(u->l, u->lck + (size_t)t * n, n * 4, cudaMemcpyDeviceToDevice, u->s);
+    k_exp<<<g1(n), 256, 0, u->s>>>(u->l, n, u->b);  // B_t
+    if ((e = make_E(u, u->b)) != cudaSuccess) return e;
+    k_gram<<<(u->P * u->P + 7) / 8, 256, 0, u->s>>>(u->Ed, L, P, u->G);
+    if ((e = xdot(u, u->E32, 1.f, u->C)) != cudaSuccess) return e;
+    {
+      const int nb = nb_thr(N);
+      k_a_bwd<<<nb, kT, 0, u->s>>>(u->C, u->G, etaA, u->K1, N, P, u->zck + (size_t)t * n, u->zbar, u->tmp, u->part);
+      k_merge<<<merge_blocks(P * P + 1), 256, 0, u->s>>>(u->part, nb, P * P + 1, 1.0, u->Gbd, nullptr);
+      k_acc_sum<<<1, 1, 0, u->s>>>(u->deta + t, u->Gbd + P * P, 1, 1.0);
+    }
+    // Ebar = E (Gbar + Gbar^T) + X Cbar^T ; Xbar += E Cbar + Ebar B^T ; lbar += B o (X^T Ebar)
+    if ((e = xw(u, u->tmp, u->XCd, nullptr)) != cudaSuccess) return e;
+    k_ebar<<<g1(lp), 256, 0, u->s>>>(u->Ed, u->Gbd, u->XCd, L, P, u->Eb32);
+    if ((e = rank(u, u->E32, u->tmp, 1.f, u->Eb32, u->b, 1.f)) != cudaSuccess) return e;
+    if ((e = xdot(u, u->Eb32, 1.f, u->d)) != cudaSuccess) return e;
+    k_fma_inplace<<<g1(n), 256, 0, u->s>>>(u->lbar, u->b, u->d, n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Runs body on the engine's stream: captured into *g on the first call,
+// replayed afterwards.
+template <class F>
+cudaError_t run_captured(edaa_unrolled* u, cudaGraphExec_t* g, F&& body) {
+  if (!*g) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(u->s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t eb = body();
+    e = cudaStreamEndCapture(u->s, &graph);
+    if (eb != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return eb;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(g, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      *g = nullptr;
+      return e;
+    }
+  }
+  return cudaGraphLaunch(*g, u->s);
 }
 
 }  // namespace eu
@@ -636,6 +806,7 @@ static edaa_status ufail(edaa_status st, const char* m) {
   edaa::set_last_error(m);
   return st;
 }
+
 #define UCK(x, m)                                              \
   do {                                                         \
     cudaError_t e__ = (x);                                     \
@@ -654,7 +825,13 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
   if (L > 32 * kLT || p > kMaxP || K1 > 5) return ufail(EDAA_ERR_UNSUPPORTED, "L <= 320, p <= 8, K1 <= 5");
   edaa_unrolled* u = new edaa_unrolled();
   u->L = L; u->N = N; u->P = p; u->T = T; u->K1 = K1; u->K2 = K2;
-  u->s = (cudaStream_t)stream;
+  u->caller = (cudaStream_t)stream;
+  if (cudaStreamCreateWithFlags(&u->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&u->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&u->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    edaa_unrolled_destroy(u);
+    return ufail(EDAA_ERR_CUDA, "stream or event creation failed in edaa_unrolled_create");
+  }
   const size_t n = (size_t)N * p, lp = (size_t)L * p;
   Buf& B = u->buf;
   u->X = B.get<float>((size_t)N * L);
@@ -668,6 +845,7 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
   u->scr = B.get<double>(lp);
   u->ls = B.get<float>((size_t)(K2 + 1) * n); u->gs = B.get<float>((size_t)std::max(K2, 1) * n);
   u->Rs = B.get<float>((size_t)std::max(K2, 1) * lp); u->deta = B.get<double>((size_t)2 * T);
+  u->eta = B.get<float>((size_t)2 * T); u->dAin = B.get<float>(n);
   u->lbar = B.get<float>(n); u->zbar = B.get<float>(n); u->Abar = B.get<float>(n);
   u->Xbar = B.get<float>((size_t)N * L); u->zeta = B.get<float>(n); u->Dbar = B.get<float>(n);
   u->bp = B.get<float>(n); u->tmp = B.get<float>(n); u->P32 = B.get<float>(lp); u->Eb32 = B.get<float>(lp);
@@ -675,7 +853,7 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
   u->sd = B.get<double>(8); u->XCd = B.get<double>(lp); u->Gbd = B.get<double>(72); u->Pd = B.get<double>(lp);
   u->Wbd = B.get<double>(64); u->eta_scr = B.get<double>(8);
   if (B.err != cudaSuccess) {
-    delete u;
+    edaa_unrolled_destroy(u);
     return ufail(EDAA_ERR_OOM, "cudaMalloc failed in edaa_unrolled_create");
   }
   *out = u;
@@ -685,6 +863,11 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
 void edaa_unrolled_destroy(edaa_unrolled* u) {
   if (!u) return;
   if (u->s) cudaStreamSynchronize(u->s);
+  if (u->g_fwd) cudaGraphExecDestroy(u->g_fwd);
+  if (u->g_bwd) cudaGraphExecDestroy(u->g_bwd);
+  if (u->ev_in) cudaEventDestroy(u->ev_in);
+  if (u->ev_out) cudaEventDestroy(u->ev_out);
+  if (u->s) cudaStreamDestroy(u->s);
   delete u;
 }
 
@@ -692,27 +875,25 @@ edaa_status edaa_unrolled_forward(edaa_unrolled* u, const float* X, uint64_t see
                                   const double* eta_B, float* E_out, float* A_out) {
   if (!u || !X || !eta_A || !eta_B) return ufail(EDAA_ERR_ARG, "edaa_unrolled_forward: NULL argument");
   const int N = u->N, P = u->P, L = u->L, n = N * P;
-  u->etaA.assign(eta_A, eta_A + u->T);
-  u->etaB.assign(eta_B, eta_B + u->T);
+  std::vector<float> eta(2 * u->T);
+  for (int t = 0; t < u->T; ++t) {
+    eta[t] = (float)eta_A[t];
+    eta[u->T + t] = (float)eta_B[t];
+  }
+  // our stream follows the caller's
+  UCK(cudaEventRecord(u->ev_in, u->caller), "order after the caller's stream");
+  UCK(cudaStreamWaitEvent(u->s, u->ev_in, 0), "order after the caller's stream");
+  UCK(cudaMemcpyAsync(u->eta, eta.data(), eta.size() * sizeof(float), cudaMemcpyHostToDevice, u->s), "copy eta");
   UCK(cudaMemcpyAsync(u->X, X, (size_t)N * L * 4, cudaMemcpyDefault, u->s), "copy X");
   // A^0 = 1/p (eq. initA0): z = -log p; B^0 = softmax(0.1 u) (eq. initB0)
   k_fill<<<g1(n), 256, 0, u->s>>>(u->z, n, -logf((float)P));
   k_init_logits<<<g1(n), 256, 0, u->s>>>(seed, N, P, u->l);
   UCK(normalise_logits(u, u->l, u->b), "init logits");
-  for (int t = 0; t < u->T; ++t) {
-    UCK(cudaMemcpyAsync(u->zck + (size_t)t * n, u->z, n * 4, cudaMemcpyDeviceToDevice, u->s), "checkpoint");
-    UCK(cudaMemcpyAsync(u->lck + (size_t)t * n, u->l, n * 4, cudaMemcpyDeviceToDevice, u->s), "checkpoint");
-    UCK(outer_forward(u, t, false), "outer forward");
-  }
-  UCK(cudaMemcpyAsync(u->zck + (size_t)u->T * n, u->z, n * 4, cudaMemcpyDeviceToDevice, u->s), "checkpoint");
-  UCK(cudaMemcpyAsync(u->lck + (size_t)u->T * n, u->l, n * 4, cudaMemcpyDeviceToDevice, u->s), "checkpoint");
-  UCK(make_E(u, u->b), "E_hat");
+  UCK(run_captured(u, &u->g_fwd, [&] { return forward_body(u); }), "forward");
   if (E_out) UCK(cudaMemcpyAsync(E_out, u->E32, (size_t)L * P * 4, cudaMemcpyDefault, u->s), "copy E");
-  if (A_out) {
-    k_exp<<<g1(n), 256, 0, u->s>>>(u->z, n, u->a);
-    k_transpose_pn<<<g1(n), 256, 0, u->s>>>(u->a, N, P, u->tmp);
-    UCK(cudaMemcpyAsync(A_out, u->tmp, (size_t)n * 4, cudaMemcpyDefault, u->s), "copy A");
-  }
+  if (A_out) UCK(cudaMemcpyAsync(A_out, u->tmp, (size_t)n * 4, cudaMemcpyDefault, u->s), "copy A");
+  UCK(cudaEventRecord(u->ev_out, u->s), "order the caller's stream after ours");
+  UCK(cudaStreamWaitEvent(u->caller, u->ev_out, 0), "order the caller's stream after ours");
   UCK(cudaGetLastError(), "forward");
   u->have_forward = true;
   return EDAA_OK;
@@ -723,89 +904,20 @@ edaa_status edaa_unrolled_backward(edaa_unrolled* u, const float* dE, const floa
   if (!u || !u->have_forward) return ufail(EDAA_ERR_STATE, "edaa_unrolled_backward needs a forward first");
   const int N = u->N, P = u->P, L = u->L, n = N * P, lp = L * P;
   std::vector<double> deA(u->T, 0.0), deB(u->T, 0.0);
-  UCK(cudaMemsetAsync(u->Xbar, 0, (size_t)N * L * 4, u->s), "zero");
-  UCK(cudaMemsetAsync(u->zbar, 0, n * 4, u->s), "zero");
-  // final state: b_T, a_T
-  UCK(cudaMemcpyAsync(u->l, u->lck + (size_t)u->T * n, n * 4, cudaMemcpyDeviceToDevice, u->s), "copy");
-  k_exp<<<g1(n), 256, 0, u->s>>>(u->l, n, u->b);
-  // E_hat = X B_T: Xbar += dE B^T; lbar = B o (X^T dE)
-  if (dE) {
-    UCK(cudaMemcpyAsync(u->Eb32, dE, (size_t)lp * 4, cudaMemcpyDefault, u->s), "copy dE");
-    UCK(rank(u, u->Eb32, u->b, 1.f, nullptr, nullptr, 0.f), "rank");
-    UCK(xdot(u, u->Eb32, 1.f, u->tmp), "xdot");
-    UCK(cudaMemsetAsync(u->lbar, 0, n * 4, u->s), "zero");
-    k_fma_inplace<<<g1(n), 256, 0, u->s>>>(u->lbar, u->b, u->tmp, n);
-  } else {
-    UCK(cudaMemsetAsync(u->lbar, 0, n * 4, u->s), "zero");
-  }
-  // A_hat = exp(z_T): zbar = a o dA  (Abar accumulator starts at dA)
-  UCK(cudaMemsetAsync(u->Abar, 0, n * 4, u->s), "zero");
-  if (dA) {
-    UCK(cudaMemcpyAsync(u->tmp, dA, (size_t)n * 4, cudaMemcpyDefault, u->s), "copy dA");
-    k_transpose_np<<<g1(n), 256, 0, u->s>>>(u->tmp, N, P, u->Abar);
-  }
-  UCK(cudaMemsetAsync(u->deta, 0, 2 * u->T * sizeof(double), u->s), "zero");
-  for (int t = u->T - 1; t >= 0; --t) {
-    // ---- recompute outer iteration t from its checkpoint
-    UCK(cudaMemcpyAsync(u->z, u->zck + (size_t)t * n, n * 4, cudaMemcpyDeviceToDevice, u->s), "copy");
-    UCK(cudaMemcpyAsync(u->l, u->lck + (size_t)t * n, n * 4, cudaMemcpyDeviceToDevice, u->s), "copy");
-    k_exp<<<g1(n), 256, 0, u->s>>>(u->l, n, u->b);
-    UCK(outer_forward(u, t, true), "recompute");
-    // after it: z = z_{t+1}, a = exp(z_{t+1}), W = A A^T; ls[k], gs[k], Rs[k], Es[k]
-    const float etaB = (float)u->etaB[t], etaA = (float)u->etaA[t];
-    UCK(cudaMemsetAsync(u->Wbd, 0, 64 * 8, u->s), "zero");
-    UCK(cudaMemsetAsync(u->Wb32, 0, 64 * 4, u->s), "zero");
-    // ---- reverse the B-steps
-    for (int k = u->K2 - 1; k >= 0; --k) {
-      const float* lk = u->ls + (size_t)k * n;
-      const float* lk1 = u->ls + (size_t)(k + 1) * n;
-      k_exp<<<g1(n), 256, 0, u->s>>>(lk1, n, u->bp);
-      k_exp<<<g1(n), 256, 0, u->s>>>(lk, n, u->b);
-      // s = column sums of lbar; zeta = lbar - B' diag(s)
-      UCK(pred(u, u->lbar, nullptr, 1, u->sd, nullptr), "colsum");
-      k_zeta<<<g1(n), 256, 0, u->s>>>(u->lbar, u->bp, u->sd, N, P, u->zeta);
-      // d eta_B += -<zeta, g>
-      UCK(pred(u, u->zeta, u->gs + (size_t)k * n, 2, u->eta_scr, nullptr), "deta");
-      k_acc_sum<<<1, 1, 0, u->s>>>(u->deta + u->T + t, u->eta_scr, P, -1.0);
-      // P = X zeta; Dbar = -eta X^T P
-      UCK(xw(u, u->zeta, u->Pd, u->P32), "P");
-      UCK(xdot(u, u->P32, -etaB, u->Dbar), "Dbar");
-      // D = B W - A^T (per pixel), Xbar += -eta (R zeta^T + P D^T)
-      k_dev<<<g1(N), 256, 0, u->s>>>(u->b, u->a, u->W, N, P, u->d);
-      UCK(rank(u, u->Rs + (size_t)k * lp, u->zeta, -etaB, u->P32, u->d, -etaB), "rank");
-      // Wbar += B^T Dbar
-      UCK(pred(u, u->b, u->Dbar, 0, u->scr, nullptr), "Wbar");
-      k_add_d<<<1, 64, 0, u->s>>>(u->Wbd, u->scr, P * P, u->Wb32);
-      // lbar = zeta + B o (Dbar W); Abar -= Dbar
-      k_bbwd<<<g1(N), 256, 0, u->s>>>(u->zeta, u->b, u->Dbar, u->W, N, P, u->lbar, u->Abar);
-    }
-    // ---- A-phase: zbar(z_{t+1}) += a o (Abar + (Wbar + Wbar^T) a)
-    k_zbar<<<g1(N), 256, 0, u->s>>>(u->a, u->Abar, u->Wb32, N, P, u->zbar);
-    UCK(cudaMemsetAsync(u->Abar, 0, n * 4, u->s), "zero");
-    // ---- reverse the A-steps from z_t with E_t = X B_t, its Gram, and c = E_t^T x
-    UCK(cudaMemcpyAsync(u->l, u->lck + (size_t)t * n, n * 4, cudaMemcpyDeviceToDevice, u->s), "copy");
-    k_exp<<<g1(n), 256, 0, u->s>>>(u->l, n, u->b);  // B_t
-    UCK(make_E(u, u->b), "E_t");
-    k_gram<<<1, 64, 0, u->s>>>(u->Ed, L, P, u->G);
-    UCK(xdot(u, u->E32, 1.f, u->C), "C");
-    {
-      const int nb = nb_thr(N);
-      k_a_bwd<<<nb, kT, 0, u->s>>>(u->C, u->G, etaA, u->K1, N, P, u->zck + (size_t)t * n, u->zbar, u->tmp, u->part);
-      k_merge<<<1, 128, 0, u->s>>>(u->part, nb, P * P + 1, 1.0, u->Gbd, nullptr);
-      k_acc_sum<<<1, 1, 0, u->s>>>(u->deta + t, u->Gbd + P * P, 1, 1.0);
-    }
-    // Ebar = E (Gbar + Gbar^T) + X Cbar^T ; Xbar += E Cbar + Ebar B^T ; lbar += B o (X^T Ebar)
-    UCK(xw(u, u->tmp, u->XCd, nullptr), "XC");
-    k_ebar<<<g1(lp), 256, 0, u->s>>>(u->Ed, u->Gbd, u->XCd, L, P, u->Eb32);
-    UCK(rank(u, u->E32, u->tmp, 1.f, u->Eb32, u->b, 1.f), "rank");
-    UCK(xdot(u, u->Eb32, 1.f, u->d), "XtEbar");
-    k_fma_inplace<<<g1(n), 256, 0, u->s>>>(u->lbar, u->b, u->d, n);
-    UCK(cudaGetLastError(), "backward");
-  }
+  UCK(cudaEventRecord(u->ev_in, u->caller), "order after the caller's stream");
+  UCK(cudaStreamWaitEvent(u->s, u->ev_in, 0), "order after the caller's stream");
+  // the adjoints of the outputs (zeros when absent) go into the engine's buffers
+  if (dE) UCK(cudaMemcpyAsync(u->Eb32, dE, (size_t)lp * 4, cudaMemcpyDefault, u->s), "copy dE");
+  else UCK(cudaMemsetAsync(u->Eb32, 0, (size_t)lp * 4, u->s), "zero");
+  if (dA) UCK(cudaMemcpyAsync(u->dAin, dA, (size_t)n * 4, cudaMemcpyDefault, u->s), "copy dA");
+  else UCK(cudaMemsetAsync(u->dAin, 0, (size_t)n * 4, u->s), "zero");
+  UCK(run_captured(u, &u->g_bwd, [&] { return backward_body(u); }), "backward");
   if (dX) UCK(cudaMemcpyAsync(dX, u->Xbar, (size_t)N * L * 4, cudaMemcpyDefault, u->s), "copy dX");
   UCK(cudaMemcpyAsync(deA.data(), u->deta, u->T * sizeof(double), cudaMemcpyDeviceToHost, u->s), "copy");
   UCK(cudaMemcpyAsync(deB.data(), u->deta + u->T, u->T * sizeof(double), cudaMemcpyDeviceToHost, u->s), "copy");
   UCK(cudaStreamSynchronize(u->s), "sync");
+  UCK(cudaEventRecord(u->ev_out, u->s), "order the caller's stream after ours");
+  UCK(cudaStreamWaitEvent(u->caller, u->ev_out, 0), "order the caller's stream after ours");
   if (d_eta_A) for (int t = 0; t < u->T; ++t) d_eta_A[t] = deA[t];
   if (d_eta_B) for (int t = 0; t < u->T; ++t) d_eta_B[t] = deB[t];
   return EDAA_OK;
