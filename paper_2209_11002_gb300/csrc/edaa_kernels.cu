@@ -108,7 +108,7 @@ struct PartialRow {
 // butterfly over the team.  The team size and every order depend only on ne
 // and Pg, so the launch mode does not change the result.  store(e, sum)
 // receives each element's total once.
-template <typename Row, typename Store>
+template <bool SCALED, typename Row, typename Store>
 __device__ void team_sums(int ne, int Pg, Row row, Store store) {
   constexpr int W = 16;
   int team = 32;
@@ -122,16 +122,18 @@ __device__ void team_sums(int ne, int Pg, Row row, Store store) {
     if (e < ne) {
       const PartialRow r = row(e);
       for (int g0 = sub; g0 < Pg; g0 += W * team) {
-        float x[W];
+        // all loads of the batch first (out-of-range partials read as 0 with scale 0)
+        float x[W], sc[W];
 #pragma unroll
         for (int q = 0; q < W; ++q) {
-          const int g = g0 + q * team;
-          x[q] = g < Pg ? r.v[(size_t)g * r.stride] : 0.f;
+          const int g = min(g0 + q * team, Pg - 1);
+          x[q] = r.v[(size_t)g * r.stride];
+          sc[q] = SCALED ? r.sc[g * r.sstride] : 1.f;
         }
 #pragma unroll
         for (int q = 0; q < W; ++q) {
-          const int g = g0 + q * team;
-          if (g < Pg) ff_add(hi[q], lo[q], r.sc ? r.sc[g * r.sstride] * x[q] : x[q]);
+          const float keep = (g0 + q * team < Pg) ? 1.f : 0.f;
+          ff_add(hi[q], lo[q], (SCALED ? sc[q] * x[q] : x[q]) * keep);
         }
       }
     }
@@ -164,7 +166,7 @@ __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
   const int l0 = lc * cd.lchunk, nl = min(cd.lchunk, L - l0);
   for (int e = tid; e < nl * P; e += kThreads) sE[e] = cd.Ed[(size_t)(l0 + e / P) * Mp + c0 + e % P];
   for (int e = tid; e < nl; e += kThreads) ssx[e] = cd.sx[l0 + e];
-  team_sums(
+  team_sums<false>(
       P * P + nl * P, Pg,
       [&](int e) {
         if (e < P * P) return PartialRow{cd.paa + (size_t)m * P * P + e, (size_t)cd.M * P * P, nullptr, 0};
@@ -228,7 +230,7 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem) {
   }
   __syncthreads();
   // round 2: scaled sums of the partials of the chunk's bands and of the ones band
-  team_sums(
+  team_sums<true>(
       (nl + 1) * P, Pg,
       [&](int e) {
         const int li = e / P, j = e - li * P;
@@ -260,12 +262,13 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem) {
   __syncthreads();
   // G = E^T E of run m over this chunk's bands, bands in order (the tensor-core
   // A-pass sums the chunks; the CUDA-core A-pass forms G from its staged panel)
-  for (int e = tid; e < P * P; e += kThreads) {
-    const int j = e / P, k = e - j * P;
-    double g = 0.0;
-    for (int li = 0; li < nl; ++li) g += sE[li * P + j] * sE[li * P + k];
-    cd.gpart[((size_t)lc * cd.M + m) * P * P + e] = g;
-  }
+  if (cd.tc)
+    for (int e = tid; e < P * P; e += kThreads) {
+      const int j = e / P, k = e - j * P;
+      double g = 0.0;
+      for (int li = 0; li < nl; ++li) g += sE[li * P + j] * sE[li * P + k];
+      cd.gpart[((size_t)lc * cd.M + m) * P * P + e] = g;
+    }
   for (int e = tid; e < nl * P; e += kThreads) {
     const int li = e / P, l = l0 + li, j = e - li * P;
     double r = -sxa[e];
