@@ -83,3 +83,17 @@ def test_argument_validation(lib):
         codes.append(ei.value.status)
     assert codes[:3] == [edaa.EDAA_ERR_ARG] * 3
     assert codes[3] == edaa.EDAA_ERR_UNSUPPORTED
+
+
+def test_trace_read_and_precision_arguments(lib):
+    """edaa_trace_read refuses a missing context or an unknown sequence, and
+    the precision field accepts exactly FP32, TF32, BF16 and TF32X3."""
+    import ctypes
+    n = ctypes.c_int(-1)
+    assert lib.edaa_trace_read(None, 0, 0, ctypes.byref(n), None, None, None) == edaa.EDAA_ERR_ARG
+    assert edaa.default_config().trace == 0
+    assert (edaa.FP32, edaa.TF32, edaa.BF16, edaa.TF32X3) == (0, 1, 2, 3)
+    X = np.ones((40, 5), np.float32)
+    with pytest.raises(edaa.EDAAError) as ei:
+        edaa.Context([dict(X=X, p=2, seeds=[1], gammas=[1.0])], T=1, precision=4)
+    assert ei.value.status == edaa.EDAA_ERR_ARG
