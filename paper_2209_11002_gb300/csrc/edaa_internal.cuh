@@ -22,7 +22,9 @@
 //   Ef/Ed L x Mp   E = X B (float32 panel and float64 master copy)
 //   Rf    L x Mp   R = E (A A^T) - X A^T, the factor of the B-gradient X^T R
 //   XAt   L x Mp   X A^T (float64), AAt M x p x p (float64)
-//   part  Pg x (L+1) x Mp  per-CTA partial sums of X W (row L: sum of W)
+//   part  Pg x Mp x (L+1)  per-CTA partial sums of X W, one column of W after
+//                  another (band L: sum of W), so that lanes holding
+//                  consecutive bands write consecutive addresses
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>

@@ -171,7 +171,7 @@ __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
       [&](int e) {
         if (e < P * P) return PartialRow{cd.paa + (size_t)m * P * P + e, (size_t)cd.M * P * P, nullptr, 0};
         const int f = e - P * P, li = f / P, j = f - li * P;
-        return PartialRow{cd.part + (size_t)(l0 + li) * Mp + c0 + j, (size_t)(L + 1) * Mp, nullptr, 0};
+        return PartialRow{cd.part + (size_t)(c0 + j) * (L + 1) + l0 + li, (size_t)(L + 1) * Mp, nullptr, 0};
       },
       [&](int e, double v) {
         if (e < P * P) saat[e] = v;
@@ -235,7 +235,7 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem) {
       [&](int e) {
         const int li = e / P, j = e - li * P;
         const int l = li < nl ? l0 + li : L;
-        return PartialRow{cd.part + (size_t)l * Mp + c0 + j, (size_t)(L + 1) * Mp, sscale + j, P};
+        return PartialRow{cd.part + (size_t)(c0 + j) * (L + 1) + l, (size_t)(L + 1) * Mp, sscale + j, P};
       },
       [&](int e, double v) { sraw[e] = v; });
   __syncthreads();

@@ -608,7 +608,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
         const int l = lane + 32 * k;
         if (l <= L) {
 #pragma unroll
-          for (int j = 0; j < P; ++j) part[(size_t)l * Mp + c0 + r * P + j] = acc[k][q][j];
+          for (int j = 0; j < P; ++j) part[(size_t)(c0 + r * P + j) * (L + 1) + l] = acc[k][q][j];
         }
       }
     }

@@ -538,14 +538,14 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
         tmem_ld8(tbase + tl + (uint32_t)(Rgp * (1 + (SPLIT ? nbt : 0) + b) + r * P), v);  // split: the running sums
         if (l <= L) {
 #pragma unroll
-          for (int j = 0; j < P; ++j) part[(size_t)l * Mp + c0 + r * P + j] = v[j];
+          for (int j = 0; j < P; ++j) part[(size_t)(c0 + r * P + j) * (L + 1) + l] = v[j];  // lanes: consecutive bands
         }
       }
     }
   } else {
     // no tile: zero partials
     float* part = cd.part + (size_t)pg * (L + 1) * Mp;
-    for (int e = tid; e < (L + 1) * nc; e += kThreads) part[(size_t)(e / nc) * Mp + c0 + e % nc] = 0.f;
+    for (int e = tid; e < (L + 1) * nc; e += kThreads) part[(size_t)c0 * (L + 1) + e] = 0.f;
   }
   __syncthreads();
   if (!bail) {
