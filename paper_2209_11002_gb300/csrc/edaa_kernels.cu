@@ -262,12 +262,13 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem) {
   __syncthreads();
   // G = E^T E of run m over this chunk's bands, bands in order (the tensor-core
   // A-pass sums the chunks; the CUDA-core A-pass forms G from its staged panel)
-  if (cd.tc)
-    for (int e = tid; e < P * P; e += kThreads) {
+  if (cd.tc)  // one warp per entry, lanes over the bands, fixed butterfly
+    for (int e = warp; e < P * P; e += kWarps) {
       const int j = e / P, k = e - j * P;
       double g = 0.0;
-      for (int li = 0; li < nl; ++li) g += sE[li * P + j] * sE[li * P + k];
-      cd.gpart[((size_t)lc * cd.M + m) * P * P + e] = g;
+      for (int li = lane; li < nl; li += 32) g += sE[li * P + j] * sE[li * P + k];
+      g = warp_sum_d(g);
+      if (lane == 0) cd.gpart[((size_t)lc * cd.M + m) * P * P + e] = g;
     }
   for (int e = tid; e < nl * P; e += kThreads) {
     const int li = e / P, l = l0 + li, j = e - li * P;
