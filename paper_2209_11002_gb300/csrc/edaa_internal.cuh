@@ -144,7 +144,7 @@ __host__ __device__ inline PassSmem pass_smem(int L, int Ls, int Lr, int p, int 
   s.RgW = rw;
   int o = 0;
   s.off_ps = o; o += Lr * s.RgS4;
-  s.off_gs = o; o += (Rm * p * p + 3) & ~3;
+  s.off_gs = o; o += Rm * p * P4;  // G of each run, rows padded to P4
   s.off_xs = o; o += Nt * Ls;
   s.off_ss = o; o += (Nt * s.RgSo + 3) & ~3;
   s.off_ws = o; o += Nt * s.RgW;

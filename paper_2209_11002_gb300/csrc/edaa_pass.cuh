@@ -179,6 +179,36 @@ __device__ __forceinline__ void load_p4(const float* src, float (&v)[PassTraits<
   }
 }
 
+// Asynchronous global -> shared copies (cp.async): the loads of a staging loop
+// are all in flight together instead of one L2 round trip per iteration.
+// With valid == false nothing is read and the destination is zero-filled.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                   static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+               "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                   static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+               "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// N floats (a multiple of 4) from 16-byte-aligned shared memory; volatile so
+// that the compiler re-issues the load where it is written rather than
+// keeping the values live in registers across a loop.
+template <int N>
+__device__ __forceinline__ void lds_row(const float* src, float (&v)[N]) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(src));
+#pragma unroll
+  for (int h = 0; h < N / 4; ++h)
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v[4 * h]), "=f"(v[4 * h + 1]), "=f"(v[4 * h + 2]), "=f"(v[4 * h + 3])
+                 : "r"(a + 16 * h));
+}
+
 __device__ __forceinline__ float f4c(const float4& v, int d) {
   return d == 0 ? v.x : (d == 1 ? v.y : (d == 2 ? v.z : v.w));
 }
@@ -224,10 +254,10 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
     const float* panel = IS_A ? cd.Ef : cd.Rf;
     for (int e = tid; e < Lr * RgS4; e += kThreads) {
       const int l = e / RgS4, cc = e - l * RgS4, r = cc / P4, j = cc - r * P4;
-      float v = 0.f;
-      if (l < L && r < nr && j < P) v = panel[(size_t)l * Mp + c0 + r * P + j];
-      Ps[e] = v;
+      const bool v = l < L && r < nr && j < P;
+      cp_async4(Ps + e, v ? panel + (size_t)l * Mp + c0 + r * P + j : panel, v);
     }
+    cp_async_wait_all();
   }
   if (tid < Rm) runEta[tid] = (tid < nr) ? (IS_A ? cd.eta1[m0 + tid] : cd.eta2[m0 + tid]) : 0.f;
   if (!IS_A) {
@@ -248,7 +278,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
       const int r = e / (P * P), jk = e - r * P * P, j = jk / P, k = jk - j * P;
       float s = 0.f;
       for (int l = 0; l < L; ++l) s = fmaf(Ps[l * RgS4 + r * P4 + j], Ps[l * RgS4 + r * P4 + k], s);
-      Gs[e] = s;
+      Gs[(r * P + j) * P4 + k] = s;
     }
     __syncthreads();
   }
@@ -280,14 +310,15 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
       const float4* Xg = reinterpret_cast<const float4*>(cd.X + (size_t)i0 * Ls);
       float4* xs4 = reinterpret_cast<float4*>(Xs);
       const int n4 = ni * (Ls >> 2), nt4 = Nt * (Ls >> 2);
-      for (int e = tid; e < nt4; e += kThreads) xs4[e] = (e < n4) ? __ldg(Xg + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int e = tid; e < nt4; e += kThreads) cp_async16(xs4 + e, e < n4 ? Xg + e : Xg, e < n4);
     }
     if (!init) {
       for (int e = tid; e < ni * nc; e += kThreads) {
         const int cc = e / ni, i = e - cc * ni;
-        Ss[i * RgSo + cc] = St[(size_t)(c0 + cc) * cd.Nst + i0 + i];
+        cp_async4(Ss + i * RgSo + cc, St + (size_t)(c0 + cc) * cd.Nst + i0 + i, true);
       }
     }
+    cp_async_wait_all();
     __syncthreads();
 
     // ---- phase 1: c = P^T x_i per (pixel, run), then the element-wise update
@@ -363,7 +394,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
           for (int q = 0; q < RQ1M; ++q) {
             const int r = wr + WR1 * q;
             const int rr = (q < RQ1 && r < nr) ? r : 0;
-            const float* G = Gs + rr * P * P;
+            const float* G = Gs + rr * P * P4;
             const float eta = runEta[rr];
             const float inv = 1.f / se[s][q];
             float a[P], mx = -EDAA_INF;
@@ -371,9 +402,13 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
             for (int j = 0; j < P; ++j) a[j] = ea[s][q][j] * inv;
 #pragma unroll
             for (int j = 0; j < P; ++j) {
+              // G's row j is re-read from shared memory at every step (a
+              // broadcast load) instead of being held in registers
+              float grow[P4];
+              lds_row<P4>(G + j * P4, grow);
               float g = -cr[s][q][j];
 #pragma unroll
-              for (int k = 0; k < P; ++k) g = fmaf(G[j * P + k], a[k], g);
+              for (int k = 0; k < P; ++k) g = fmaf(grow[k], a[k], g);
               z[s][q][j] = fmaf(-eta, g, z[s][q][j]);
               mx = fmaxf(mx, z[s][q][j]);
             }
