@@ -330,32 +330,34 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
 #pragma unroll
         for (int j = 0; j < P; ++j) cr[s][q][j] = 0.f;
     if (need_panel && (!IS_A || K1 > 0)) {
+      // Branch-free inner loop: a slot beyond SPT re-reads slot 0's pixel and
+      // a run beyond the group re-reads run 0's panel columns; their sums are
+      // never stored, and every load stays inside the tile and the panel.
+      const float4* xrow[SPTM];
+      const float* prow[RQ1M];
+#pragma unroll
+      for (int s = 0; s < SPTM; ++s) xrow[s] = Xs4 + (((lane + 32 * (wp + (s < SPT ? WP1 * s : 0))) * Ls) >> 2);
+#pragma unroll
+      for (int q = 0; q < RQ1M; ++q) {
+        const int r = wr + WR1 * q;
+        prow[q] = Ps + ((q < RQ1 && r < nr) ? r : 0) * P4;
+      }
 #pragma unroll 2
       for (int l = 0; l < Lr; l += 4) {
         float4 xv[SPTM];
 #pragma unroll
-        for (int s = 0; s < SPTM; ++s) {
-          if (s < SPT) {
-            const int il = lane + 32 * (wp + WP1 * s);
-            xv[s] = Xs4[(il * Ls + l) >> 2];
-          } else {
-            xv[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-          }
-        }
+        for (int s = 0; s < SPTM; ++s) xv[s] = xrow[s][l >> 2];
 #pragma unroll
         for (int q = 0; q < RQ1M; ++q) {
-          const int r = wr + WR1 * q;
-          if (q < RQ1 && r < nr) {
 #pragma unroll
-            for (int d = 0; d < 4; ++d) {
-              float pv[P4];
-              load_p4<P>(Ps + (l + d) * RgS4 + r * P4, pv);
+          for (int d = 0; d < 4; ++d) {
+            float pv[P4];
+            load_p4<P>(prow[q] + (l + d) * RgS4, pv);
 #pragma unroll
-              for (int s = 0; s < SPTM; ++s) {
-                const float x = f4c(xv[s], d);
+            for (int s = 0; s < SPTM; ++s) {
+              const float x = f4c(xv[s], d);
 #pragma unroll
-                for (int j = 0; j < P; ++j) cr[s][q][j] = fmaf(x, pv[j], cr[s][q][j]);
-              }
+              for (int j = 0; j < P; ++j) cr[s][q][j] = fmaf(x, pv[j], cr[s][q][j]);
             }
           }
         }
@@ -563,9 +565,14 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
         }
       }
     }
-    bool act2[RQ2M];
+    // Branch-free like phase 1: a run slot beyond the group accumulates run
+    // 0's weights and is never written out.
+    const float* wcol[RQ2M];
 #pragma unroll
-    for (int q = 0; q < RQ2M; ++q) act2[q] = q < RQ2 && wr2 + WR2 * q < nr;
+    for (int q = 0; q < RQ2M; ++q) {
+      const int r = wr2 + WR2 * q;
+      wcol[q] = Ws + ((q < RQ2 && r < nr) ? r : 0) * P4;
+    }
     const bool last_in = lane + 32 * (LT - 1) <= L;  // bands of the earlier groups are all <= L
 #pragma unroll 2
     for (int i = wp2; i < ni; i += WP2) {
@@ -576,10 +583,8 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
       xv[LT - 1] = last_in ? xr[32 * (LT - 1)] : 0.f;
 #pragma unroll
       for (int q = 0; q < RQ2M; ++q) {
-        if (!act2[q]) continue;
-        const int r = wr2 + WR2 * q;
         float w[P4];
-        load_p4<P>(Ws + i * RgW + r * P4, w);
+        load_p4<P>(wcol[q] + i * RgW, w);
 #pragma unroll
         for (int k = 0; k < LT; ++k)
 #pragma unroll
