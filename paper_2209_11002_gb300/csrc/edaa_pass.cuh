@@ -257,7 +257,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
       const bool v = l < L && r < nr && j < P;
       cp_async4(Ps + e, v ? panel + (size_t)l * Mp + c0 + r * P + j : panel, v);
     }
-    cp_async_wait_all();
+    // completed together with the first tile's copies
   }
   if (tid < Rm) runEta[tid] = (tid < nr) ? (IS_A ? cd.eta1[m0 + tid] : cd.eta2[m0 + tid]) : 0.f;
   if (!IS_A) {
@@ -272,16 +272,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
       if (pg == 0 && live) cd.bref[c0 + r * P + j] = k;
     }
   }
-  __syncthreads();
-  if (IS_A && need_panel && K1 > 0) {
-    for (int e = tid; e < nr * P * P; e += kThreads) {
-      const int r = e / (P * P), jk = e - r * P * P, j = jk / P, k = jk - j * P;
-      float s = 0.f;
-      for (int l = 0; l < L; ++l) s = fmaf(Ps[l * RgS4 + r * P4 + j], Ps[l * RgS4 + r * P4 + k], s);
-      Gs[(r * P + j) * P4 + k] = s;
-    }
-    __syncthreads();
-  }
+  bool g_pending = IS_A && need_panel && K1 > 0;  // G = P^T P, formed once the panel has landed
 
   const int wp = warp % WP1, wr = warp / WP1;
   const int wp2 = warp % WP2, wr2 = warp / WP2;
@@ -320,6 +311,16 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
     }
     cp_async_wait_all();
     __syncthreads();
+    if (g_pending) {
+      for (int e = tid; e < nr * P * P; e += kThreads) {
+        const int r = e / (P * P), jk = e - r * P * P, j = jk / P, k = jk - j * P;
+        float s = 0.f;
+        for (int l = 0; l < L; ++l) s = fmaf(Ps[l * RgS4 + r * P4 + j], Ps[l * RgS4 + r * P4 + k], s);
+        Gs[(r * P + j) * P4 + k] = s;
+      }
+      __syncthreads();
+      g_pending = false;
+    }
 
     // ---- phase 1: c = P^T x_i per (pixel, run), then the element-wise update
     float cr[SPTM][RQ1M][P];
@@ -599,9 +600,10 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
       }
     }
   }  // tiles
+  cp_async_wait_all();  // a work item without tiles still owns its panel copies
 
   // ---- end of pass: reduce phase-2 accumulators over pixel groups, write partials
-  float* buf = Xs;
+  float* buf = Xs;  // column-major (L+1) x RgS4: a warp's lanes touch consecutive words
   for (int g = WP2 - 1; g >= 1; --g) {
     __syncthreads();
     if (wp2 == g) {
@@ -614,7 +616,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
           const int l = lane + 32 * k;
           if (l <= L) {
 #pragma unroll
-            for (int j = 0; j < P; ++j) buf[l * RgS4 + r * P4 + j] = acc[k][q][j];
+            for (int j = 0; j < P; ++j) buf[(r * P4 + j) * (L + 1) + l] = acc[k][q][j];
           }
         }
       }
@@ -630,7 +632,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
           const int l = lane + 32 * k;
           if (l <= L) {
 #pragma unroll
-            for (int j = 0; j < P; ++j) acc[k][q][j] += buf[l * RgS4 + r * P4 + j];
+            for (int j = 0; j < P; ++j) acc[k][q][j] += buf[(r * P4 + j) * (L + 1) + l];
           }
         }
       }
