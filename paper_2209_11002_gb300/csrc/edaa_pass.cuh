@@ -67,7 +67,14 @@ __device__ __forceinline__ float tile_exp(int key) {
 // so every CTA and the merge compute the same k.
 __device__ __forceinline__ int ref_exponent(const CubeDev& cd, int m, int c) {
   double s = 0.0;
-  for (int lc = 0; lc < cd.nlchunk; ++lc) s += cd.rho[(size_t)lc * cd.Mp + c];
+  for (int lc0 = 0; lc0 < cd.nlchunk; lc0 += 8) {  // loads in batches, sum in chunk order
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = lc0 + u < cd.nlchunk ? cd.rho[(size_t)(lc0 + u) * cd.Mp + c] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (lc0 + u < cd.nlchunk) s += v[u];
+  }
   const double t = -cd.eta2d[m] * s * 1.4426950408889634;
   if (!(fabs(t) < 16384.0)) return t < 0.0 ? -16384 : 0;  // also non-finite
   return (int)rint(t);
@@ -314,9 +321,15 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
     if (g_pending) {
       for (int e = tid; e < nr * P * P; e += kThreads) {
         const int r = e / (P * P), jk = e - r * P * P, j = jk / P, k = jk - j * P;
-        float s = 0.f;
-        for (int l = 0; l < L; ++l) s = fmaf(Ps[l * RgS4 + r * P4 + j], Ps[l * RgS4 + r * P4 + k], s);
-        Gs[(r * P + j) * P4 + k] = s;
+        // four interleaved partial sums (the panel rows from L to Lr are zero)
+        const float* pj = Ps + r * P4 + j;
+        const float* pk = Ps + r * P4 + k;
+        float s4[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int l = 0; l < Lr; l += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) s4[u] = fmaf(pj[(l + u) * RgS4], pk[(l + u) * RgS4], s4[u]);
+        }
+        Gs[(r * P + j) * P4 + k] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
       }
       __syncthreads();
       g_pending = false;
@@ -343,7 +356,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
         const int r = wr + WR1 * q;
         prow[q] = Ps + ((q < RQ1 && r < nr) ? r : 0) * P4;
       }
-#pragma unroll 2
+#pragma unroll 4
       for (int l = 0; l < Lr; l += 4) {
         float4 xv[SPTM];
 #pragma unroll
@@ -575,7 +588,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
       wcol[q] = Ws + ((q < RQ2 && r < nr) ? r : 0) * P4;
     }
     const bool last_in = lane + 32 * (LT - 1) <= L;  // bands of the earlier groups are all <= L
-#pragma unroll 2
+#pragma unroll 4
     for (int i = wp2; i < ni; i += WP2) {
       const float* xr = Xs + i * Ls + lane;
       float xv[LT];
