@@ -148,7 +148,7 @@ __host__ __device__ inline PassSmem pass_smem(int L, int Ls, int Lr, int p, int 
   s.off_xs = o; o += Nt * Ls;
   s.off_ss = o; o += (Nt * s.RgSo + 3) & ~3;
   s.off_ws = o; o += Nt * s.RgW;
-  s.off_col = o; o += 6 * s.RgS4;  // B: lse, frame, tile key, reference k, 2^-Mn, frame of the tile
+  s.off_col = o; o += 7 * s.RgS4;  // B: lse, frame, tile key, reference k, 2^-Mn, frame of the tile, 2^(k-Mn)
   s.off_run = o; o += (2 * Rm + 3) & ~3;
   // end-of-pass reduction buffer ((L+1) x RgS4) reuses the region from off_xs
   const int need = s.off_xs + (L + 1) * s.RgS4 + kWarps * Rm * 36;

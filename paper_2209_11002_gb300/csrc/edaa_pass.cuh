@@ -80,11 +80,13 @@ __device__ __forceinline__ int ref_exponent(const CubeDev& cd, int m, int c) {
   return (int)rint(t);
 }
 
-// The same with 2^-Mn precomputed (p2) for the common case k = 0.
-__device__ __forceinline__ float shifted_weight(float u, float Mn, int k);
-__device__ __forceinline__ float shifted_weight_p2(float u, float Mn, float p2, int k) {
-  if (k != 0) return shifted_weight(u, Mn, k);
-  return (fabsf(u) < 1.f) ? expm1f(u) * p2 : exp2f(fmaf(u, kLog2e, -Mn)) - p2;
+// The same with the column's powers of two precomputed: p2 = 2^-Mn and
+// p2k = 2^(k-Mn) (a product with an exact power of two is the single rounding
+// ldexpf makes, down to the subnormal range).
+__device__ __forceinline__ float shifted_weight_p2(float u, float Mn, float p2, int k, float p2k) {
+  if (k == 0) return (fabsf(u) < 1.f) ? expm1f(u) * p2 : exp2f(fmaf(u, kLog2e, -Mn)) - p2;
+  const float s = fmaf(u, kLog2e, -(float)k);
+  return (fabsf(s) < 1.5f) ? expm1f(s * kLn2) * p2k : exp2f(fmaf(u, kLog2e, -Mn)) - p2k;
 }
 
 // Shifted weight of logit u in the power-of-two frame Mn with reference 2^k:
@@ -252,17 +254,21 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
   int* colRef = colKey + sm.RgS4;  // B: reference exponent k of the shifted weights
   float* colP2 = reinterpret_cast<float*>(colRef + sm.RgS4);  // B: 2^-Mn of the current tile's frame
   float* colMn = colP2 + sm.RgS4;                              // B: the current tile's frame Mn
+  float* colP2k = colMn + sm.RgS4;                             // B: 2^(k-Mn)
   float* runEta = smem + sm.off_run;
   const int RgS4 = sm.RgS4, RgSo = sm.RgSo, RgW = sm.RgW;
 
   // ---- stage the panel (E for A, R for B), per-run step sizes, column stats
+  // Panel layout: band quads, then runs, then the quad's 4 bands x P4 columns,
+  // so that phase 1 reads a run's 4 x P4 block at fixed offsets from one pointer.
   const bool need_panel = !init;
   if (need_panel) {
     const float* panel = IS_A ? cd.Ef : cd.Rf;
     for (int e = tid; e < Lr * RgS4; e += kThreads) {
       const int l = e / RgS4, cc = e - l * RgS4, r = cc / P4, j = cc - r * P4;
       const bool v = l < L && r < nr && j < P;
-      cp_async4(Ps + e, v ? panel + (size_t)l * Mp + c0 + r * P + j : panel, v);
+      cp_async4(Ps + (l >> 2) * 4 * RgS4 + r * 4 * P4 + (l & 3) * P4 + j,
+                v ? panel + (size_t)l * Mp + c0 + r * P + j : panel, v);
     }
     // completed together with the first tile's copies
   }
@@ -322,12 +328,12 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
       for (int e = tid; e < nr * P * P; e += kThreads) {
         const int r = e / (P * P), jk = e - r * P * P, j = jk / P, k = jk - j * P;
         // four interleaved partial sums (the panel rows from L to Lr are zero)
-        const float* pj = Ps + r * P4 + j;
-        const float* pk = Ps + r * P4 + k;
+        const float* pj = Ps + r * 4 * P4 + j;
+        const float* pk = Ps + r * 4 * P4 + k;
         float s4[4] = {0.f, 0.f, 0.f, 0.f};
         for (int l = 0; l < Lr; l += 4) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) s4[u] = fmaf(pj[(l + u) * RgS4], pk[(l + u) * RgS4], s4[u]);
+          for (int u = 0; u < 4; ++u) s4[u] = fmaf(pj[l * RgS4 + u * P4], pk[l * RgS4 + u * P4], s4[u]);
         }
         Gs[(r * P + j) * P4 + k] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
       }
@@ -354,7 +360,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
 #pragma unroll
       for (int q = 0; q < RQ1M; ++q) {
         const int r = wr + WR1 * q;
-        prow[q] = Ps + ((q < RQ1 && r < nr) ? r : 0) * P4;
+        prow[q] = Ps + ((q < RQ1 && r < nr) ? r : 0) * 4 * P4;
       }
 #pragma unroll 4
       for (int l = 0; l < Lr; l += 4) {
@@ -366,7 +372,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
 #pragma unroll
           for (int d = 0; d < 4; ++d) {
             float pv[P4];
-            load_p4<P>(prow[q] + (l + d) * RgS4, pv);
+            load_p4<P>(prow[q] + l * RgS4 + d * P4, pv);
 #pragma unroll
             for (int s = 0; s < SPTM; ++s) {
               const float x = f4c(xv[s], d);
@@ -521,6 +527,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
         const float Mn = fmaxf(colM[c], tile_exp(colKey[c]));
         colMn[c] = Mn;
         colP2[c] = Mn == -EDAA_INF ? 0.f : ldexpf(1.f, -(int)Mn);
+        colP2k[c] = Mn == -EDAA_INF ? 0.f : ldexpf(1.f, colRef[c] - (int)Mn);
       }
       __syncthreads();
 #pragma unroll
@@ -539,7 +546,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
             if (j < P && valid) {
               const int c = r * P4 + j;
               // w = e^u 2^-Mn minus the reference weight 2^(k-Mn) (k = 0: uniform b)
-              w[j] = shifted_weight_p2(ur[s][q][j], colMn[c], colP2[c], colRef[c]);
+              w[j] = shifted_weight_p2(ur[s][q][j], colMn[c], colP2[c], colRef[c], colP2k[c]);
             }
           }
           if (valid) {
