@@ -79,6 +79,14 @@ typedef struct {
   int trace;          /* 1: record when each phase of a launch sequence starts and
                          ends (GPU global timer; read with edaa_trace_read).  0
                          (default): no recording.                                   */
+  int tile[4];        /* explicit launch shape of the CUDA-core passes, applied to
+                         every CUDA-core cube: {runs per CTA group, pixel warps of
+                         phase 1, pixels per lane of phase 1 (1, 2, or 4 for
+                         p >= 3), pixel warps of phase 2}; the pixel tile is
+                         32 x tile[1] x tile[2] (32..128).  All zero (default):
+                         the built-in shape, or the autotuner's with autotune = 1.
+                         A shape outside the compiled register tiles or the shared
+                         memory of one CTA fails edaa_init with EDAA_ERR_ARG.     */
 } edaa_config;
 
 typedef struct {

@@ -42,16 +42,19 @@ struct TileCfg {
   int Rm, WP1, SPT, WP2;
 };
 
-// Register-tile limits of the compiled kernels (must match PassTraits).
+// Register-tile limits of the compiled kernels (must match PassTraits): the
+// default slot shape (up to spt_max pixels x rq1_max runs per thread) and,
+// for p >= 3, the four-pixel shape (4 pixels x 1 run).
 int rq1_max(int p) { return p <= 2 ? 4 : (p <= 4 ? 2 : 1); }
 int spt_max(int p) { return p <= 4 ? 2 : 1; }
 int rq2_max(int p) { return p <= 2 ? 4 : (p <= 4 ? 2 : 1); }
 
 bool tile_ok(const TileCfg& t, int L, int p, int M) {
   if (t.Rm < 1 || t.Rm > M) return false;
-  if (8 % t.WP1 || 8 % t.WP2 || t.SPT < 1 || t.SPT > spt_max(p)) return false;
+  const bool four = t.SPT == 4 && p >= 3;
+  if (8 % t.WP1 || 8 % t.WP2 || t.SPT < 1 || (!four && t.SPT > spt_max(p))) return false;
   const int WR1 = 8 / t.WP1, WR2 = 8 / t.WP2;
-  if ((t.Rm + WR1 - 1) / WR1 > rq1_max(p)) return false;
+  if ((t.Rm + WR1 - 1) / WR1 > (four ? 1 : rq1_max(p))) return false;
   if ((t.Rm + WR2 - 1) / WR2 > rq2_max(p)) return false;
   const int Nt = 32 * t.WP1 * t.SPT;
   const PassSmem s = pass_smem(L, padded_ld(L), round_up(L, 4), p, t.Rm, Nt);
@@ -99,7 +102,7 @@ std::vector<TileCfg> tile_candidates(int L, int p, int M) {
   std::vector<TileCfg> out;
   for (int Rm : {1, 2, 3, 4, 5, 6, 8, 10, 12, 16})
     for (int WP1 : {1, 2, 4, 8})
-      for (int SPT : {1, 2})
+      for (int SPT : {1, 2, 4})
         for (int WP2 : {1, 2, 4, 8}) {
           TileCfg t{Rm, WP1, SPT, WP2};
           const int Nt = 32 * WP1 * SPT;
@@ -123,6 +126,7 @@ void set_last_error(const char* msg) { g_err = msg; }
 struct CubeHost {
   int L, N, p, M, Ls, Lr, Mp;
   TileCfg tile;
+  bool tile_fixed = false;  // set by the caller (edaa_config.tile): not autotuned
   int RG, Pg, Nt, ntiles, lchunk, nlchunk;
   void* arena = nullptr;
   size_t arena_bytes = 0;
@@ -440,7 +444,7 @@ static edaa_status sync_status(edaa_ctx* c) {
 static edaa_status autotune(edaa_ctx* c) {
   for (size_t ci = 0; ci < c->cubes.size(); ++ci) {
     CubeHost& h = c->cubes[ci];
-    if (h.tc) continue;  // tensor-core cubes have a fixed shape (tc_tile)
+    if (h.tc || h.tile_fixed) continue;  // tensor-core cubes have a fixed shape (tc_tile)
     auto key = std::make_tuple(c->device, h.L, h.N, h.p, h.M);
     auto it = tune_cache().find(key);
     if (it != tune_cache().end()) {
@@ -501,6 +505,7 @@ void edaa_config_default(edaa_config* cfg) {
   cfg->barrier_timeout_ms = 2000.0;
   cfg->center = 1;
   cfg->trace = 0;
+  for (int i = 0; i < 4; ++i) cfg->tile[i] = 0;
 }
 
 const char* edaa_last_error(void) { return g_err.c_str(); }
@@ -541,6 +546,13 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
     if (!q.seeds || !q.gammas) return fail(EDAA_ERR_ARG, "seeds and gammas are required");
     for (int m = 0; m < q.M; ++m)
       if (!(q.gammas[m] > 0.0) || !isfinite(q.gammas[m])) return fail(EDAA_ERR_ARG, "gammas must be finite and > 0");
+    if (conf.tile[0] != 0) {
+      const TileCfg t{conf.tile[0], conf.tile[1], conf.tile[2], conf.tile[3]};
+      const bool pos = t.Rm > 0 && t.WP1 > 0 && t.SPT > 0 && t.WP2 > 0;
+      const int Nt = pos ? 32 * t.WP1 * t.SPT : 0;
+      if (!pos || Nt < 32 || Nt > 128 || !tile_ok(t, q.L, q.p, q.M))
+        return fail(EDAA_ERR_ARG, "tile: launch shape outside the compiled register tiles or shared memory");
+    }
   }
   edaa_ctx* c = new edaa_ctx();
   c->cfg = conf;
@@ -579,6 +591,8 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
     h.seeds.assign(q.seeds, q.seeds + q.M);
     h.gammas.assign(q.gammas, q.gammas + q.M);
     h.tile = default_tile(q.L, q.p, q.M);
+    h.tile_fixed = conf.tile[0] != 0;  // validated above
+    if (h.tile_fixed) h.tile = TileCfg{conf.tile[0], conf.tile[1], conf.tile[2], conf.tile[3]};
     // tensor cores only where the ensemble makes the contractions dense (M p >= 64)
     if (conf.precision != EDAA_FP32 && h.Mp >= 64) {
       h.tc = conf.precision == EDAA_BF16 ? 2 : (conf.precision == EDAA_TF32X3 ? 3 : 1);

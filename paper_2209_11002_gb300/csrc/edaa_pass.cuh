@@ -167,12 +167,18 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned expected, i
 // Pass work item: one CTA, one run group (Rm runs), pixel tiles pg, pg+Pg, ...
 // Template: P endmembers, LT = ceil((L+1)/32) l-values per lane in phase 2.
 // ---------------------------------------------------------------------------
-template <int P>
+// Slot shapes of phase 1 and the element-wise step: SW = 0 is the default
+// (up to SPTM pixels x RQ1M runs per thread); SW = 4 is four pixels x one
+// run.  Phase 1 reloads every operand word it multiplies through the
+// shared-memory pipe, whose register write-back (one word per lane per
+// cycle per SM) is the limit: a thread tile of a pixels x b columns does a*b
+// FMAs per a+b words, so 4 x P4 beats 2 x 2P4 (and 1 x P4 for p > 4).
+template <int P, int SW = 0>
 struct PassTraits {
   static constexpr int P4 = (P + 3) & ~3;
   static constexpr int PP = P * (P + 1) / 2;
-  static constexpr int RQ1M = (P <= 2) ? 4 : (P <= 4 ? 2 : 1);  // runs per warp, phase 1
-  static constexpr int SPTM = (P <= 4) ? 2 : 1;                  // pixels per lane, phase 1
+  static constexpr int RQ1M = SW == 4 ? 1 : ((P <= 2) ? 4 : (P <= 4 ? 2 : 1));  // runs per warp, phase 1
+  static constexpr int SPTM = SW == 4 ? 4 : ((P <= 4) ? 2 : 1);                 // pixels per lane, phase 1
   static constexpr int RQ2M = (P <= 2) ? 4 : (P <= 4 ? 2 : 1);  // runs per warp, phase 2
 };
 
@@ -223,10 +229,10 @@ __device__ __forceinline__ float f4c(const float4& v, int d) {
 }
 
 // kind: 0 = A-pass (K1 steps; init => A^0), 1 = B-pass (init => B^0 logits)
-template <int P, int LT, bool IS_A>
+template <int P, int LT, bool IS_A, int SW>
 __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeDev& cd, int rg, int pg,
                                        float* smem, int K1, bool init) {
-  using TR = PassTraits<P>;
+  using TR = PassTraits<P, SW>;
   constexpr int P4 = TR::P4;
   constexpr int PP = TR::PP;
   constexpr int RQ1M = TR::RQ1M;
@@ -717,7 +723,6 @@ __device__ __noinline__ void fit_item(const CubeDev& cd, int rg, int pg, float* 
   using TR = PassTraits<P>;
   constexpr int P4 = TR::P4;
   constexpr int RQ1M = TR::RQ1M;
-  constexpr int SPTM = TR::SPTM;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int L = cd.L, Ls = cd.Ls, Lr = cd.Lr, N = cd.N, Mp = cd.Mp, Rm = cd.Rm;
   const int m0 = rg * Rm, nr_all = min(Rm, cd.M - m0);
@@ -760,9 +765,7 @@ __device__ __noinline__ void fit_item(const CubeDev& cd, int rg, int pg, float* 
         Ss[i * RgSo + cc] = cd.logA[(size_t)(c0 + cc) * cd.Nst + i0 + i];
       }
       __syncthreads();
-#pragma unroll
-      for (int s = 0; s < SPTM; ++s) {
-        if (s >= SPT) continue;
+      for (int s = 0; s < SPT; ++s) {  // once per solve: a plain loop over the tile's pixel slots
         const int il = lane + 32 * (wp + WP1 * s);
         const bool valid = il < ni;
 #pragma unroll
@@ -837,6 +840,21 @@ template <int P, bool IS_A, int PREC>
 __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const CubeDev& cd, int rg, int pg,
                                           unsigned char* smem_raw, int K1, bool init);
 
+template <int P, int SW>
+__device__ __forceinline__ void pass_lt(const Batch* bt, const CubeDev& cd, int rg, int pg, float* smem, int k1,
+                                        bool init, bool is_a) {
+  if (cd.LT <= 5) {
+    if (is_a) pass_item<P, 5, true, SW>(bt, cd, rg, pg, smem, k1, init);
+    else pass_item<P, 5, false, SW>(bt, cd, rg, pg, smem, k1, init);
+  } else if (cd.LT <= 7) {
+    if (is_a) pass_item<P, 7, true, SW>(bt, cd, rg, pg, smem, k1, init);
+    else pass_item<P, 7, false, SW>(bt, cd, rg, pg, smem, k1, init);
+  } else {
+    if (is_a) pass_item<P, 10, true, SW>(bt, cd, rg, pg, smem, k1, init);
+    else pass_item<P, 10, false, SW>(bt, cd, rg, pg, smem, k1, init);
+  }
+}
+
 template <int P>
 __device__ __forceinline__ void pass_dispatch_impl(const Batch* bt, const CubeDev& cd, int rg, int pg, float* smem,
                                                  int ph) {
@@ -862,16 +880,10 @@ __device__ __forceinline__ void pass_dispatch_impl(const Batch* bt, const CubeDe
     }
     return;
   }
-  if (cd.LT <= 5) {
-    if (is_a) pass_item<P, 5, true>(bt, cd, rg, pg, smem, k1, init);
-    else pass_item<P, 5, false>(bt, cd, rg, pg, smem, k1, init);
-  } else if (cd.LT <= 7) {
-    if (is_a) pass_item<P, 7, true>(bt, cd, rg, pg, smem, k1, init);
-    else pass_item<P, 7, false>(bt, cd, rg, pg, smem, k1, init);
-  } else {
-    if (is_a) pass_item<P, 10, true>(bt, cd, rg, pg, smem, k1, init);
-    else pass_item<P, 10, false>(bt, cd, rg, pg, smem, k1, init);
-  }
+  if (P >= 3 && cd.SPT == 4)
+    pass_lt<P, 4>(bt, cd, rg, pg, smem, k1, init, is_a);
+  else
+    pass_lt<P, 0>(bt, cd, rg, pg, smem, k1, init, is_a);
 }
 
 

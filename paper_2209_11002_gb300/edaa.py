@@ -34,7 +34,8 @@ class Config(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int), ("K1", ctypes.c_int), ("K2", ctypes.c_int), ("normalize", ctypes.c_int),
                 ("precision", ctypes.c_int), ("fit_norm", ctypes.c_int), ("coherence", ctypes.c_int),
                 ("fit_ratio", ctypes.c_double), ("persistent", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("barrier_timeout_ms", ctypes.c_double), ("center", ctypes.c_int), ("trace", ctypes.c_int)]
+                ("barrier_timeout_ms", ctypes.c_double), ("center", ctypes.c_int), ("trace", ctypes.c_int),
+                ("tile", ctypes.c_int * 4)]
 
 
 class CubeDesc(ctypes.Structure):
@@ -108,6 +109,8 @@ def default_config(**overrides) -> Config:
     for k, v in overrides.items():
         if not hasattr(cfg, k):
             raise KeyError(k)
+        if k == "tile":  # (runs per group, phase-1 pixel warps, pixels per lane, phase-2 pixel warps)
+            v = (ctypes.c_int * 4)(*[int(x) for x in v])
         setattr(cfg, k, v)
     return cfg
 

@@ -97,3 +97,23 @@ def test_trace_read_and_precision_arguments(lib):
     with pytest.raises(edaa.EDAAError) as ei:
         edaa.Context([dict(X=X, p=2, seeds=[1], gammas=[1.0])], T=1, precision=4)
     assert ei.value.status == edaa.EDAA_ERR_ARG
+
+
+def test_tile_argument_is_validated_before_any_device_call(lib):
+    """edaa_config.tile: all zero by default; a launch shape outside the
+    compiled register tiles (four pixels per lane needs p >= 3 and one run
+    per warp), outside 32..128 pixels, or with more runs than the cube has,
+    fails with EDAA_ERR_ARG before the library touches a device."""
+    assert list(edaa.default_config().tile) == [0, 0, 0, 0]
+    X = np.ones((300, 20), np.float32)
+    bad = [(8, 1, 4, 1, 2),   # four pixels per lane with p = 2
+           (4, 4, 2, 1, 4),   # 256-pixel tile
+           (9, 1, 2, 1, 4),   # more runs per group than runs (M = 8)
+           (8, 1, 3, 1, 4),   # three pixels per lane is not compiled
+           (8, 0, 2, 1, 4)]   # no phase-1 warps
+    for rm, wp1, spt, wp2, p in bad:
+        with pytest.raises(edaa.EDAAError) as ei:
+            edaa.Context([dict(X=X, p=p, seeds=list(range(8)), gammas=[1.0] * 8)], T=1,
+                         tile=(rm, wp1, spt, wp2))
+        assert ei.value.status == edaa.EDAA_ERR_ARG, (rm, wp1, spt, wp2, p)
+

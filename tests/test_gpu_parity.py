@@ -53,14 +53,19 @@ def test_initial_state_matches_oracle():
             assert np.abs(E - X @ B0).max() < 1e-5
 
 
-@pytest.mark.parametrize("persistent", [1, 0])
-def test_gradients_per_outer_iteration(persistent):
+@pytest.mark.parametrize("persistent,tile", [(1, None), (0, None), (1, (3, 1, 4, 1)), (0, (3, 1, 4, 2)),
+                                             (1, (3, 2, 2, 2)), (1, (2, 4, 1, 8))])
+def test_gradients_per_outer_iteration(persistent, tile):
     """grad_A and grad_B (the 2(...) gradients of eqs. update_A / update_B) at
-    every outer-iteration boundary t = 0..3, norm-wise relative error <= 1e-5."""
+    every outer-iteration boundary t = 0..3, norm-wise relative error <= 1e-5,
+    for the built-in launch shape and for explicit ones: four pixels per
+    lane, two pixels x two runs, one pixel per lane (ragged last tiles: 2333
+    pixels in tiles of 32 and 128)."""
     cube = synth.make_cube(48, 2333, 4, alpha=0.5, snr_db=30, M=3, gamma_choices=(0.5, 1.0, 2.0), seed=6)
     refs = [_oracle(cube, m, 3, record=True)["hist"] for m in range(cube.M)]
     errs = {}
-    with _ctx([cube], T=3, persistent=persistent) as ctx:
+    kw = {} if tile is None else dict(tile=tile)
+    with _ctx([cube], T=3, persistent=persistent, **kw) as ctx:
         for t in range(4):
             for m in range(cube.M):
                 gA, gB = ctx.grad(0, m, device="cpu")
@@ -72,18 +77,20 @@ def test_gradients_per_outer_iteration(persistent):
     assert max(max(v) for v in errs.values()) <= 1e-5
 
 
-def test_large_step_factors_urban_shape():
+@pytest.mark.parametrize("tile", [None, (2, 1, 4, 1)])
+def test_large_step_factors_urban_shape(tile):
     """gamma = 8 and 4, the top of the step-factor set S, on the Urban-shaped
     cube (L=162, N=94249, p=6).  One B-step there moves whole columns of
     logits by tens of nats, to maxima well below zero, so the shifted
     accumulation has to take its reference below the column's mean weight.
     The loss at every outer boundary t <= 3 within 1e-4 of the oracle, and
-    A, E within 1e-3 at t = 3."""
+    A, E within 1e-3 at t = 3; built-in launch shape and four pixels per lane."""
     cube = synth.workload(synth.URBAN_PRECISION, M=2)
     cube.gammas = np.array([8.0, 4.0])
     T = 3
     refs = [_oracle(cube, m, T, record=True) for m in range(2)]
-    with _ctx([cube], T=T) as ctx:
+    kw = {} if tile is None else dict(tile=tile)
+    with _ctx([cube], T=T, **kw) as ctx:
         for t in range(T + 1):
             loss = ctx.loss(0)
             for m in range(2):
