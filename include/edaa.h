@@ -183,6 +183,12 @@ int edaa_outer_done(const edaa_ctx* ctx);
 edaa_status edaa_describe(const edaa_ctx* ctx, int cube, int* runs_per_group, int* pixel_tile,
                           int* ctas_per_group, int* grid, int* launches_per_solve);
 
+/* The CUDA-core launch shape of cube `cube` in the form of edaa_config.tile
+ * ({runs per CTA group, phase-1 pixel warps, pixels per lane, phase-2 pixel
+ * warps}), e.g. the one the autotuner kept, so that a later context can pin
+ * it.  Tensor-core cubes report the shape of their fit pass. */
+edaa_status edaa_describe_tile(const edaa_ctx* ctx, int cube, int tile[4]);
+
 void edaa_destroy(edaa_ctx* ctx);
 
 /* Thread-local text of the last error on this thread ("" if none). */

@@ -865,6 +865,17 @@ edaa_status edaa_describe(const edaa_ctx* c, int cube, int* runs_per_group, int*
   return EDAA_OK;
 }
 
+edaa_status edaa_describe_tile(const edaa_ctx* c, int cube, int tile[4]) {
+  if (!c || !tile) return fail(EDAA_ERR_ARG, "ctx or tile is NULL");
+  if (cube < 0 || cube >= (int)c->cubes.size()) return fail(EDAA_ERR_ARG, "cube index out of range");
+  const TileCfg& t = c->cubes[cube].tile;
+  tile[0] = t.Rm;
+  tile[1] = t.WP1;
+  tile[2] = t.SPT;
+  tile[3] = t.WP2;
+  return EDAA_OK;
+}
+
 edaa_status edaa_trace_read(edaa_ctx* c, int which, int cap, int* n, int* phase, double* start_us, double* dur_us) {
   if (!c || !n) return fail(EDAA_ERR_ARG, "ctx or n is NULL");
   if (which < 0 || which > 2) return fail(EDAA_ERR_ARG, "which must be 0, 1 or 2");

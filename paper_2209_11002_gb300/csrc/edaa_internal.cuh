@@ -131,7 +131,7 @@ struct Batch {
 // Shared-memory carve-up of a pass work item (in floats).
 struct PassSmem {
   int RgS4, RgSo, RgW;
-  int off_ps, off_gs, off_xs, off_ss, off_ws, off_col, off_run, total;
+  int off_ps, off_gs, off_bar, off_xs, off_ss, off_ws, off_col, off_run, total;
 };
 
 __host__ __device__ inline PassSmem pass_smem(int L, int Ls, int Lr, int p, int Rm, int Nt) {
@@ -145,6 +145,7 @@ __host__ __device__ inline PassSmem pass_smem(int L, int Ls, int Lr, int p, int 
   int o = 0;
   s.off_ps = o; o += Lr * s.RgS4;
   s.off_gs = o; o += Rm * p * P4;  // G of each run, rows padded to P4
+  s.off_bar = o; o += 4;             // the X tile's mbarrier (below the end-of-pass buffer)
   s.off_xs = o; o += Nt * Ls;
   s.off_ss = o; o += (Nt * s.RgSo + 3) & ~3;
   s.off_ws = o; o += Nt * s.RgW;

@@ -129,6 +129,40 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// mbarrier helpers (shared by the CUDA-core and tensor-core passes)
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* b, int c) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(c) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* b) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+// bounded wait for phase `par` of the barrier; false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t par, long long timeout_ns) {
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(par)
+        : "memory");
+    if (ok) return true;
+    if ((long long)(global_ns() - t0) > timeout_ns) return false;
+  }
+}
+// One bulk (TMA) copy of `bytes` contiguous bytes global -> shared, completing
+// on barrier b; both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(b))
+               : "memory");
+}
+
 // Bounded grid barrier: generation counter + arrival counter.  A CTA that
 // waits longer than timeout_ns, or sees another CTA's time-out, sets the
 // status bit and returns false so that the kernel can exit; it never traps.
@@ -292,6 +326,14 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
     }
   }
   bool g_pending = IS_A && need_panel && K1 > 0;  // G = P^T P, formed once the panel has landed
+  // the X tile arrives by one bulk copy per tile, completing on xbar
+  uint64_t* xbar = reinterpret_cast<uint64_t*>(smem + sm.off_bar);
+  uint32_t xpar = 0;
+  if (tid == 0) {
+    mbar_init(xbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
 
   const int wp = warp % WP1, wr = warp / WP1;
   const int wp2 = warp % WP2, wr2 = warp / WP2;
@@ -316,11 +358,14 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
   for (int tile = pg; tile < cd.ntiles; tile += cd.Pg) {
     const int i0 = tile * Nt;
     const int ni = min(Nt, N - i0);
-    {  // X tile: ni contiguous rows of Ls floats; rows >= ni zero
-      const float4* Xg = reinterpret_cast<const float4*>(cd.X + (size_t)i0 * Ls);
+    {  // X tile: ni contiguous rows of Ls floats (16-byte multiples) by one bulk copy; rows >= ni zero
       float4* xs4 = reinterpret_cast<float4*>(Xs);
       const int n4 = ni * (Ls >> 2), nt4 = Nt * (Ls >> 2);
-      for (int e = tid; e < nt4; e += kThreads) cp_async16(xs4 + e, e < n4 ? Xg + e : Xg, e < n4);
+      if (tid == 0) {
+        mbar_expect(xbar, (uint32_t)n4 * 16u);
+        bulk_copy(xs4, cd.X + (size_t)i0 * Ls, (uint32_t)n4 * 16u, xbar);
+      }
+      for (int e = n4 + tid; e < nt4; e += kThreads) xs4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (!init) {
       for (int e = tid; e < ni * nc; e += kThreads) {
@@ -329,6 +374,8 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
       }
     }
     cp_async_wait_all();
+    if (!mbar_wait(xbar, xpar, bt->timeout_ns)) atomicOr(bt->status, kStatTimeout);
+    xpar ^= 1u;
     __syncthreads();
     if (g_pending) {
       for (int e = tid; e < nr * P * P; e += kThreads) {
@@ -627,6 +674,7 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
     }
   }  // tiles
   cp_async_wait_all();  // a work item without tiles still owns its panel copies
+  if (tid == 0) mbar_inval(xbar);  // every wait on it has returned (the tile loop ends in a block barrier)
 
   // ---- end of pass: reduce phase-2 accumulators over pixel groups, write partials
   float* buf = Xs;  // column-major (L+1) x RgS4: a warp's lanes touch consecutive words

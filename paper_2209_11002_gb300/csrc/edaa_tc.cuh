@@ -31,28 +31,7 @@ namespace edaa {
 constexpr int kTcStages = 3;
 constexpr int kTcTile = 128;
 
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, int c) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(c) : "memory");
-}
-__device__ __forceinline__ void mbar_expect(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-// bounded wait for phase `par` of the barrier; false on time-out
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t par, long long timeout_ns) {
-  const unsigned long long t0 = global_ns();
-  while (true) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(par)
-        : "memory");
-    if (ok) return true;
-    if ((long long)(global_ns() - t0) > timeout_ns) return false;
-  }
-}
+// su32, mbar_init, mbar_expect and the bounded mbar_wait live in edaa_pass.cuh
 __device__ __forceinline__ void tma2d(void* dst, const CUtensorMap* m, int c0, int c1, uint64_t* b) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(

@@ -27,7 +27,7 @@ EXPORTS = ["edaa_config_default", "edaa_init", "edaa_reset", "edaa_step", "edaa_
            "edaa_select_rule", "edaa_get", "edaa_grad", "edaa_loss", "edaa_step_sizes", "edaa_sync",
            "edaa_outer_done", "edaa_describe", "edaa_destroy", "edaa_last_error", "edaa_selftest_barrier",
            "edaa_fit_eval_static", "edaa_unrolled_create", "edaa_unrolled_forward", "edaa_unrolled_backward",
-           "edaa_unrolled_destroy", "edaa_trace_read"]
+           "edaa_unrolled_destroy", "edaa_trace_read", "edaa_describe_tile"]
 
 
 class Config(ctypes.Structure):
@@ -89,6 +89,7 @@ def load_library():
         "edaa_unrolled_backward": (ctypes.c_int, [vp, vp, vp, vp, dp, dp]),
         "edaa_unrolled_destroy": (None, [vp]),
         "edaa_trace_read": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip, ip, dp, dp]),
+        "edaa_describe_tile": (ctypes.c_int, [vp, ctypes.c_int, ip]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -274,7 +275,11 @@ class Context:
         vals = [ctypes.c_int() for _ in range(5)]
         _check(self.lib.edaa_describe(self.h, cube, *[ctypes.byref(v) for v in vals]), "edaa_describe")
         keys = ["runs_per_group", "pixel_tile", "ctas_per_group", "grid", "launches_per_solve"]
-        return {k: v.value for k, v in zip(keys, vals)}
+        out = {k: v.value for k, v in zip(keys, vals)}
+        tile = (ctypes.c_int * 4)()
+        _check(self.lib.edaa_describe_tile(self.h, cube, tile), "edaa_describe_tile")
+        out["tile"] = tuple(tile)  # the edaa_config.tile form of the CUDA-core launch shape
+        return out
 
 
 def fit_eval_static(X, E, A, stream=None):

@@ -66,6 +66,7 @@ def test_gradients_per_outer_iteration(persistent, tile):
     errs = {}
     kw = {} if tile is None else dict(tile=tile)
     with _ctx([cube], T=3, persistent=persistent, **kw) as ctx:
+        assert tile is None or ctx.describe(0)["tile"] == tile
         for t in range(4):
             for m in range(cube.M):
                 gA, gB = ctx.grad(0, m, device="cpu")
