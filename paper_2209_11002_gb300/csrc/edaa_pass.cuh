@@ -367,10 +367,10 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
       }
       for (int e = n4 + tid; e < nt4; e += kThreads) xs4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (!init) {
-      for (int e = tid; e < ni * nc; e += kThreads) {
-        const int cc = e / ni, i = e - cc * ni;
-        cp_async4(Ss + i * RgSo + cc, St + (size_t)(c0 + cc) * cd.Nst + i0 + i, true);
+    if (!init) {  // a warp per state column, lanes along the pixels
+      for (int cc = warp; cc < nc; cc += kWarps) {
+        const float* src = St + (size_t)(c0 + cc) * cd.Nst + i0;
+        for (int i = lane; i < ni; i += 32) cp_async4(Ss + i * RgSo + cc, src + i, true);
       }
     }
     cp_async_wait_all();
@@ -616,9 +616,9 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
     }
 
     // ---- write the new state back (coalesced along pixels)
-    for (int e = tid; e < ni * nc; e += kThreads) {
-      const int cc = e / ni, i = e - cc * ni;
-      St[(size_t)(c0 + cc) * cd.Nst + i0 + i] = Ss[i * RgSo + cc];
+    for (int cc = warp; cc < nc; cc += kWarps) {
+      float* dst = St + (size_t)(c0 + cc) * cd.Nst + i0;
+      for (int i = lane; i < ni; i += 32) dst[i] = Ss[i * RgSo + cc];
     }
 
     // ---- phase 2: acc[l][c] += sum_i X[i][l] W[i][c]  (l = 0..L, row L = ones band)
