@@ -86,7 +86,9 @@ typedef struct {
                          32 x tile[1] x tile[2] (32..128).  All zero (default):
                          the built-in shape, or the autotuner's with autotune = 1.
                          A shape outside the compiled register tiles or the shared
-                         memory of one CTA fails edaa_init with EDAA_ERR_ARG.     */
+                         memory of one CTA fails edaa_init with EDAA_ERR_ARG.
+                         On tensor-core cubes tile[0] alone applies: the runs per
+                         CTA group, capped by what tensor memory holds.           */
 } edaa_config;
 
 typedef struct {

@@ -135,6 +135,8 @@ struct CubeHost {
   double* scale = nullptr; // per-pixel 1/||x_i|| (FP64)
   // tensor-core path
   int tc = 0, esz = 4, kp = 0, Npad = 0;
+  int tc_rg = 0;           // run groups of a tensor-core cube (0: the fewest the TMEM allows)
+  int tc_rm_fixed = 0;     // runs per group set by the caller (edaa_config.tile[0])
   void* Xk = nullptr;      // N x kp compute-type copy of the centred X (pixel-major)
   void* XT = nullptr;      // (L+1) x Npad band-major copy
   CUtensorMap* tmaps = nullptr;  // device, 4 maps
@@ -176,8 +178,8 @@ static edaa_status check_status(edaa_ctx* c) {
 static void tc_tile(CubeHost& h) {
   const int rgp_max = tc_rgp_max(h.L, h.esz, h.tc == 3);
   const int rm_max = std::max(1, std::min({128, rgp_max / h.p, 2048 / (h.p * h.p)}));
-  const int RG = (h.M + rm_max - 1) / rm_max;
-  h.tile.Rm = (h.M + RG - 1) / RG;
+  const int RG = std::min(h.M, std::max((h.M + rm_max - 1) / rm_max, h.tc_rg));
+  h.tile.Rm = h.tile_fixed ? std::min(h.tc_rm_fixed, rm_max) : (h.M + RG - 1) / RG;
   h.tile.WP1 = 4;  // the CUDA-core fit pass runs on the same 128-pixel tiles
   h.tile.SPT = 1;
   h.tile.WP2 = 1;
@@ -441,10 +443,68 @@ static edaa_status sync_status(edaa_ctx* c) {
 // Autotuner: time each candidate launch shape on this cube's data (one
 // A-pass + merge and one B-pass + merge, as separate launches) and keep the
 // fastest; results are cached per (device, L, N, p, M).
+// Time of 2 outer iterations (one launch per phase, after a warm-up one) with
+// the batch's current shapes.
+static edaa_status time_candidate(edaa_ctx* c, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  edaa_status st = push_batch(c);
+  if (st != EDAA_OK) return st;
+  st = run_init(c);
+  if (st != EDAA_OK) return st;
+  const int persistent = c->cfg.persistent;
+  c->cfg.persistent = 0;
+  st = enqueue(c, MODE_OUTER, 1, nullptr);
+  CK(cudaEventRecord(e0, c->stream), "event");
+  if (st == EDAA_OK) st = enqueue(c, MODE_OUTER, 2, nullptr);
+  CK(cudaEventRecord(e1, c->stream), "event");
+  c->cfg.persistent = persistent;
+  if (st != EDAA_OK) return st;
+  CK(cudaEventSynchronize(e1), "event sync");
+  CK(cudaEventElapsedTime(ms, e0, e1), "elapsed");
+  return EDAA_OK;
+}
+
+std::map<std::tuple<int, int, int, int, int, int>, int>& tc_tune_cache() {
+  static std::map<std::tuple<int, int, int, int, int, int>, int> c;
+  return c;
+}
+
+// CUDA-core cubes: the tile candidates.  Tensor-core cubes: the number of run
+// groups, from the fewest the tensor memory allows up to three more (smaller
+// groups give each pass more CTAs and shorter epilogues per tile).
 static edaa_status autotune(edaa_ctx* c) {
-  for (size_t ci = 0; ci < c->cubes.size(); ++ci) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  edaa_status st = EDAA_OK;
+  for (size_t ci = 0; ci < c->cubes.size() && st == EDAA_OK; ++ci) {
     CubeHost& h = c->cubes[ci];
-    if (h.tc || h.tile_fixed) continue;  // tensor-core cubes have a fixed shape (tc_tile)
+    if (h.tile_fixed) continue;
+    if (h.tc) {
+      auto key = std::make_tuple(c->device, h.L, h.N, h.p, h.M, h.tc);
+      auto it = tc_tune_cache().find(key);
+      if (it != tc_tune_cache().end()) {
+        h.tc_rg = it->second;
+        continue;
+      }
+      h.tc_rg = 0;
+      tc_tile(h);
+      const int rg0 = (h.M + h.tile.Rm - 1) / h.tile.Rm;
+      int best = rg0, last_rm = 0;
+      float best_ms = 1e30f;
+      for (int rg = rg0; rg <= std::min(h.M, rg0 + 3) && st == EDAA_OK; ++rg) {
+        h.tc_rg = rg;
+        plan(c);
+        if (h.tile.Rm == last_rm) continue;  // the same groups as a smaller count
+        last_rm = h.tile.Rm;
+        st = make_tmaps(c, h);
+        float ms = 0.f;
+        if (st == EDAA_OK) st = time_candidate(c, e0, e1, &ms);
+        if (st == EDAA_OK && ms < best_ms) { best_ms = ms; best = rg; }
+      }
+      h.tc_rg = best;
+      if (st == EDAA_OK) tc_tune_cache()[key] = best;
+      continue;
+    }
     auto key = std::make_tuple(c->device, h.L, h.N, h.p, h.M);
     auto it = tune_cache().find(key);
     if (it != tune_cache().end()) {
@@ -454,37 +514,27 @@ static edaa_status autotune(edaa_ctx* c) {
     std::vector<TileCfg> cands = tile_candidates(h.L, h.p, h.M);
     TileCfg best = h.tile;
     float best_ms = 1e30f;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0), "event");
-    CK(cudaEventCreate(&e1), "event");
     for (const auto& t : cands) {
       h.tile = t;
       plan(c);
       if (cube_smem(h) > c->smem) continue;
-      edaa_status st = push_batch(c);
-      if (st != EDAA_OK) return st;
-      st = run_init(c);
-      if (st != EDAA_OK) return st;
-      // warm-up then time 2 outer iterations with one launch per phase
-      const int persistent = c->cfg.persistent;
-      c->cfg.persistent = 0;
-      st = enqueue(c, MODE_OUTER, 1, nullptr);
-      CK(cudaEventRecord(e0, c->stream), "event");
-      if (st == EDAA_OK) st = enqueue(c, MODE_OUTER, 2, nullptr);
-      CK(cudaEventRecord(e1, c->stream), "event");
-      c->cfg.persistent = persistent;
-      if (st != EDAA_OK) return st;
-      CK(cudaEventSynchronize(e1), "event sync");
       float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+      st = time_candidate(c, e0, e1, &ms);
+      if (st != EDAA_OK) break;
       if (ms < best_ms) { best_ms = ms; best = t; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     h.tile = best;
-    tune_cache()[key] = best;
+    if (st == EDAA_OK) tune_cache()[key] = best;
   }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != EDAA_OK) return st;
   plan(c);
+  for (auto& h : c->cubes)
+    if (h.tc) {
+      st = make_tmaps(c, h);
+      if (st != EDAA_OK) return st;
+    }
   return push_batch(c);
 }
 
@@ -593,6 +643,7 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
     h.tile = default_tile(q.L, q.p, q.M);
     h.tile_fixed = conf.tile[0] != 0;  // validated above
     if (h.tile_fixed) h.tile = TileCfg{conf.tile[0], conf.tile[1], conf.tile[2], conf.tile[3]};
+    h.tc_rm_fixed = conf.tile[0];
     // tensor cores only where the ensemble makes the contractions dense (M p >= 64)
     if (conf.precision != EDAA_FP32 && h.Mp >= 64) {
       h.tc = conf.precision == EDAA_BF16 ? 2 : (conf.precision == EDAA_TF32X3 ? 3 : 1);

@@ -56,6 +56,30 @@ def test_tensor_core_ensemble_against_oracle(prec, persistent):
     assert np.all(np.isfinite(fit)) and 0 <= best < 16
 
 
+@pytest.mark.parametrize("runs", [8, 6, 4])
+def test_tensor_core_run_groups_against_oracle(runs):
+    """Smaller run groups (padded widths 32, 32 and 16 columns instead of 64;
+    the autotuner's candidates) with BF16 operands: the same bars as the
+    default grouping, and the same result with autotune = 1."""
+    cube = synth.make_cube(64, 3001, 4, alpha=0.3, snr_db=25, M=16, gamma_choices=(0.5, 1.0, 2.0), seed=41)
+    T = 10
+    Xn = O.normalize_pixels(cube.X)
+    with _ctx(cube, T=T, precision=edaa.BF16, tile=(runs, 1, 4, 1)) as ctx:
+        assert ctx.describe(0)["runs_per_group"] == runs
+        ctx.solve()
+        loss = ctx.loss(0)
+        got = {m: ctx.get(0, m, device="cpu") for m in (0, 7, 15)}
+    for m, (E, A, B) in got.items():
+        ref = O.edaa(Xn, 4, T, 5, 5, int(cube.seeds[m]), float(cube.gammas[m]))
+        lr = O.objective(Xn, ref["A"], ref["B"])
+        assert abs(loss[m] - lr) / lr <= TOL[edaa.BF16]
+        assert np.abs(A - ref["A"]).max() <= TOL[edaa.BF16]
+        assert np.abs(E - ref["E"]).max() <= TOL[edaa.BF16]
+    with _ctx(cube, T=T, precision=edaa.BF16, autotune=1) as tuned:
+        tuned.solve()
+        assert np.max(np.abs(tuned.loss(0) - loss) / loss) <= 1e-3
+
+
 def test_uneven_batch_mixes_tensor_core_and_cuda_core_cubes():
     """One launch where one cube is dense enough for tensor cores (M p = 64)
     and another is not (M p = 6): both against the oracle."""
