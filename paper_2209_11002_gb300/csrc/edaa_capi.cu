@@ -216,6 +216,7 @@ static void plan(edaa_ctx* c) {
     CubeDev& d = h.dev;
     d.L = h.L; d.Ls = h.Ls; d.Lr = h.Lr; d.N = h.N; d.p = h.p; d.M = h.M; d.Mp = h.Mp;
     d.Nst = round_up(h.N, 32);
+    d.logN = log((double)h.N);
     d.LT = (h.L + 1 + 31) / 32;
     d.Rm = h.tile.Rm; d.RG = h.RG; d.Pg = h.Pg; d.Nt = h.Nt; d.WP1 = h.tile.WP1; d.SPT = h.tile.SPT;
     d.WP2 = h.tile.WP2; d.ntiles = h.ntiles;

@@ -68,6 +68,7 @@ enum Phase {
 struct CubeDev {
   int L, Ls, Lr, N, p, M, Mp, LT;
   int Nst;                     // row length of the state arrays logA / logB (N rounded up to 32)
+  double logN;                 // log N (the B logits live in the frame log(N b))
   int Rm, RG, Pg, Nt, WP1, SPT, WP2, ntiles;
   int cta0;                    // first pass work item of this cube
   int lchunk, nlchunk, unit0;  // merge work items: M * nlchunk from unit0

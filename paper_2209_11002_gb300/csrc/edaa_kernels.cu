@@ -246,14 +246,21 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem) {
     // 2^(k-mx) in the merged frame; add N 2^(k-mx) back to the denominator
     const double wref = ldexp(1.0, cd.bref[c] - (int)mx);
     const double S = sraw[nl * P + j] + wref * (double)cd.N;
-    if (lc == 0) cd.lse[c] = (float)(mx * 0.69314718055994531 + log(S) - log((double)cd.N));
+    if (lc == 0) {
+      // log S = e ln 2 + log f (S = f 2^e, f in [1/2, 1)): f rounded to float
+      // and a float logarithm err by about 1e-7 absolute, below the float lse's
+      // own rounding; this GPU's FP64 pipe makes a double log cost microseconds.
+      int ex = 0;
+      const double f = frexp(S, &ex);
+      cd.lse[c] = (float)((mx + (double)ex) * 0.69314718055994531 + (double)logf((float)f) - cd.logN);
+    }
     sw[j] = wref;
-    sw[kMaxP + j] = S;
+    sw[kMaxP + j] = 1.0 / S;
   }
   __syncthreads();
   for (int e = tid; e < nl * P; e += kThreads) {
     const int li = e / P, l = l0 + li, j = e - li * P;
-    const double s = (sraw[e] + sw[j] * ssx[li]) / sw[kMaxP + j];
+    const double s = (sraw[e] + sw[j] * ssx[li]) * sw[kMaxP + j];
     cd.Ed[(size_t)l * Mp + c0 + j] = s;
     cd.Ef[(size_t)l * Mp + c0 + j] = (float)s;
     if (cd.tc) store_panel(cd, cd.panelE, c0 + j, l, s);
@@ -262,12 +269,12 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem) {
   __syncthreads();
   // G = E^T E of run m over this chunk's bands, bands in order (the tensor-core
   // A-pass sums the chunks; the CUDA-core A-pass forms G from its staged panel)
-  if (cd.tc)  // one warp per entry, lanes over the bands, fixed butterfly
+  if (cd.tc)  // one warp per entry, lanes over the bands, fixed butterfly; FP32 like the A-pass's use of G
     for (int e = warp; e < P * P; e += kWarps) {
       const int j = e / P, k = e - j * P;
-      double g = 0.0;
-      for (int li = lane; li < nl; li += 32) g += sE[li * P + j] * sE[li * P + k];
-      g = warp_sum_d(g);
+      float g = 0.f;
+      for (int li = lane; li < nl; li += 32) g = fmaf((float)sE[li * P + j], (float)sE[li * P + k], g);
+      g = warp_sum(g);
       if (lane == 0) cd.gpart[((size_t)lc * cd.M + m) * P * P + e] = g;
     }
   for (int e = tid; e < nl * P; e += kThreads) {
