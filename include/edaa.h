@@ -87,8 +87,9 @@ typedef struct {
                          the built-in shape, or the autotuner's with autotune = 1.
                          A shape outside the compiled register tiles or the shared
                          memory of one CTA fails edaa_init with EDAA_ERR_ARG.
-                         On tensor-core cubes tile[0] alone applies: the runs per
-                         CTA group, capped by what tensor memory holds.           */
+                         On tensor-core cubes tile[0] alone applies (1..M, the
+                         other entries unchecked): the runs per CTA group, capped
+                         by what tensor memory holds.                             */
 } edaa_config;
 
 typedef struct {

@@ -599,9 +599,10 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
       if (!(q.gammas[m] > 0.0) || !isfinite(q.gammas[m])) return fail(EDAA_ERR_ARG, "gammas must be finite and > 0");
     if (conf.tile[0] != 0) {
       const TileCfg t{conf.tile[0], conf.tile[1], conf.tile[2], conf.tile[3]};
+      const bool tc = conf.precision != EDAA_FP32 && q.M * q.p >= 64;  // tensor-core cube: tile[0] alone
       const bool pos = t.Rm > 0 && t.WP1 > 0 && t.SPT > 0 && t.WP2 > 0;
       const int Nt = pos ? 32 * t.WP1 * t.SPT : 0;
-      if (!pos || Nt < 32 || Nt > 128 || !tile_ok(t, q.L, q.p, q.M))
+      if (tc ? (t.Rm < 1 || t.Rm > q.M) : (!pos || Nt < 32 || Nt > 128 || !tile_ok(t, q.L, q.p, q.M)))
         return fail(EDAA_ERR_ARG, "tile: launch shape outside the compiled register tiles or shared memory");
     }
   }

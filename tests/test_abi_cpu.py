@@ -116,4 +116,13 @@ def test_tile_argument_is_validated_before_any_device_call(lib):
             edaa.Context([dict(X=X, p=p, seeds=list(range(8)), gammas=[1.0] * 8)], T=1,
                          tile=(rm, wp1, spt, wp2))
         assert ei.value.status == edaa.EDAA_ERR_ARG, (rm, wp1, spt, wp2, p)
+    # a tensor-core cube (BF16, M p = 64) checks tile[0] alone: 1..M
+    Xb = np.ones((300, 20), np.float32)
+    kw = dict(p=4, seeds=list(range(16)), gammas=[1.0] * 16)
+    with pytest.raises(edaa.EDAAError) as ei:
+        edaa.Context([dict(X=Xb, **kw)], T=1, precision=edaa.BF16, tile=(17, 0, 0, 0))
+    assert ei.value.status == edaa.EDAA_ERR_ARG
+    with pytest.raises(edaa.EDAAError) as ei:  # accepted; then no device on this machine
+        edaa.Context([dict(X=Xb, **kw)], T=1, precision=edaa.BF16, tile=(12, 0, 0, 0))
+    assert ei.value.status != edaa.EDAA_ERR_ARG
 
