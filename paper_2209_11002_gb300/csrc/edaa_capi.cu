@@ -176,7 +176,7 @@ static edaa_status check_status(edaa_ctx* c) {
 // column count Rgp fits TMEM next to one accumulator per 128-band tile
 // (Rgp * (1 + band tiles) <= 512 columns, Rgp <= 256), balanced over groups.
 static void tc_tile(CubeHost& h) {
-  const int rgp_max = tc_rgp_max(h.L, h.esz, h.tc == 3);
+  const int rgp_max = tc_rgp_max(h.L, h.esz, h.tc == 3, h.p);
   const int rm_max = std::max(1, std::min({128, rgp_max / h.p, 2048 / (h.p * h.p)}));
   const int RG = std::min(h.M, std::max((h.M + rm_max - 1) / rm_max, h.tc_rg));
   h.tile.Rm = h.tile_fixed ? std::min(h.tc_rm_fixed, rm_max) : (h.M + RG - 1) / RG;
@@ -243,7 +243,8 @@ static size_t pass_item_smem(const CubeHost& h) {
   if (h.tc) {
     const int rb = std::min(h.tile.Rm, (8 / h.tile.WP1) * rq1_max(h.p));
     s = (size_t)pass_smem(h.L, h.Ls, h.Lr, h.p, rb, 128).total * 4;  // fit pass in run blocks
-    s = std::max(s, (size_t)tc_smem(round_up(h.tile.Rm * h.p, 16), h.esz, h.tc == 3).total);
+    const int rgp = round_up(h.tile.Rm * h.p, 16);  // the widest group this cube can take (smaller ones need less)
+    s = std::max(s, (size_t)tc_smem(rgp, h.esz, h.tc == 3, h.p).total);
   }
   return s;
 }

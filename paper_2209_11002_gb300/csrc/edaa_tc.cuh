@@ -28,6 +28,10 @@
 
 namespace edaa {
 
+// Ring stages of a tensor-core pass.  Three keep contraction 2's X streaming
+// in during the epilogue; deeper rings (tried up to the shared-memory limit)
+// measured slower, the larger carve-out leaving less L1 for the epilogue's
+// state lines.
 constexpr int kTcStages = 3;
 constexpr int kTcTile = 128;
 
@@ -131,32 +135,42 @@ __device__ __forceinline__ float to_tf32(float x) {
 struct TcSmem {
   uint32_t stage_bytes, w_off, misc_off, total;
 };
-// Shared memory of a tensor-core pass.  A ring stage holds one 128 x 128-byte
-// chunk of X and the panel chunk (Rgp x 128 B; with split operands both the
-// high and the low part); W holds the weights of one 128-pixel tile in
-// 128-byte pixel chunks (split: high and low part); 32 KB for barriers,
-// column statistics, G, step sizes and A A^T sums; 1 KB alignment slack.
-__host__ __device__ inline TcSmem tc_smem(int Rgp, int esz, bool split) {
+// Shared memory of a tensor-core pass.  A ring stage
+// holds one 128 x 128-byte chunk of X and the panel chunk (Rgp x 128 B; with
+// split operands both the high and the low part); W holds the weights of one
+// 128-pixel tile in 128-byte pixel chunks (split: high and low part); the
+// misc region holds the barriers and flags (256 B), seven 256-entry column
+// arrays, the step sizes (128), G (2048) and the A A^T sums (4 x Rm x PP with
+// Rm <= Rgp / p); 1 KB alignment slack.
+__host__ __device__ inline uint32_t tc_misc_bytes(int Rgp, int p) {
+  const uint32_t rm = (uint32_t)(Rgp / p), pp = (uint32_t)(p * (p + 1) / 2);
+  return (256u + 7u * 256u * 4u + 128u * 4u + 2048u * 4u + 4u * rm * pp * 4u + 1023u) & ~1023u;
+}
+__host__ __device__ inline TcSmem tc_smem(int Rgp, int esz, bool split, int p) {
   TcSmem s;
   const uint32_t pnl = ((uint32_t)Rgp * 128u + 1023u) & ~1023u;
   const uint32_t parts = split ? 2u : 1u;
   s.stage_bytes = 128u * 128u + parts * pnl;
   const uint32_t npc = 128u / (128u / (uint32_t)esz);  // pixel chunks of 128 bytes per 128-pixel tile
-  s.w_off = 1024u + kTcStages * s.stage_bytes;
+  s.w_off = 1024u + (uint32_t)kTcStages * s.stage_bytes;
   s.misc_off = s.w_off + parts * npc * pnl;
-  s.total = s.misc_off + 32768u;
+  s.total = s.misc_off + tc_misc_bytes(Rgp, p);
   return s;
 }
+// 226 KB: one CTA's 227 KB of shared memory less 1 KB for the program
+// kernel's static shared memory
+constexpr uint32_t kTcSmemCap = 232448u - 1024u;
+
 
 // Largest padded run-group width (a multiple of 16): TMEM holds C (Rgp
 // columns) and one Acc per 128-band tile (split operands: a per-tile Acc and
 // a running sum per band tile), with 8 spare columns so that the 8-wide TMEM
 // reads of the last run stay inside the 512 allocated; the shared memory
-// above stays within 227 KB.
-__host__ __device__ inline int tc_rgp_max(int L, int esz, bool split) {
+// above stays within kTcSmemCap.
+__host__ __device__ inline int tc_rgp_max(int L, int esz, bool split, int p) {
   const int nbt = (L + 1 + 127) / 128;
   int r = ((512 - 8) / (1 + (split ? 2 : 1) * nbt)) & ~15;
-  while (r > 16 && tc_smem(r, esz, split).total > 232448u) r -= 16;
+  while (r > 16 && tc_smem(r, esz, split, p).total > kTcSmemCap) r -= 16;
   return r;
 }
 

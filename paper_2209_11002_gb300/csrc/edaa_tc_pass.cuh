@@ -30,7 +30,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   const CUtensorMap* tmXlo = cd.tmaps + 4;  // split operands: the low parts
   const CUtensorMap* tmXTlo = cd.tmaps + 5;
   const CUtensorMap* tmPanLo = cd.tmaps + (IS_A ? 6 : 7);
-  const TcSmem S = tc_smem(Rgp, ESZ, SPLIT);
+  const TcSmem S = tc_smem(Rgp, ESZ, SPLIT, P);
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* Wsm = sm + (S.w_off - 1024u);
   const uint32_t wchunk = ((uint32_t)Rgp * 128u + 1023u) & ~1023u;
