@@ -462,7 +462,7 @@ static edaa_status time_candidate(edaa_ctx* c, cudaEvent_t e0, cudaEvent_t e1, f
   if (st != EDAA_OK) return st;
   CK(cudaEventSynchronize(e1), "event sync");
   CK(cudaEventElapsedTime(ms, e0, e1), "elapsed");
-  return EDAA_OK;
+  return sync_status(c);  // a timed-out wait ends the tuning with an error rather than more waits
 }
 
 std::map<std::tuple<int, int, int, int, int, int>, int>& tc_tune_cache() {
@@ -482,10 +482,14 @@ static edaa_status autotune(edaa_ctx* c) {
     CubeHost& h = c->cubes[ci];
     if (h.tile_fixed) continue;
     if (h.tc) {
+      // the cube's tensor maps follow its run groups: rebuilt for each
+      // candidate and for the one kept, before any other cube is timed
       auto key = std::make_tuple(c->device, h.L, h.N, h.p, h.M, h.tc);
       auto it = tc_tune_cache().find(key);
       if (it != tc_tune_cache().end()) {
         h.tc_rg = it->second;
+        plan(c);
+        st = make_tmaps(c, h);
         continue;
       }
       h.tc_rg = 0;
@@ -504,7 +508,11 @@ static edaa_status autotune(edaa_ctx* c) {
         if (st == EDAA_OK && ms < best_ms) { best_ms = ms; best = rg; }
       }
       h.tc_rg = best;
-      if (st == EDAA_OK) tc_tune_cache()[key] = best;
+      if (st == EDAA_OK) {
+        tc_tune_cache()[key] = best;
+        plan(c);
+        st = make_tmaps(c, h);
+      }
       continue;
     }
     auto key = std::make_tuple(c->device, h.L, h.N, h.p, h.M);
