@@ -131,8 +131,8 @@ def unrolled_workload(args, rank, world):
 # kernels as they stand (NVTX range "timed", second k_edaa launch).  Keyed by
 # (workload, precision, outer iterations); absent entries report null.
 SOLVE_DRAM_BYTES = {
-    ("jasper", "fp32", 100): 28869120 + 232329472,
-    ("jasper", "bf16", 100): 26341120 + 5796864,
+    ("jasper", "fp32", 100): 26544640 + 443870464,
+    ("jasper", "bf16", 100): 26184448 + 29152000,
 }
 
 
