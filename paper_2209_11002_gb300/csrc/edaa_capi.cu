@@ -643,7 +643,7 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
   c->hb.coh_mode = conf.coherence;
   c->hb.timeout_ns = (long long)(conf.barrier_timeout_ms * 1e6);
   for (int i = 0; i < n_cubes; ++i) {
-    CubeHost h;
+    CubeHost h{};
     const edaa_cube& q = cubes[i];
     h.L = q.L; h.N = q.N; h.p = q.p; h.M = q.M;
     h.Ls = padded_ld(q.L);

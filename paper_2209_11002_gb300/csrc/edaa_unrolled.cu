@@ -352,7 +352,7 @@ __device__ __forceinline__ void a_steps(float* z, const float* c, const float* G
 }
 
 __global__ void k_a_fwd(const float* __restrict__ C, const float* __restrict__ Gg, const float* __restrict__ etap,
-                        int K1, int N, int P, const float* __restrict__ zin, float* __restrict__ zout) {
+                        int K1, int N, int P, const float* zin, float* zout) {  // zin may be zout (in place)
   const float eta = *etap;
   __shared__ float G[kMaxP * kMaxP];
   if (threadIdx.x < P * P) G[threadIdx.x] = Gg[threadIdx.x];
@@ -381,8 +381,8 @@ __global__ void k_dev(const float* __restrict__ b, const float* __restrict__ a, 
 }
 
 // l' = l - eta g (unnormalised)
-__global__ void k_axpy(const float* __restrict__ l, const float* __restrict__ g, const float* __restrict__ etap, int n,
-                       float* __restrict__ o) {
+__global__ void k_axpy(const float* l, const float* __restrict__ g, const float* __restrict__ etap, int n,
+                       float* o) {  // l may be o (in place)
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) o[e] = fmaf(-*etap, g[e], l[e]);
 }
