@@ -156,7 +156,7 @@ __device__ void team_sums(int ne, int Pg, Row row, Store store) {
 
 // A-merge of run m over band chunk lc: X A^T = sum of the partials + (1/p) sum_i x_i
 // (shifted accumulation), A A^T, and R = E A A^T - X A^T for the next B-pass.
-// Every load that does not depend on another is issued in the first round.
+// Every load that does not depend on another is issued in the first step.
 __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
   const int tid = threadIdx.x;
   const int P = cd.p, L = cd.L, Mp = cd.Mp, Pg = cd.Pg, c0 = m * P;
@@ -211,7 +211,7 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem) {
   double *sraw = sd + ms.sraw, *sprod = sd + ms.sprod;
   float* sscale = reinterpret_cast<float*>(sd + ms.sscale);  // Pg x P
   const int l0 = lc * cd.lchunk, nl = min(cd.lchunk, L - l0);
-  // round 1: everything that does not depend on the partial sums
+  // first load step: everything that does not depend on the partial sums
   for (int e = tid; e < Pg * P; e += kThreads) sscale[e] = cd.pmax[(size_t)(e / P) * Mp + c0 + e % P];
   for (int e = tid; e < nl * P; e += kThreads) sxa[e] = cd.XAt[(size_t)(l0 + e / P) * Mp + c0 + e % P];
   for (int e = tid; e < nl; e += kThreads) ssx[e] = cd.sx[l0 + e];
@@ -229,7 +229,7 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem) {
     if (lane == 0) sw[j] = (double)mx;
   }
   __syncthreads();
-  // round 2: scaled sums of the partials of the chunk's bands and of the ones band
+  // second step: scaled sums of the partials of the chunk's bands and of the ones band
   team_sums<true>(
       (nl + 1) * P, Pg,
       [&](int e) {
