@@ -1,23 +1,35 @@
-"""Benchmark: batched-ensemble EDAA throughput on one GB300 (and N replicas).
+"""Benchmark: batched mixed-precision ensemble EDAA on one GB300 (and N GPUs).
 
-Workload (one "step"): the Jasper-Ridge-shaped synthetic cube (L=198,
-N=100x100, p=4, Dirichlet(0.3), 25 dB), M=50 runs with gamma in {0.5,1,2},
-T=100 outer iterations of K1=5 A-steps + K2=5 B-steps (Algorithm 1), then
-fit, coherence and Algorithm 2's selection.  Unit: run-steps/s, one
-run-step = one inner A- or B-update of one run (M*T*(K1+K2) per step).
+Default workload (one "step"): the Urban-shaped synthetic cube (L=162,
+N=307x307=94249, p=6, Dirichlet(0.2), 20 dB), an ensemble of M=64 runs with
+step factors drawn from the paper's set S, T=100 outer iterations of K1=5
+A-steps + K2=5 B-steps (Algorithm 1), then fit, coherence and Algorithm 2's
+selection.  Unit: run-steps/s, one run-step = one inner A- or B-update of one
+run (M*T*(K1+K2) per step).
 
-value: device-timed, X resident in HBM.  e2e: the same metric through the
-C ABI with host buffers (X uploaded from pinned memory each step, the
-selected run's E, A and B and every run's fit/coherence read back).
-`--impl reference` times the FP64 CPU oracle on the same workload instead.
-Under torchrun every rank solves its own M=50 ensemble (independent runs,
-no collective on the data path: weak scaling).
+`--precision auto` (the default) runs the tensor-core precisions in order of
+speed (BF16, TF32, split TF32) once, untimed, and times the first whose
+selected run's final loss is within 1 % of the plain FP32 ensemble's selected
+run (the matched-loss bar); FP32 when none is.  Beside it the line reports
+plain FP32 single-run EDAA (M=1, CUDA cores) on the same cube, with the
+selected run's seed and step factor, timed the same way, and the ratio.
+
+value: device-timed (CUDA events on the library's stream around the solve,
+a CUDA-graph replay of the persistent solve launch and the fit launch), X
+resident in HBM, L2 flushed between steps.  e2e: the same metric through the
+C ABI with host buffers (X uploaded from pinned memory each step, the selected
+run's E, A and B and every run's fit/coherence read back).  `--impl reference`
+times the FP64 CPU oracle on the same workload instead.
+
+Under torchrun the ensemble is sharded: every rank solves its own block of
+M runs of one global ensemble of world*M runs (same cube, weak scaling), and
+Algorithm 2 selects once over all of them after an all-gather of the 2M
+(fit, coherence) values per rank -- the method's one exchange step.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -30,14 +42,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ensemble EDAA steps/sec vs plain FP32 at matched loss; HBM GB/s vs peak"
 UNIT = "run-steps/s"
-WORKLOAD = "jasper-shape synthetic cube L=198 N=10000 p=4, M=50 runs, T=100, K1=K2=5, FP32"
 WORKLOADS = {
-    "jasper": WORKLOAD,
-    "samson": "samson-shape synthetic cube L=156 N=9025 p=3, M=1 run (plain single EDAA run), T=100, K1=K2=5, FP32",
-    "urban": "urban-shape synthetic cube L=162 N=94249 p=6, M=64 runs, T=100, K1=K2=5, FP32",
-    "uneven": "8 synthetic cubes of uneven L, N, p (seed 1004), M=16 runs each, one launch, T=100, K1=K2=5, FP32",
-    "apex-unrolled": "apex-shape synthetic cube L=285 N=13542 p=4, unrolled T=20, K1=K2=5, forward+backward, FP32",
+    "urban": "urban-shape synthetic cube L=162 N=94249 p=6 (Dirichlet 0.2, 20 dB), M=64 runs, gamma in S, "
+             "T=100, K1=K2=5",
+    "jasper": "jasper-shape synthetic cube L=198 N=10000 p=4 (Dirichlet 0.3, 25 dB), M=50 runs, gamma in "
+              "{0.5,1,2}, T=100, K1=K2=5",
+    "samson": "samson-shape synthetic cube L=156 N=9025 p=3, M=1 run (plain single EDAA run), T=100, K1=K2=5",
+    "uneven": "8 synthetic cubes of uneven L, N, p (seed 1004), M=16 runs each, one launch, T=100, K1=K2=5",
+    "apex-unrolled": "apex-shape synthetic cube L=285 N=13542 p=4, unrolled T=20, K1=K2=5, forward+backward",
 }
+PRECISIONS = ("fp32", "tf32", "bf16", "tf32x3")
+DTYPE = {"fp32": "f32", "tf32": "tf32 (fp32 accumulate)", "bf16": "bf16 (fp32 accumulate)",
+         "tf32x3": "f32 via split tf32 (hi*hi + hi*lo + lo*hi, fp32 accumulate)"}
 
 
 def matched_loss(loss32, best32, loss, best):
@@ -66,14 +82,25 @@ def matched_loss(loss32, best32, loss, best):
             "within_1pct": bool(worst_sel <= 0.01)}
 
 
-def make_workload_cubes(name: str, rank: int):
+def workload_spec(name: str):
+    """The synthetic-cube recipe of a single-cube workload."""
     from paper_2209_11002_gb300 import synth
+    spec = {"jasper": synth.JASPER_ENSEMBLE, "samson": synth.SAMSON_EDAA, "urban": synth.URBAN_PRECISION}[name]
+    return spec
+
+
+def make_workload_cubes(name: str, rank: int = 0, world: int = 1):
+    """The workload's cubes; with world > 1 rank r keeps runs [r M, (r+1) M)
+    of a world*M-run ensemble of the same cube (the ensemble is sharded)."""
+    from paper_2209_11002_gb300 import sharded, synth
     if name == "uneven":
         return synth.uneven_batch()
-    spec = {"jasper": synth.JASPER_ENSEMBLE, "samson": synth.SAMSON_EDAA, "urban": synth.URBAN_PRECISION}[name]
+    spec = workload_spec(name)
     cube = synth.workload(spec)
-    # distinct ensembles per rank: same cube, run seeds drawn from a rank-specific stream
-    cube.seeds, cube.gammas = synth.run_params(rank_seed(spec["seed"], rank), cube.M, spec["gamma_choices"])
+    M = cube.M
+    seeds, gammas = synth.run_params(spec["seed"], M * world, spec["gamma_choices"])
+    lo, hi = sharded.shard_bounds(M * world, rank, world)
+    cube.seeds, cube.gammas = seeds[lo:hi], gammas[lo:hi]
     return [cube]
 
 
@@ -125,11 +152,13 @@ def unrolled_workload(args, rank, world):
     return 0
 
 
-
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one persistent
-# solve launch, from an ncu capture of `bench.py --steps 1 --warmup 3` with the
-# kernels as they stand (NVTX range "timed", second k_edaa launch).  Keyed by
-# (workload, precision, outer iterations); absent entries report null.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel, from ncu captures with the kernels as they stand; keyed by
+# (workload, precision, outer iterations).  Absent entries report null.
+# Jasper: the persistent solve launch itself.  Urban: one launch per phase
+# (--persistent 0) of one outer iteration, scaled to the T outer iterations
+# of the persistent launch (the passes of every outer iteration move the same
+# data).
 SOLVE_DRAM_BYTES = {
     ("jasper", "fp32", 100): 26544640 + 443870464,
     ("jasper", "bf16", 100): 26184448 + 29152000,
@@ -145,11 +174,6 @@ def _peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-def fp32_alu_peak_tflops(sm_count: int, mhz: float) -> float:
-    """FP32 CUDA-core peak: 4 SM partitions x 32 FP32 lanes = 128 FMA/clk/SM."""
-    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
-
-
 def algorithmic_flops_per_outer(L, N, p, M, K1, K2):
     """Two contractions over the resident pixel tile per X pass ((1+K2) passes),
     plus the K1 fused A-updates (G a: 2p^2, update: ~8p per run-pixel)."""
@@ -158,9 +182,16 @@ def algorithmic_flops_per_outer(L, N, p, M, K1, K2):
 
 
 def algorithmic_bytes_per_outer(L, N, p, M, K2, sx=4):
-    """X streamed once per pass plus A and B state read and written."""
+    """X streamed once per pass ((1+K2) passes) plus the A state read and
+    written once; the B state is regenerable (its logits are linear in the
+    pixel), so it is not algorithmic traffic."""
     Mp = M * p
-    return (1 + K2) * L * N * sx + 2.0 * Mp * N * 4 + K2 * 2.0 * Mp * N * 4
+    return (1 + K2) * L * N * sx + 2.0 * Mp * N * 4
+
+
+def stateful_b_bytes_per_outer(N, p, M, K2):
+    """B logits read and written by each of the K2 B-passes, when stored."""
+    return K2 * 2.0 * M * p * N * 4
 
 
 class ClockSampler:
@@ -214,11 +245,6 @@ def dist_env():
     return rank, world, local
 
 
-def rank_seed(base_seed: int, rank: int) -> int:
-    """Each rank solves its own ensemble of the same cube: distinct run seeds."""
-    return base_seed + 7919 * rank
-
-
 def max_over_ranks(x: float, world: int, device=None) -> float:
     """Largest value over all ranks (the job's time is its slowest rank's)."""
     if world <= 1:
@@ -234,6 +260,13 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
     """Weak scaling: every rank processes the same units; the rate is all ranks'
     units over the slowest rank's time."""
     return world * units_per_rank / seconds_max
+
+
+def oracle_sample_plan(cube, seconds=5.0):
+    """Outer iterations of one oracle run taking about `seconds` on the host:
+    the oracle costs about 7e-9 s per (band x pixel x step) element."""
+    per_outer = 7e-9 * cube.L * cube.N * 10
+    return max(1, min(100, int(seconds / per_outer)))
 
 
 def run_oracle_sample(cube, n_runs: int, T: int, K1: int = 5, K2: int = 5):
@@ -255,26 +288,70 @@ def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    from paper_2209_11002_gb300 import synth
-    cube = synth.workload(synth.JASPER_ENSEMBLE)
-    T = 20  # one step = one run of 20 outer iterations (a bounded sample)
+    if args.workload in ("uneven", "apex-unrolled"):
+        print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the oracle on the "
+                          "single-cube workloads only"}), flush=True)
+        return 0
+    cube = make_workload_cubes(args.workload)[0]
+    T = oracle_sample_plan(cube)  # one step = one run of T outer iterations (a bounded sample)
     for _ in range(args.warmup):
         run_oracle_sample(cube, 1, T)
-    rates, total = [], 0.0
-    for k in range(args.steps):
-        r, dt = run_oracle_sample(cube, 1, T)
-        rates.append(r)
+    total = 0.0
+    for _ in range(args.steps):
+        _, dt = run_oracle_sample(cube, 1, T)
         total += dt
     value = args.steps * T * 10 / total
+    sample = f"1 run x {T} outer iterations ({T * 10} run-steps) of the same cube per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "1 run x 20 outer iterations per step"},
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-                             "sample": "1 run x 20 outer iterations (200 run-steps) per step"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def time_solves(ctx, stream, cubes, steps, warmup, flush, world, global_select=None):
+    """Times `steps` solves (reset, then the solve's graph replay, then
+    Algorithm 2) after `warmup` untimed ones.  Returns per-step device ms,
+    per-step solve ms (the graph replay alone) and the last selections."""
+    import torch
+
+    def one(ev=None):
+        ctx.reset()
+        if ev is not None:
+            ev[0].record(stream)
+        ctx.solve()
+        if ev is not None:
+            ev[1].record(stream)
+        sel = [ctx.select(ci) for ci in range(len(cubes))]
+        if global_select is not None:
+            sel[0] = global_select(sel[0])
+        return sel
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms, kern_ms, sel = [], [], None
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))  # evict X and state from the 129 MB L2 between steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        e0.record(stream)
+        sel = one(kev)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(kev[0].elapsed_time(kev[1]))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    return step_ms, kern_ms, sel
 
 
 def main():
@@ -286,10 +363,12 @@ def main():
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-matched", action="store_true",
+                    help="skip the FP32 comparison legs (matched loss, single run); profiling runs")
     ap.add_argument("--outer", type=int, default=100, help="outer iterations T (100: the paper's)")
-    ap.add_argument("--workload", default="jasper", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="urban", choices=sorted(WORKLOADS))
     ap.add_argument("--autotune", type=int, default=1)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "tf32x3"])
+    ap.add_argument("--precision", default="auto", choices=("auto",) + PRECISIONS)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -297,7 +376,7 @@ def main():
     import numpy as np
     import torch
 
-    from paper_2209_11002_gb300 import build, edaa, synth
+    from paper_2209_11002_gb300 import build, edaa, sharded
 
     rank, world, local = dist_env()
     if not torch.cuda.is_available():
@@ -306,100 +385,136 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    build.build_library()
+        if rank == 0:  # one build into the shared tree, then every rank loads it
+            build.build_library()
+        dist.barrier()
+    else:
+        build.build_library()
     edaa.load_library()
 
     T, K1, K2 = args.outer, 5, 5
     if args.workload == "apex-unrolled":
         return unrolled_workload(args, rank, world)
-    cubes = make_workload_cubes(args.workload, rank)
+    cubes = make_workload_cubes(args.workload, rank, world)
     stream = torch.cuda.Stream()
     Xds = [torch.from_numpy(c.pixel_major()).cuda() for c in cubes]
-    prec = {"fp32": edaa.FP32, "tf32": edaa.TF32, "bf16": edaa.BF16, "tf32x3": edaa.TF32X3}[args.precision]
-    ctx = edaa.Context([dict(X=Xd, p=c.p, seeds=c.seeds, gammas=c.gammas) for Xd, c in zip(Xds, cubes)],
-                       stream=stream, T=T, K1=K1, K2=K2, persistent=args.persistent, autotune=args.autotune,
-                       precision=prec)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    cube = cubes[0]
-    L, N, p, M = cube.L, cube.N, cube.p, cube.M
+    PREC = {"fp32": edaa.FP32, "tf32": edaa.TF32, "bf16": edaa.BF16, "tf32x3": edaa.TF32X3}
 
-    def one_step(ev=None):
-        ctx.reset()
-        if ev is not None:
-            ev[0].record(stream)
-        ctx.step(T)
-        if ev is not None:
-            ev[1].record(stream)
+    def context(prec, cs=None, **kw):
+        cs = cubes if cs is None else cs
+        return edaa.Context([dict(X=Xd, p=c.p, seeds=c.seeds, gammas=c.gammas) for Xd, c in zip(Xds, cs)],
+                            stream=stream, T=T, K1=K1, K2=K2, persistent=args.persistent, precision=PREC[prec], **kw)
+
+    global_select = None
+    if world > 1 and len(cubes) == 1:
+        M_loc = cubes[0].M
+
+        def global_select(sel):  # Algorithm 2 over all ranks' runs, once
+            best, fit, mu = sel
+            gbest, gfit, gmu = sharded.global_select(fit, mu, ratio=1.05)
+            return gbest, gfit, gmu
+
+    # ---- which precision: the fastest whose selected run matches plain FP32 within 1 %
+    candidates = {"auto": ["bf16", "tf32", "tf32x3"]}.get(args.precision, [args.precision])
+    choice, matched, tried = None, None, {}
+    ref32 = None
+    if not args.no_matched and candidates != ["fp32"]:
+        ref = context("fp32")
+        ref.solve()
+        ref32 = ([ref.loss(ci) for ci in range(len(cubes))], [ref.select(ci)[0] for ci in range(len(cubes))])
+        ref.close()
+    ctx = None
+    for cand in candidates:
+        ctx = context(cand, autotune=args.autotune)
+        if ref32 is None:
+            choice = cand
+            break
         ctx.solve()
-        return [ctx.select(ci) for ci in range(len(cubes))][0]
+        m = matched_loss(ref32[0], ref32[1], [ctx.loss(ci) for ci in range(len(cubes))],
+                         [ctx.select(ci)[0] for ci in range(len(cubes))])
+        tried[cand] = m
+        if m["within_1pct"] or args.precision != "auto":
+            choice, matched = cand, m
+            break
+        ctx.close()
+        ctx = None
+    if ctx is None:  # no tensor-core precision met the bar: plain FP32 ensemble
+        choice = "fp32"
+        ctx = context("fp32", autotune=args.autotune)
 
-    for _ in range(args.warmup):
-        one_step()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    # ---- the timed ensemble
     sampler = ClockSampler(local)
     sampler.start()
     torch.cuda.nvtx.range_push("timed")  # lets ncu --nvtx-include "timed/" pick the timed launches
-    step_ms, kern_ms = [], []
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(float(k))  # evict X and state from the 129 MB L2 between steps
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        kev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-        e0.record(stream)
-        best, fit, mu = one_step(kev)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        kern_ms.append(kev[0].elapsed_time(kev[1]))
-    torch.cuda.synchronize()
+    step_ms, kern_ms, sel = time_solves(ctx, stream, cubes, args.steps, args.warmup, flush, world, global_select)
     torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     total_ms = max_over_ranks(sum(step_ms), world, "cuda")
     run_steps = sum(c.M for c in cubes) * T * (K1 + K2)
     value = whole_job_rate(run_steps * args.steps, world, total_ms / 1e3)
+    best = sel[0][0]
 
-    # roofline of the dominant kernel: the persistent solve launch (T outer iterations)
+    # ---- roofline of the dominant kernel: the persistent solve launch (T outer iterations)
     peaks, peak_kind = _peaks()
-    props = torch.cuda.get_device_properties(local)
-    flops_launch = T * sum(algorithmic_flops_per_outer(c.L, c.N, c.p, c.M, K1, K2) for c in cubes)
     kern_avg_s = statistics.mean(kern_ms) / 1e3
-    achieved = flops_launch / kern_avg_s / 1e12
-    tensor = args.precision != "fp32" and all(c.M * c.p >= 64 for c in cubes)
+    tensor = choice != "fp32" and all(c.M * c.p >= 64 for c in cubes)
+    sx = 2 if choice == "bf16" else 4
+    flops_launch = T * sum(algorithmic_flops_per_outer(c.L, c.N, c.p, c.M, K1, K2) for c in cubes)
+    bytes_launch = T * sum(algorithmic_bytes_per_outer(c.L, c.N, c.p, c.M, K2, sx) for c in cubes)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
     if tensor:
-        # the solve is one long launch: sustained bf16 peak; TF32 at the nominal TF32/BF16 ratio 1.1/2.25
-        bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
-        # split TF32 issues three MMAs per product: its peak in algorithmic FLOPs is a third of TF32's
-        peak = bf16 if args.precision == "bf16" else bf16 * 1.1 / 2.25 / (3 if args.precision == "tf32x3" else 1)
-        peak_source = (f"{peak_kind} sustained dense bf16 {bf16} TFLOP/s" +
-                       ("" if args.precision == "bf16" else " x nominal TF32/BF16 ratio 1.1/2.25") +
-                       (" / 3 MMAs per product" if args.precision == "tf32x3" else ""))
+        bf16 = peaks.get("bf16_tflops_sustained", 1700.0)  # the solve is one long launch: sustained peak
+        flop_peak = bf16 if choice == "bf16" else bf16 * 1.1 / 2.25 / (3 if choice == "tf32x3" else 1)
+        flop_src = (f"{peak_kind} sustained dense bf16 {bf16} TFLOP/s" +
+                    ("" if choice == "bf16" else " x nominal TF32/BF16 ratio 1.1/2.25") +
+                    (" / 3 MMAs per product" if choice == "tf32x3" else ""))
     else:
-        peak = fp32_alu_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
-        peak_source = (f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 x "
-                       f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max clock)")
-    roofline = {"bound": "tensor" if tensor else "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": SOLVE_DRAM_BYTES.get((args.workload, args.precision, T)) if args.persistent else None,
-                "kernel": "k_edaa (persistent solve, T outer iterations)", "peak_source": peak_source,
-                "kernel_ms": statistics.mean(kern_ms),
-                "effective_gbs": T * sum(algorithmic_bytes_per_outer(c.L, c.N, c.p, c.M, K2,
-                                                                      2 if args.precision == "bf16" else 4)
-                                         for c in cubes) / kern_avg_s / 1e9}
-    # matched loss: the same runs in plain FP32 (CUDA cores), untimed
-    matched = None
-    if args.precision != "fp32":
-        ref = edaa.Context([dict(X=Xd, p=c.p, seeds=c.seeds, gammas=c.gammas) for Xd, c in zip(Xds, cubes)],
-                           stream=stream, T=T, K1=K1, K2=K2, persistent=args.persistent, precision=edaa.FP32)
-        ref.solve()
-        ctx.reset()
-        ctx.solve()
-        matched = matched_loss([ref.loss(ci) for ci in range(len(cubes))], [ref.select(ci)[0] for ci in range(len(cubes))],
-                               [ctx.loss(ci) for ci in range(len(cubes))], [ctx.select(ci)[0] for ci in range(len(cubes))])
-        ref.close()
+        flop_peak = edaa.measure_fma_peak(stream)
+        flop_src = "FP32 FMA loop measured on this GPU just before the timed region (edaa_measure_fma_peak)"
+    t_flop, t_hbm = flops_launch / (flop_peak * 1e12), bytes_launch / (hbm_peak * 1e9)
+    flop_frac = flops_launch / kern_avg_s / 1e12 / flop_peak
+    hbm_frac = bytes_launch / kern_avg_s / 1e9 / hbm_peak
+    traffic = SOLVE_DRAM_BYTES.get((args.workload, choice, T)) if args.persistent else None
+    if t_hbm >= t_flop:
+        roofline = {"bound": "hbm", "achieved": bytes_launch / kern_avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_frac, "traffic": traffic}
+    else:
+        roofline = {"bound": "tensor" if tensor else "alu", "achieved": flops_launch / kern_avg_s / 1e12,
+                    "peak": flop_peak, "unit": "TFLOP/s", "frac": flop_frac, "traffic": traffic}
+    roofline.update({
+        "kernel": "k_edaa persistent solve launch (T outer iterations) + fit launch, one CUDA-graph replay",
+        "kernel_ms": statistics.mean(kern_ms), "algorithmic_bytes": bytes_launch, "algorithmic_flops": flops_launch,
+        "hbm": {"effective_gbs": bytes_launch / kern_avg_s / 1e9, "peak_gbs": hbm_peak, "frac": hbm_frac,
+                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)",
+                "stateful_b_gbs": T * sum(stateful_b_bytes_per_outer(c.N, c.p, c.M, K2) for c in cubes)
+                / kern_avg_s / 1e9},
+        "flops": {"achieved_tflops": flops_launch / kern_avg_s / 1e12, "peak_tflops": flop_peak, "frac": flop_frac,
+                  "peak_source": flop_src},
+    })
 
-    # end to end through the C ABI with host buffers
+    # ---- plain FP32 single-run EDAA on the same cube (the selected run's seed and step factor)
+    single = None
+    if not args.no_matched and world == 1:
+        c0 = cubes[0]
+        b0 = best if 0 <= best < c0.M else 0
+        one = [type(c0)(X=c0.X, E_true=c0.E_true, A_true=c0.A_true, seeds=c0.seeds[b0:b0 + 1],
+                        gammas=c0.gammas[b0:b0 + 1], snr_db=c0.snr_db, name=c0.name)]
+        sctx = edaa.Context([dict(X=Xds[0], p=c0.p, seeds=one[0].seeds, gammas=one[0].gammas)], stream=stream,
+                            T=T, K1=K1, K2=K2, persistent=args.persistent, precision=edaa.FP32,
+                            autotune=args.autotune)
+        s_step, s_kern, _ = time_solves(sctx, stream, one, max(3, args.steps // 2), args.warmup, flush, 1)
+        s_rate = T * (K1 + K2) * len(s_step) / (sum(s_step) / 1e3)
+        s_loss = float(sctx.loss(0)[0])
+        ens_loss = float(ctx.loss(0)[b0])
+        single = {"value": s_rate, "unit": UNIT, "ms_per_step": statistics.mean(s_step), "precision": "fp32",
+                  "runs": 1, "seed": int(one[0].seeds[0]), "gamma": float(one[0].gammas[0]),
+                  "speedup": value / s_rate,
+                  "selected_run_rel_loss_diff": abs(ens_loss - s_loss) / s_loss,
+                  "within_1pct": bool(abs(ens_loss - s_loss) <= 0.01 * s_loss)}
+        sctx.close()
+
+    # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
         Xhs = [torch.from_numpy(c.pixel_major()).pin_memory() for c in cubes]
@@ -410,7 +525,6 @@ def main():
         def e2e_step():
             for ci, Xh in enumerate(Xhs):
                 ctx.reset(ci, Xh)
-            ctx.step(T)
             ctx.solve()
             for ci in range(len(cubes)):
                 b, f, m = ctx.select(ci)
@@ -430,24 +544,24 @@ def main():
                "h2d_bytes_per_step": sum(c.N * c.L * 4 for c in cubes),
                "d2h_bytes_per_step": sum((c.L * c.p + 2 * c.N * c.p) * 4 + 2 * c.M * 8 + 4 for c in cubes)}
 
-    launches_solve = ctx.describe(0)["launches_per_solve"]
-    launches = (1 if args.persistent else 5) + (1 if args.persistent else T * (2 + 2 * K2)) + launches_solve
+    desc = ctx.describe(0)
+    launches = (1 if args.persistent else 5) + desc["launches_per_solve"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "tf32": "tf32 (fp32 accumulate)", "bf16": "bf16 (fp32 accumulate)",
-                      "tf32x3": "f32 via split tf32 (hi*hi + hi*lo + lo*hi, fp32 accumulate)"}[args.precision],
-            "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload] if args.outer == 100 else
-                       WORKLOADS[args.workload] + f" (T={T})", "global_batch_runs": sum(c.M for c in cubes) * world,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[choice], "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload] if T == 100 else WORKLOADS[args.workload] + f" (T={T})",
+                       "precision": choice, "global_batch_runs": sum(c.M for c in cubes) * world,
                        "cubes": [dict(L=c.L, N=c.N, p=c.p, M=c.M) for c in cubes],
                        "T": T, "K1": K1, "K2": K2, "l2": "flushed between timed steps (512 MB write)",
-                       "persistent": args.persistent, "autotune": args.autotune, "launch": ctx.describe(0)},
+                       "persistent": args.persistent, "autotune": args.autotune, "launch": desc,
+                       "parallelism": f"ensemble sharded over {world} GPU(s)" if world > 1 else "1 GPU"},
             "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches * args.steps,
-            "matched_loss": matched,
-            "selected_run": int(best)}
+            "matched_loss": matched, "precision_candidates": tried, "fp32_single_run": single,
+            "selected_run": int(best), "graph_replay": desc["graph"] == 1}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_runs, To = min(2, cube.M), (50 if cube.N * cube.L < 4e6 else 3)
+        cube = cubes[0]
+        To = oracle_sample_plan(cube, 8.0)
+        n_runs = min(2, cube.M)
         rate, dt = run_oracle_sample(cube, n_runs, To)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                                 "sample": f"{n_runs} runs x {To} outer iterations ({n_runs * To * 10} run-steps, "

@@ -182,9 +182,13 @@ int edaa_outer_done(const edaa_ctx* ctx);
 
 /* Describes the launch shape picked for cube `cube` (for logs and tests):
  * runs per CTA group, pixel tile, CTAs per run group, persistent grid size,
- * and the number of kernel launches the last edaa_solve enqueued. */
+ * the number of kernel launches the last edaa_solve enqueued, and the graph
+ * state: 1 when the last edaa_solve replayed its captured CUDA graph, -1 when
+ * capturing failed and solves launch their kernels directly (the capture
+ * error was left in edaa_last_error by that edaa_solve, which still
+ * succeeded), 0 before the first edaa_solve.  NULL outputs are skipped. */
 edaa_status edaa_describe(const edaa_ctx* ctx, int cube, int* runs_per_group, int* pixel_tile,
-                          int* ctas_per_group, int* grid, int* launches_per_solve);
+                          int* ctas_per_group, int* grid, int* launches_per_solve, int* graph_state);
 
 /* The CUDA-core launch shape of cube `cube` in the form of edaa_config.tile
  * ({runs per CTA group, phase-1 pixel warps, pixels per lane, phase-2 pixel
@@ -203,6 +207,13 @@ const char* edaa_last_error(void);
  * give up after timeout_ms and the call must return EDAA_ERR_TIMEOUT with the
  * device still usable (no trap, no hang).  extra = 0 must return EDAA_OK. */
 edaa_status edaa_selftest_barrier(int grid, int extra, double timeout_ms, void* stream);
+
+/* Measures the FP32 FMA throughput of the current device (TFLOP/s, best of
+ * five timed launches of a register-resident loop of independent FMA chains,
+ * about 0.1 s in total) on `stream`; synchronises.  It is the roofline
+ * denominator of the CUDA-core passes, whose work is FP32 FMAs (Algorithm 1's
+ * contractions and element-wise steps); the paper has no counterpart. */
+edaa_status edaa_measure_fma_peak(double* tflops, void* stream);
 
 /* ---- Differentiable unrolled solve (one run) ------------------------------
  * Algorithm 1 unrolled for T outer iterations with one step size per block:
@@ -251,11 +262,19 @@ void edaa_unrolled_destroy(edaa_unrolled* u);
  *      loss[M] = ||X - E A||_F^2 (FP64, NULL skips) must be device memory.
  * Limits: 1 <= p <= 8 and 1 <= M <= 64 (the size of the static array);
  * larger sizes return EDAA_ERR_UNSUPPORTED with a message, nothing runs.
- * Asynchronous on `stream` (a cudaStream_t).  The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Calls on
- * one device share the array, so calls whose GPU work overlaps race: the
- * caller serialises them (one stream, or an event between streams). */
+ * Inputs and outputs must be memory of the current device (or managed);
+ * anything else returns EDAA_ERR_ARG.  Asynchronous on `stream` (a
+ * cudaStream_t).  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Under CUDA's default lazy module loading
+ * the library's device image -- its code and this array -- is loaded onto a
+ * device by the first library call that needs it there, which is this
+ * lookup when no other library call came first on that device; the load
+ * takes device memory from the driver.  A caller whose allocator will
+ * reserve the whole GPU makes one library call on each device before that;
+ * a load that finds no memory returns EDAA_ERR_OOM.  Calls on one device
+ * share the array, so calls whose GPU work overlaps race: the caller
+ * serialises them (one stream, or an event between streams). */
 edaa_status edaa_fit_eval_static(const float* X, int L, int N, int p, int M, const float* E, const float* A,
                                  double* fit, double* fitmax, double* loss, void* stream);
 

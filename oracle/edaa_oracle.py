@@ -233,22 +233,3 @@ def select(fits: Sequence[float], mus: Sequence[float], ratio: float = 1.05) -> 
         if mus[m] < mus[best]:
             best = m
     return best
-
-
-def model_selection(X: np.ndarray, p: int, T: int, K1: int, K2: int, seeds: Sequence[int],
-                    gammas: Sequence[float], ratio: float = 1.05, fit_mode: int = 0,
-                    coh_mode: int = 0) -> Dict:
-    """Algorithm 2 around Algorithm 1: M runs, their fits and coherences, and
-    the selected index."""
-    runs: List[Dict] = []
-    fits, mus = [], []
-    for s, g in zip(seeds, gammas):
-        r = edaa(X, p, T, K1, K2, int(s), float(g))
-        r["fit"] = fit_l1(X, r["E"], r["A"], fit_mode)
-        r["mu"] = coherence(r["E"], coh_mode)
-        r["loss"] = objective(X, r["A"], r["B"])
-        runs.append(r)
-        fits.append(r["fit"])
-        mus.append(r["mu"])
-    return {"runs": runs, "fits": np.array(fits), "mus": np.array(mus),
-            "best": select(fits, mus, ratio)}

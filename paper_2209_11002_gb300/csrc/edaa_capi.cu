@@ -164,6 +164,7 @@ struct edaa_ctx {
   cudaGraphExec_t g_solve = nullptr;
   int g_solve_n = -1;
   bool graphs_ok = true;
+  int graph_state = 0;  // 1: the last edaa_solve replayed its captured graph; -1: capture failed; 0: no solve yet
   int launches_last_solve = 0;
 };
 
@@ -790,6 +791,10 @@ edaa_status edaa_solve(edaa_ctx* c) {
       }
     }
     if (e != cudaSuccess) {
+      // reported, not fatal: this and later solves launch directly
+      // (edaa_describe's graph state is -1 and edaa_last_error says why)
+      g_err = std::string("CUDA-graph capture of the solve failed (solves launch directly): ") +
+              cudaGetErrorString(e);
       cudaGetLastError();
       c->graphs_ok = false;
       c->g_solve = nullptr;
@@ -797,7 +802,9 @@ edaa_status edaa_solve(edaa_ctx* c) {
   }
   if (c->graphs_ok && c->g_solve) {
     CK(cudaGraphLaunch(c->g_solve, c->stream), "graph launch");
+    c->graph_state = 1;
   } else {
+    c->graph_state = -1;
     st = enqueue(c, MODE_OUTER, n, &launches);
     if (st == EDAA_OK) st = enqueue(c, MODE_FIT, 0, &launches);
     if (st != EDAA_OK) return st;
@@ -915,7 +922,7 @@ edaa_status edaa_step_sizes(edaa_ctx* c, int cube, double* eta1, double* eta2) {
 int edaa_outer_done(const edaa_ctx* c) { return c ? c->outer_done : -1; }
 
 edaa_status edaa_describe(const edaa_ctx* c, int cube, int* runs_per_group, int* pixel_tile, int* ctas_per_group,
-                          int* grid, int* launches_per_solve) {
+                          int* grid, int* launches_per_solve, int* graph_state) {
   if (!c) return fail(EDAA_ERR_ARG, "ctx is NULL");
   if (cube < 0 || cube >= (int)c->cubes.size()) return fail(EDAA_ERR_ARG, "cube index out of range");
   const CubeHost& h = c->cubes[cube];
@@ -924,6 +931,7 @@ edaa_status edaa_describe(const edaa_ctx* c, int cube, int* runs_per_group, int*
   if (ctas_per_group) *ctas_per_group = h.Pg;
   if (grid) *grid = c->grid;
   if (launches_per_solve) *launches_per_solve = c->launches_last_solve;
+  if (graph_state) *graph_state = c->graph_state;
   return EDAA_OK;
 }
 
@@ -971,6 +979,37 @@ void edaa_destroy(edaa_ctx* c) {
   if (c->d_trace) cudaFree(c->d_trace);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
+}
+
+edaa_status edaa_measure_fma_peak(double* tflops, void* stream) {
+  if (!tflops) return fail(EDAA_ERR_ARG, "tflops is NULL");
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = sms * 8, iters = 1 << 16;
+  float* out = nullptr;
+  CK(cudaMalloc(&out, (size_t)blocks * 256 * sizeof(float)), "cudaMalloc");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double best = 0.0;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = launch_fma_peak(out, blocks, iters, s);  // warm-up
+  for (int r = 0; r < 5 && e == cudaSuccess; ++r) {
+    e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = launch_fma_peak(out, blocks, iters, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && ms > 0.f) best = std::max(best, fma_peak_flops_per_launch(blocks, iters) / (ms * 1e-3) / 1e12);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  if (e != cudaSuccess) return cuda_fail(e, "FMA probe");
+  *tflops = best;
+  return EDAA_OK;
 }
 
 edaa_status edaa_selftest_barrier(int grid, int extra, double timeout_ms, void* stream) {

@@ -201,5 +201,7 @@ cudaError_t program_occupancy(int* blocks_per_sm, size_t smem);
 int program_phase_count(int mode, int n_outer, int K2);
 int program_phase_id(int mode, int s, int K2);
 cudaError_t launch_tc_prepare(const CubeDev& hc, void* Xk, void* XT, int Npad, cudaStream_t s);
+cudaError_t launch_fma_peak(float* out, int blocks, int iters, cudaStream_t s);
+double fma_peak_flops_per_launch(int blocks, int iters);
 
 }  // namespace edaa

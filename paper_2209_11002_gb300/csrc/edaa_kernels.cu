@@ -744,6 +744,32 @@ cudaError_t launch_tc_prepare(const CubeDev& hc, void* Xk, void* XT, int Npad, c
   return cudaGetLastError();
 }
 
+// FP32 FMA throughput probe (the roofline denominator of the CUDA-core
+// passes).  kFmaChains independent dependency chains per thread, unrolled so
+// that loop control is a small fraction of the issued instructions; the
+// chains are folded into one store per thread so that none is dead code.
+constexpr int kFmaChains = 16;
+__global__ void __launch_bounds__(256) k_fma_peak(float* __restrict__ out, int iters, float b, float c) {
+  float a[kFmaChains];
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) a[k] = (float)threadIdx.x * 1e-3f + (float)k;
+#pragma unroll 8
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) a[k] = fmaf(a[k], b, c);
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) s += a[k];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t launch_fma_peak(float* out, int blocks, int iters, cudaStream_t s) {
+  k_fma_peak<<<blocks, 256, 0, s>>>(out, iters, 0.9999999f, 1e-7f);
+  return cudaGetLastError();
+}
+
+double fma_peak_flops_per_launch(int blocks, int iters) { return 2.0 * kFmaChains * (double)iters * blocks * 256.0; }
+
 __global__ void k_barrier_test(unsigned* bar, int* status, unsigned expected, long long timeout_ns) {
   grid_barrier(bar, expected, status, timeout_ns);
 }

@@ -10,7 +10,14 @@
 //
 // The array is g_fit_scratch below: kFitScratchDoubles doubles (384 KiB).  It
 // is part of the library's device image, so every GPU that loads the library
-// holds it until the process exits.  All calls on a device share it and each
+// holds it until the process exits.  The image (all of the library's device
+// code and this array) is loaded onto a device by the first call that needs
+// it there: under CUDA's default lazy module loading, if this entry point is
+// the first library call on a device, its set-up (the symbol lookup below)
+// is what loads the image, and that takes device memory from the driver.
+// A caller whose allocator later reserves the whole GPU must therefore make
+// one library call on each device before that; a load that finds no memory
+// is reported as EDAA_ERR_OOM.  All calls on a device share it and each
 // call leaves its partials there; every slot the final reduction reads is
 // written earlier in the same call, so nothing needs clearing between calls,
 // but calls whose work overlaps on the GPU (different streams, or different
@@ -114,13 +121,16 @@ __global__ void k_fit_static_reduce(const double* scratch, int blocks, int M, do
 std::mutex g_setup_mu;
 void* g_scratch_ptr[kFitMaxDevices] = {};
 
-bool is_device_ptr(const void* p) {
+// Device memory of the current device `dev` (or managed memory): a pointer to
+// another GPU's memory would be read by kernels running on this one.
+bool is_device_ptr(const void* p, int dev) {
   cudaPointerAttributes pa;
   if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+  if (pa.type == cudaMemoryTypeManaged) return true;
+  return pa.type == cudaMemoryTypeDevice && pa.device == dev;
 }
 
 }  // namespace
@@ -144,8 +154,9 @@ extern "C" edaa_status edaa_fit_eval_static(const float* X, int L, int N, int p,
   if (dev < 0 || dev >= kFitMaxDevices) return reject(EDAA_ERR_UNSUPPORTED, "edaa_fit_eval_static: device index");
   const void* ptrs[6] = {X, E, A, fit, fitmax, loss};
   for (const void* q : ptrs)
-    if (q && !is_device_ptr(q))
-      return reject(EDAA_ERR_ARG, "edaa_fit_eval_static: inputs and outputs must be device memory");
+    if (q && !is_device_ptr(q, dev))
+      return reject(EDAA_ERR_ARG,
+                    "edaa_fit_eval_static: inputs and outputs must be device memory of the current device");
   void* scratch = nullptr;
   {
     // One-time set-up per device, with that device current: the host-side
@@ -156,6 +167,10 @@ extern "C" edaa_status edaa_fit_eval_static(const float* X, int L, int N, int p,
       const cudaError_t e = cudaGetSymbolAddress(&ptr, g_fit_scratch);
       if (e != cudaSuccess || !ptr) {
         cudaGetLastError();
+        // the lookup loads the library's device image when nothing has yet
+        if (e == cudaErrorMemoryAllocation)
+          return reject(EDAA_ERR_OOM, "edaa_fit_eval_static: no device memory to load the library's device code "
+                                      "and static scratch (make one library call before reserving the GPU)");
         return reject(EDAA_ERR_CUDA, "edaa_fit_eval_static: cudaGetSymbolAddress of the static scratch failed");
       }
       g_scratch_ptr[dev] = ptr;

@@ -27,7 +27,7 @@ EXPORTS = ["edaa_config_default", "edaa_init", "edaa_reset", "edaa_step", "edaa_
            "edaa_select_rule", "edaa_get", "edaa_grad", "edaa_loss", "edaa_step_sizes", "edaa_sync",
            "edaa_outer_done", "edaa_describe", "edaa_destroy", "edaa_last_error", "edaa_selftest_barrier",
            "edaa_fit_eval_static", "edaa_unrolled_create", "edaa_unrolled_forward", "edaa_unrolled_backward",
-           "edaa_unrolled_destroy", "edaa_trace_read", "edaa_describe_tile"]
+           "edaa_unrolled_destroy", "edaa_trace_read", "edaa_describe_tile", "edaa_measure_fma_peak"]
 
 
 class Config(ctypes.Structure):
@@ -78,7 +78,7 @@ def load_library():
         "edaa_step_sizes": (ctypes.c_int, [vp, ctypes.c_int, dp, dp]),
         "edaa_sync": (ctypes.c_int, [vp]),
         "edaa_outer_done": (ctypes.c_int, [vp]),
-        "edaa_describe": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, ip, ip, ip]),
+        "edaa_describe": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, ip, ip, ip, ip]),
         "edaa_destroy": (None, [vp]),
         "edaa_last_error": (ctypes.c_char_p, []),
         "edaa_selftest_barrier": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, vp]),
@@ -90,6 +90,7 @@ def load_library():
         "edaa_unrolled_destroy": (None, [vp]),
         "edaa_trace_read": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip, ip, dp, dp]),
         "edaa_describe_tile": (ctypes.c_int, [vp, ctypes.c_int, ip]),
+        "edaa_measure_fma_peak": (ctypes.c_int, [dp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -272,9 +273,9 @@ class Context:
         return ph[:k], t0[:k], dt[:k]
 
     def describe(self, cube: int = 0) -> Dict[str, int]:
-        vals = [ctypes.c_int() for _ in range(5)]
+        vals = [ctypes.c_int() for _ in range(6)]
         _check(self.lib.edaa_describe(self.h, cube, *[ctypes.byref(v) for v in vals]), "edaa_describe")
-        keys = ["runs_per_group", "pixel_tile", "ctas_per_group", "grid", "launches_per_solve"]
+        keys = ["runs_per_group", "pixel_tile", "ctas_per_group", "grid", "launches_per_solve", "graph"]
         out = {k: v.value for k, v in zip(keys, vals)}
         tile = (ctypes.c_int * 4)()
         _check(self.lib.edaa_describe_tile(self.h, cube, tile), "edaa_describe_tile")
@@ -296,6 +297,15 @@ def fit_eval_static(X, E, A, stream=None):
     _check(lib.edaa_fit_eval_static(_ptr(X), L, N, p, M, _ptr(E), _ptr(A), _ptr(out[0]), _ptr(out[1]),
                                     _ptr(out[2]), s), "edaa_fit_eval_static")
     return out[0], out[1], out[2]
+
+
+def measure_fma_peak(stream=None) -> float:
+    """FP32 FMA throughput of the current device in TFLOP/s (edaa_measure_fma_peak)."""
+    lib = load_library()
+    out = ctypes.c_double(0.0)
+    s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream) if stream else None
+    _check(lib.edaa_measure_fma_peak(ctypes.byref(out), s), "edaa_measure_fma_peak")
+    return out.value
 
 
 def selftest_barrier(grid: int, extra: int, timeout_ms: float, stream=None) -> int:
