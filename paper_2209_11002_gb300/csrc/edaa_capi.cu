@@ -245,7 +245,7 @@ static size_t pass_item_smem(const CubeHost& h) {
     const int rb = std::min(h.tile.Rm, (8 / h.tile.WP1) * rq1_max(h.p));
     s = (size_t)pass_smem(h.L, h.Ls, h.Lr, h.p, rb, 128).total * 4;  // fit pass in run blocks
     const int rgp = round_up(h.tile.Rm * h.p, 16);  // the widest group this cube can take (smaller ones need less)
-    s = std::max(s, (size_t)tc_smem(rgp, h.esz, h.tc == 3, h.p).total);
+    s = std::max(s, (size_t)tc_smem_max(rgp, h.esz, h.tc == 3, h.p));
   }
   return s;
 }
@@ -266,7 +266,9 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
   };
   const size_t N = h.N, L = h.L, Mp = h.Mp, M = h.M, p = h.p, Ls = h.Ls;
   const size_t Nst = round_up(h.N, 32);  // state rows: one run column over the pixels
-  size_t oX = take(N * Ls * 4), oXin = take(N * L * 4), oA = take(Nst * Mp * 4), oB = take(Nst * Mp * 4);
+  const size_t tcb = h.tc ? 1 : 0, parts = h.tc == 3 ? 2 : 1;  // split operands: high and low copies
+  // tensor-core cubes keep no B logits (regenerated from the RNG, S and Lambda)
+  size_t oX = take(N * Ls * 4), oXin = take(N * L * 4), oA = take(Nst * Mp * 4), oB = take((1 - tcb) * Nst * Mp * 4);
   size_t oEf = take(L * Mp * 4), oEd = take(L * Mp * 8), oRf = take(L * Mp * 4), oXAt = take(L * Mp * 8);
   size_t oAAt = take(M * p * p * 8), olse = take(Mp * 4), oe1 = take(M * 4), oe2 = take(M * 4);
   size_t oe1d = take(M * 8), oe2d = take(M * 8), osig = take(M * 8);
@@ -276,10 +278,11 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
   size_t oseeds = take(M * 8), ogam = take(M * 8);
   size_t orho = take(L * Mp * 8), obref = take(Mp * 4);  // nlchunk <= L band chunks
   size_t ogpart = take(L * M * p * p * 8);
-  const size_t tcb = h.tc ? 1 : 0, parts = h.tc == 3 ? 2 : 1;  // split operands: high and low copies
   size_t oXk = take(tcb * parts * N * h.kp * h.esz), oXT = take(tcb * parts * (L + 1) * h.Npad * h.esz);
-  size_t opE = take(tcb * parts * Mp * h.kp * h.esz), opR = take(tcb * parts * Mp * h.kp * h.esz);
-  size_t otm = take(tcb * 8 * 128);
+  size_t opE = take(tcb * parts * Mp * h.kp * h.esz), opS = take(tcb * 2 * Mp * h.kp * h.esz);
+  size_t oSd = take(tcb * L * Mp * 8), oRd = take(tcb * L * Mp * 8), olam = take(tcb * Mp * 8);
+  size_t or16 = take(tcb * Nst * Mp * 2);
+  size_t otm = take(tcb * TM_COUNT * 128);
   size_t oscale = take(N * 8), oxbar = take(L * 8), osx = take((L + 1) * 8), obsum = take((size_t)normalize_blocks(h.N) * L * 8);
   if (assign) {
     char* b = (char*)h.arena;
@@ -287,7 +290,7 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
     d.X = (float*)(b + oX);
     h.X_in = (float*)(b + oXin);
     d.logA = (float*)(b + oA);
-    d.logB = (float*)(b + oB);
+    d.logB = h.tc ? nullptr : (float*)(b + oB);
     d.Ef = (float*)(b + oEf);
     d.Ed = (double*)(b + oEd);
     d.Rf = (float*)(b + oRf);
@@ -319,8 +322,13 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
     if (h.tc) {
       h.Xk = b + oXk;
       h.XT = b + oXT;
+      d.Xk = h.Xk;
       d.panelE = b + opE;
-      d.panelR = b + opR;
+      d.panelS = b + opS;
+      d.Sd = (double*)(b + oSd);
+      d.Rd = (double*)(b + oRd);
+      d.lamd = (double*)(b + olam);
+      d.r16 = (uint16_t*)(b + or16);
       h.tmaps = (CUtensorMap*)(b + otm);
       d.tmaps = h.tmaps;
     }
@@ -358,23 +366,23 @@ static edaa_status make_tmaps(edaa_ctx* c, CubeHost& h) {
   const CUtensorMapDataType dt = h.esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const cuuint32_t kch = 128 / h.esz, es[2] = {1, 1};
   const int rgp = round_up(h.tile.Rm * h.p, 16);
-  // [X pixel-major, X band-major, panel E, panel R], then with split operands
-  // the same four for the low parts, which follow the high parts in memory
-  CUtensorMap m[8];
+  // the operand maps (128-byte swizzle, K-major boxes), in TcMap order; with
+  // split operands the low parts follow the high parts in memory
+  CUtensorMap m[TM_COUNT];
+  memset(m, 0, sizeof m);
   const size_t nXk = (size_t)h.N * h.kp * h.esz, nXT = (size_t)(h.L + 1) * h.Npad * h.esz;
   const size_t nP = (size_t)h.Mp * h.kp * h.esz;
-  char* lo[4] = {(char*)h.Xk + nXk, (char*)h.XT + nXT, (char*)h.dev.panelE + nP, (char*)h.dev.panelR + nP};
-  struct Spec { void* ptr; cuuint64_t inner, outer; cuuint32_t box_outer; } spec[8] = {
-      {h.Xk, (cuuint64_t)h.kp, (cuuint64_t)h.N, 128},
-      {h.XT, (cuuint64_t)h.Npad, (cuuint64_t)(h.L + 1), 128},
-      {h.dev.panelE, (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp},
-      {h.dev.panelR, (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp},
-      {lo[0], (cuuint64_t)h.kp, (cuuint64_t)h.N, 128},
-      {lo[1], (cuuint64_t)h.Npad, (cuuint64_t)(h.L + 1), 128},
-      {lo[2], (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp},
-      {lo[3], (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp}};
-  const int nmaps = h.tc == 3 ? 8 : 4;
-  for (int i = 0; i < nmaps; ++i) {
+  struct Spec { void* ptr; cuuint64_t inner, outer; cuuint32_t box_outer; bool used; } spec[TM_STATE] = {
+      {h.Xk, (cuuint64_t)h.kp, (cuuint64_t)h.N, 128, true},
+      {h.XT, (cuuint64_t)h.Npad, (cuuint64_t)(h.L + 1), 128, true},
+      {h.dev.panelE, (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp, true},
+      {h.dev.panelS, (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp, true},
+      {(char*)h.Xk + nXk, (cuuint64_t)h.kp, (cuuint64_t)h.N, 128, h.tc == 3},
+      {(char*)h.XT + nXT, (cuuint64_t)h.Npad, (cuuint64_t)(h.L + 1), 128, h.tc == 3},
+      {(char*)h.dev.panelE + nP, (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp, h.tc == 3},
+      {(char*)h.dev.panelS + nP, (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp, true}};
+  for (int i = 0; i < TM_STATE; ++i) {
+    if (!spec[i].used) continue;
     const cuuint64_t dims[2] = {spec[i].inner, spec[i].outer};
     const cuuint64_t strides[1] = {spec[i].inner * (cuuint64_t)h.esz};
     const cuuint32_t box[2] = {kch, spec[i].box_outer};
@@ -382,6 +390,22 @@ static edaa_status make_tmaps(edaa_ctx* c, CubeHost& h) {
                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(EDAA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   }
+  {  // the log-abundance state, float32 Mp x Nst: boxes of 128 pixels x one run group's rows, unswizzled
+    const int Nst = round_up(h.N, 32);
+    const cuuint64_t dims[2] = {(cuuint64_t)Nst, (cuuint64_t)h.Mp};
+    const cuuint64_t strides[1] = {(cuuint64_t)Nst * 4};
+    const cuuint32_t box[2] = {128, (cuuint32_t)(h.tile.Rm * h.p)};
+    const CUresult r = enc(&m[TM_STATE], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h.dev.logA, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(EDAA_ERR_CUDA, "cuTensorMapEncodeTiled failed (state map)");
+    const cuuint64_t strides16[1] = {(cuuint64_t)Nst * 2};
+    const CUresult r2 = enc(&m[TM_R16], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, h.dev.r16, dims, strides16, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r2 != CUDA_SUCCESS) return fail(EDAA_ERR_CUDA, "cuTensorMapEncodeTiled failed (uniforms map)");
+  }
+  const int nmaps = TM_COUNT;
   CK(cudaMemcpyAsync(h.tmaps, m, nmaps * sizeof(CUtensorMap), cudaMemcpyHostToDevice, c->stream),
      "upload tensor maps");
   return EDAA_OK;
@@ -422,6 +446,11 @@ static edaa_status run_init(edaa_ctx* c) {
   for (auto& h : c->cubes) {
     CK(cudaMemsetAsync(h.dev.XAt, 0, (size_t)h.L * h.Mp * 8, c->stream), "zero");
     CK(cudaMemsetAsync(h.dev.AAt, 0, (size_t)h.M * h.p * h.p * 8, c->stream), "zero");
+    if (h.tc) {  // S and Lambda start from B^0 (no B-step taken); the B^0 uniforms
+      CK(cudaMemsetAsync(h.dev.Sd, 0, (size_t)h.L * h.Mp * 8, c->stream), "zero");
+      CK(cudaMemsetAsync(h.dev.lamd, 0, (size_t)h.Mp * 8, c->stream), "zero");
+      if (h.tc != 3) CK(launch_fill_r16(h.dev, c->stream), "B^0 uniforms");
+    }
   }
   edaa_status st = enqueue(c, MODE_INIT, 0, nullptr);
   if (st != EDAA_OK) return st;
@@ -436,8 +465,8 @@ static edaa_status sync_status(edaa_ctx* c) {
   if (st & kStatTimeout) {
     c->broken = true;
     char msg[160];
-    snprintf(msg, sizeof msg, "a bounded wait timed out (status 0x%x: bit 0 grid barrier; bits 9-13 tensor-core "
-             "pipeline stages)", st);
+    snprintf(msg, sizeof msg, "a bounded wait timed out (status 0x%x: bit 0 grid barrier; bits 9-14 tensor-core "
+             "pipeline stages and the A state tile)", st);
     return fail(EDAA_ERR_TIMEOUT, msg);
   }
   return EDAA_OK;

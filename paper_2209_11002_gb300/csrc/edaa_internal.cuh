@@ -25,6 +25,17 @@
 //   part  Pg x Mp x (L+1)  per-CTA partial sums of X W, one column of W after
 //                  another (band L: sum of W), so that lanes holding
 //                  consecutive bands write consecutive addresses
+// Tensor-core cubes keep no B logits: eq. (update_B)'s gradient row of pixel
+// i is x_i^T R, linear in the pixel, so after s B-steps the logits are
+//     u_i = 0.1 r_i - Lambda - x_i^T S,   S = sum over the steps of eta2 R
+// (r: the SplitMix64 uniforms of eq. initB0, Lambda: the per-column sum of
+// the log-normalisers).  The B-pass regenerates them from r, S and Lambda:
+//   Sd    L x Mp   S after the last completed B-step (float64)
+//   Rd    L x Mp   R in float64 (the B-merge commits Sd += eta2 Rd of the
+//                  step just taken)
+//   lamd  Mp       Lambda after the last completed B-step (float64)
+//   panelS Mp x kp the next B-pass's S + eta2 R, K-major, as a high and a
+//                  low part in the compute type (two MMAs per product)
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -108,9 +119,40 @@ struct CubeDev {
   int tc_nkc;   // 128-byte K chunks over the bands (contraction 1)
   int tc_nbt;   // 128-band tiles (contraction 2)
   int tc_kp;    // row length (elements) of the K-major X copy and panels
-  const CUtensorMap* tmaps;  // [X pixel-major, X band-major, panel E, panel R]
+  const CUtensorMap* tmaps;  // TM_COUNT maps in TcMap order
+  const void* Xk;            // N x tc_kp compute-type copy of the centred X (split: then its low part)
   void* panelE;              // Mp x tc_kp, compute type (K-major E^T)
-  void* panelR;              // Mp x tc_kp, compute type (K-major R^T)
+  void* panelS;              // 2 x Mp x tc_kp, compute type: high, then low part of (S + eta2 R)^T
+  double* Sd;                // L x Mp: S of the last completed B-step (tensor-core cubes)
+  double* Rd;                // L x Mp: R in float64 (tensor-core cubes)
+  double* lamd;              // Mp: Lambda of the last completed B-step (tensor-core cubes)
+  uint16_t* r16;             // Mp x Nst: the B^0 uniforms of tensor-core cubes in 16-bit fixed point
+};
+
+// The TF32 and BF16 tensor-core passes read the uniforms of eq. (initB0)
+// from a table filled once per initialisation: entry (column c = m p + j,
+// pixel i) is the top 16 bits q of SplitMix64 output i p + j + 1 of run m's
+// seed, and the uniform is (q + 1/2) 2^-16, within 2^-17 of the 24-bit draw
+// the CUDA-core passes use (the logits 0.1 u differ by at most 7.6e-7, far
+// below those modes' operand rounding).  The split-operand mode, held to the
+// FP32 path's accuracy, draws the 24-bit uniforms in the pass instead: near
+// uniform B the B-gradient factor cancels to the deviation of B^0 from
+// uniform (about 3 %), which magnifies the table's error about 30-fold.
+constexpr float kR16Scale = 0.1f / 65536.f;
+
+// Tensor maps of a tensor-core cube, in this order.
+enum TcMap {
+  TM_X = 0,      // X pixel-major (contraction 1's A operand)
+  TM_XT = 1,     // X band-major (contraction 2's A operand)
+  TM_E = 2,      // panel E (A-pass contraction 1)
+  TM_S = 3,      // panel S + eta2 R, high part (B-pass contraction 1)
+  TM_XLO = 4,    // split operands: low parts of X, X band-major, E
+  TM_XTLO = 5,
+  TM_ELO = 6,
+  TM_SLO = 7,    // panel S + eta2 R, low part
+  TM_STATE = 8,  // the log-abundance state (Mp x Nst float32), boxes of 128 pixels x one run group
+  TM_R16 = 9,    // the B^0 uniforms (Mp x Nst uint16), same boxes
+  TM_COUNT = 10
 };
 
 struct Batch {
@@ -201,6 +243,7 @@ cudaError_t program_occupancy(int* blocks_per_sm, size_t smem);
 int program_phase_count(int mode, int n_outer, int K2);
 int program_phase_id(int mode, int s, int K2);
 cudaError_t launch_tc_prepare(const CubeDev& hc, void* Xk, void* XT, int Npad, cudaStream_t s);
+cudaError_t launch_fill_r16(const CubeDev& hc, cudaStream_t s);
 cudaError_t launch_fma_peak(float* out, int blocks, int iters, cudaStream_t s);
 double fma_peak_flops_per_launch(int blocks, int iters);
 

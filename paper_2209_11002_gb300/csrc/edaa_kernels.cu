@@ -67,6 +67,24 @@ __device__ __forceinline__ void store_panel(const CubeDev& cd, void* panel, int 
   }
 }
 
+// The B-pass panel of a tensor-core cube: v = S + eta2 R (column c, band l)
+// as a high part and a low part in the compute type, v ~ hi + lo to about
+// 2^-17 (BF16) or 2^-22 (TF32) relative; contraction 1 adds both products.
+__device__ __forceinline__ void store_panel_s(const CubeDev& cd, int c, int l, double v) {
+  const size_t o = (size_t)c * cd.tc_kp + l, lo = (size_t)cd.Mp * cd.tc_kp;
+  if (cd.tc == 2) {
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+    __nv_bfloat16* ps = reinterpret_cast<__nv_bfloat16*>(cd.panelS);
+    ps[o] = h;
+    ps[lo + o] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+  } else {
+    const float h = tf32_rna((float)v);
+    float* ps = reinterpret_cast<float*>(cd.panelS);
+    ps[o] = h;
+    ps[lo + o] = tf32_rna((float)(v - (double)h));
+  }
+}
+
 // rho[lc][c] = sum over the chunk's bands of E[l][c] R[l][c], in a fixed
 // order (lanes strided over the bands, then a butterfly): the reference
 // exponent of the next B-pass is derived from these sums.
@@ -187,8 +205,12 @@ __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
     cd.XAt[(size_t)l * Mp + c0 + j] = xat;
     double r = -xat;
     for (int k = 0; k < P; ++k) r += sE[li * P + k] * saat[k * P + j];
-    cd.Rf[(size_t)l * Mp + c0 + j] = (float)r;
-    if (cd.tc) store_panel(cd, cd.panelR, c0 + j, l, r);
+    const size_t o = (size_t)l * Mp + c0 + j;
+    cd.Rf[o] = (float)r;
+    if (cd.tc) {  // the next B-pass contracts X with S + eta2 R
+      cd.Rd[o] = r;
+      store_panel_s(cd, c0 + j, l, cd.Sd[o] + cd.eta2d[m] * r);
+    }
     sprod[e] = sE[e] * r;
   }
   __syncthreads();
@@ -202,7 +224,12 @@ __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
 // E = X B = (sum_g 2^(e_g-mx) part_g + 2^(k-mx) sum_i x_i) / S, and the
 // stored lse is mx ln 2 + log S - log N (logits live in the frame log(N b)).
 // Then G = E^T E (chunk sums) and R = E A A^T - X A^T for the next pass.
-__device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem) {
+// Tensor-core cubes keep no B logits (they are u = 0.1 r - Lambda - x^T S):
+// a B-merge after a B-step (commit) first adds that step's eta2 R to S, and
+// its lc == 0 unit adds the step's log-normaliser to Lambda (the first
+// B-merge, after the initial pass, sets Lambda); the new R then gives the
+// next B-pass's panel S + eta2 R.
+__device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool commit) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int P = cd.p, L = cd.L, Mp = cd.Mp, Pg = cd.Pg, c0 = m * P;
   const MergeSmem ms = merge_smem(cd.lchunk, P, Pg);
@@ -252,7 +279,9 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem) {
       // own rounding; this GPU's FP64 pipe makes a double log cost microseconds.
       int ex = 0;
       const double f = frexp(S, &ex);
-      cd.lse[c] = (float)((mx + (double)ex) * 0.69314718055994531 + (double)logf((float)f) - cd.logN);
+      const double lse = (mx + (double)ex) * 0.69314718055994531 + (double)logf((float)f) - cd.logN;
+      cd.lse[c] = (float)lse;
+      if (cd.tc) cd.lamd[c] = (commit ? cd.lamd[c] : 0.0) + lse;
     }
     sw[j] = wref;
     sw[kMaxP + j] = 1.0 / S;
@@ -277,12 +306,22 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem) {
       g = warp_sum(g);
       if (lane == 0) cd.gpart[((size_t)lc * cd.M + m) * P * P + e] = g;
     }
+  const double eta2 = cd.tc ? cd.eta2d[m] : 0.0;
   for (int e = tid; e < nl * P; e += kThreads) {
     const int li = e / P, l = l0 + li, j = e - li * P;
     double r = -sxa[e];
     for (int k = 0; k < P; ++k) r += sE[li * P + k] * saat[k * P + j];
-    cd.Rf[(size_t)l * Mp + c0 + j] = (float)r;
-    if (cd.tc) store_panel(cd, cd.panelR, c0 + j, l, r);
+    const size_t o = (size_t)l * Mp + c0 + j;
+    cd.Rf[o] = (float)r;
+    if (cd.tc) {
+      double sv = cd.Sd[o];
+      if (commit) {  // the step just taken used R from the previous merge
+        sv += eta2 * cd.Rd[o];
+        cd.Sd[o] = sv;
+      }
+      cd.Rd[o] = r;
+      store_panel_s(cd, c0 + j, l, sv + eta2 * r);
+    }
     sprod[e] = sE[e] * r;
   }
   __syncthreads();
@@ -297,7 +336,7 @@ __device__ void merge_phase(const Batch* __restrict__ bt, int ph, float* smem) {
     const int local = u - cd.unit0;
     const int m = local / cd.nlchunk, lc = local - m * cd.nlchunk;
     if (ph == PH_AM) merge_a_unit(cd, m, lc, smem);
-    else merge_b_unit(cd, m, lc, smem);
+    else merge_b_unit(cd, m, lc, smem, ph == PH_BM);
   }
 }
 
@@ -704,9 +743,47 @@ __global__ void k_gather_ab(const float* logA, const float* logB, const float* l
   if (B) B[e] = (float)exp((double)logB[src] - (double)lse[m * p + j] - log((double)N));
 }
 
+// B of a tensor-core cube, regenerated: b_i = exp(0.1 r_i - Lambda - x_i^T S - log N),
+// one thread per entry, FP64.  x is the centred pixel as contraction 1 saw it
+// (the compute-type copy Xk: BF16, TF32, or the sum of its two TF32 parts),
+// so that b is the B the solve's logits and normalisers describe.
+__global__ void k_gather_b_regen(const void* __restrict__ Xk, int kp, int tc, const double* __restrict__ Sd,
+                                 const double* __restrict__ lamd, const uint16_t* __restrict__ r16,
+                                 const uint64_t* __restrict__ seeds, int Nst, int L, int N, int Mp, int p, int m,
+                                 double logN, float* __restrict__ B) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * p) return;
+  const int i = e / p, j = e % p, c = m * p + j;
+  double dot = 0.0;
+  for (int l = 0; l < L; ++l) {
+    const size_t o = (size_t)i * kp + l;
+    double x;
+    if (tc == 2) {
+      x = (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(Xk)[o]);
+    } else {
+      const float* xf = reinterpret_cast<const float*>(Xk);
+      x = (double)xf[o] + (tc == 3 ? (double)xf[(size_t)N * kp + o] : 0.0);
+    }
+    dot += x * Sd[(size_t)l * Mp + c];
+  }
+  // as the tensor-core passes read it: the 16-bit table, or (split operands) the 24-bit draw
+  const float u0 = tc == 3 ? 0.1f * uniform24(seeds[m], (uint64_t)i * p + j + 1)
+                           : ((float)r16[(size_t)c * Nst + i] + 0.5f) * kR16Scale;
+  B[e] = (float)exp((double)u0 - lamd[c] - dot - logN);
+}
+
 cudaError_t launch_gather(const CubeDev& hc, int run, float* E, float* A, float* B, cudaStream_t s) {
   if (E) k_gather_e<<<(hc.L * hc.p + 255) / 256, 256, 0, s>>>(hc.Ed, hc.xbar, hc.L, hc.Mp, hc.p, run, E);
-  if (A || B) k_gather_ab<<<(hc.N * hc.p + 255) / 256, 256, 0, s>>>(hc.logA, hc.logB, hc.lse, hc.N, hc.Nst, hc.p, run, A, B);
+  if (hc.tc) {
+    if (A) k_gather_ab<<<(hc.N * hc.p + 255) / 256, 256, 0, s>>>(hc.logA, nullptr, nullptr, hc.N, hc.Nst, hc.p, run, A,
+                                                                 nullptr);
+    if (B)
+      k_gather_b_regen<<<(hc.N * hc.p + 255) / 256, 256, 0, s>>>(hc.Xk, hc.tc_kp, hc.tc, hc.Sd, hc.lamd, hc.r16,
+                                                                 hc.seeds, hc.Nst, hc.L, hc.N, hc.Mp, hc.p, run,
+                                                                 hc.logN, B);
+  } else if (A || B) {
+    k_gather_ab<<<(hc.N * hc.p + 255) / 256, 256, 0, s>>>(hc.logA, hc.logB, hc.lse, hc.N, hc.Nst, hc.p, run, A, B);
+  }
   return cudaGetLastError();
 }
 
@@ -737,6 +814,24 @@ __global__ void k_tc_prepare(const float* __restrict__ X, int L, int Ls, int N, 
       }
     }
   }
+}
+
+// The uniforms of eq. (initB0) for the tensor-core passes: r16[c][i] = top 16
+// bits of SplitMix64 output i p + j + 1 of run m's seed (c = m p + j); the
+// padding pixels [N, Nst) hold 0.
+__global__ void k_fill_r16(const uint64_t* __restrict__ seeds, int N, int Nst, int p, int Mp,
+                           uint16_t* __restrict__ r16) {
+  const size_t n = (size_t)Mp * Nst;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / Nst), i = (int)(e - (size_t)c * Nst);
+    const int m = c / p, j = c - m * p;
+    r16[e] = i < N ? (uint16_t)(splitmix64_out(seeds[m], (uint64_t)i * p + j + 1) >> 48) : (uint16_t)0;
+  }
+}
+
+cudaError_t launch_fill_r16(const CubeDev& hc, cudaStream_t s) {
+  k_fill_r16<<<1024, 256, 0, s>>>(hc.seeds, hc.N, hc.Nst, hc.p, hc.Mp, hc.r16);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_tc_prepare(const CubeDev& hc, void* Xk, void* XT, int Npad, cudaStream_t s) {

@@ -102,11 +102,14 @@ __device__ __forceinline__ float shifted_weight(float u, float Mn, int k) {
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output number n of the
 // generator seeded with `seed` is the variant-13 finaliser of seed + n*gamma.
-__device__ __forceinline__ uint64_t splitmix64_out(uint64_t seed, uint64_t n) {
-  uint64_t z = seed + n * 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kSplitMixGamma = 0x9E3779B97F4A7C15ull;
+__device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t splitmix64_out(uint64_t seed, uint64_t n) {
+  return splitmix64_mix(seed + n * kSplitMixGamma);
 }
 // u ~ U[0,1) with 24 bits, exact in float32 (eq. initB0)
 __device__ __forceinline__ float uniform24(uint64_t seed, uint64_t n) {

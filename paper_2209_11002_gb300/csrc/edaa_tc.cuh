@@ -4,14 +4,21 @@
 // Per CTA: one run group (Rg = Rm*p columns, padded to Rgp, a multiple of
 // 16) and the pixel tiles pg, pg + Pg, ... of 128 pixels.  Per tile:
 //   1. C (128 px x Rgp) = X_tile (128 x L) * Panel^T: the tile's pixel-major
-//      rows and the panel (E for the A-pass, R for the B-pass, stored K-major
-//      as Mp x Kp) stream through a ring of TMA stages (128-byte swizzle,
-//      K-major) into tcgen05.mma with the accumulator in TMEM columns [0, Rgp).
+//      rows and the panel stream through a ring of TMA stages (128-byte
+//      swizzle, K-major) into tcgen05.mma with the accumulator in TMEM columns
+//      [0, Rgp).  The A-pass's panel is E.  The B-pass's is S + eta2 R, the
+//      running sum of eta2 times the B-gradient factors R of every B-step so
+//      far (eq. update_B), as a high and a low part (two MMAs per K chunk).
 //   2. Epilogue (8 warps; warp w reads TMEM lanes 32*(w%4).. = its pixels and
-//      handles the runs of parity w/4): the per-run element-wise step of the
-//      CUDA-core pass (K1 fused A-steps, or the B-logit update and online
-//      softmax in the power-of-two frame), writing the new state to global
-//      memory and W = weights - reference (shifted accumulation) into shared
+//      handles the runs of parity w/4):
+//      A: the tile's log-abundance state arrives in shared memory by one TMA
+//         load issued before contraction 1; the K1 fused A-steps update it in
+//         place and one TMA store writes it back.
+//      B: no per-pixel state.  The logits are u = 0.1 r - Lambda - C, with r
+//         the SplitMix64 uniforms of B^0 regenerated in registers (eq.
+//         initB0); u goes back into C's TMEM columns while the column maxima
+//         are formed, and the weights are computed from there.
+//      Both write W = weights - reference (shifted accumulation) into shared
 //      memory in the swizzled K-major layout the MMA reads.
 //   3. Acc (bands x Rgp) += X_bands (128 bands x 128 px) * W^T for each
 //      128-band tile, the band-major copy of X streaming through the same TMA
@@ -132,46 +139,75 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-struct TcSmem {
-  uint32_t stage_bytes, w_off, misc_off, total;
-};
-// Shared memory of a tensor-core pass.  A ring stage
-// holds one 128 x 128-byte chunk of X and the panel chunk (Rgp x 128 B; with
-// split operands both the high and the low part); W holds the weights of one
-// 128-pixel tile in 128-byte pixel chunks (split: high and low part); the
-// misc region holds the barriers and flags (256 B), seven 256-entry column
-// arrays, the step sizes (128), G (2048) and the A A^T sums (4 x Rm x PP with
-// Rm <= Rgp / p); 1 KB alignment slack.
-__host__ __device__ inline uint32_t tc_misc_bytes(int Rgp, int p) {
-  const uint32_t rm = (uint32_t)(Rgp / p), pp = (uint32_t)(p * (p + 1) / 2);
-  return (256u + 7u * 256u * 4u + 128u * 4u + 2048u * 4u + 4u * rm * pp * 4u + 1023u) & ~1023u;
-}
-__host__ __device__ inline TcSmem tc_smem(int Rgp, int esz, bool split, int p) {
-  TcSmem s;
-  const uint32_t pnl = ((uint32_t)Rgp * 128u + 1023u) & ~1023u;
-  const uint32_t parts = split ? 2u : 1u;
-  s.stage_bytes = 128u * 128u + parts * pnl;
-  const uint32_t npc = 128u / (128u / (uint32_t)esz);  // pixel chunks of 128 bytes per 128-pixel tile
-  s.w_off = 1024u + (uint32_t)kTcStages * s.stage_bytes;
-  s.misc_off = s.w_off + parts * npc * pnl;
-  s.total = s.misc_off + tc_misc_bytes(Rgp, p);
-  return s;
-}
 // 226 KB: one CTA's 227 KB of shared memory less 1 KB for the program
 // kernel's static shared memory
 constexpr uint32_t kTcSmemCap = 232448u - 1024u;
 
+struct TcSmem {
+  uint32_t stages, stage_bytes, w_off, state_off, misc_off, total;
+};
+// Shared memory of a tensor-core pass, per pass kind.  A ring stage holds one
+// 128 x 128-byte chunk of X and the panel chunks (Rgp x 128 B each): the
+// A-pass's panel E (split operands: its high and low part), the B-pass's
+// panel S + eta2 R as a high and a low part.  W holds the weights of one
+// 128-pixel tile in 128-byte pixel chunks (split: high and low part).  The
+// tile's slice of a per-pixel table follows (Rgp rows of 128 pixels): the
+// A-pass's log-abundance state, the B-pass's B^0 uniforms.  The misc region
+// holds the barriers and flags (256 B), eight 256-entry column arrays, the
+// step sizes (128), G (2048) and the A A^T sums (4 x Rm x PP with
+// Rm <= Rgp / p); 1 KB alignment slack.
+__host__ __device__ inline uint32_t tc_misc_bytes(int Rgp, int p) {
+  const uint32_t rm = (uint32_t)(Rgp / p), pp = (uint32_t)(p * (p + 1) / 2);
+  return (256u + 8u * 256u * 4u + 128u * 4u + 2048u * 4u + 4u * rm * pp * 4u + 1023u) & ~1023u;
+}
+__host__ __device__ inline TcSmem tc_smem_n(int Rgp, int esz, bool split, int p, bool is_a, uint32_t stages) {
+  TcSmem s;
+  const uint32_t pnl = ((uint32_t)Rgp * 128u + 1023u) & ~1023u;
+  const uint32_t pparts = (split || !is_a) ? 2u : 1u;
+  const uint32_t wparts = split ? 2u : 1u;
+  const uint32_t npc = (uint32_t)esz;  // 128-byte pixel chunks per 128-pixel tile (128 / (128 / esz))
+  s.stages = stages;
+  s.stage_bytes = 128u * 128u + pparts * pnl;
+  s.w_off = 1024u + stages * s.stage_bytes;
+  s.state_off = s.w_off + wparts * npc * pnl;
+  // the per-tile slice of a per-pixel table: A the state (float), B the B^0 uniforms (uint16)
+  s.misc_off = s.state_off + (((uint32_t)Rgp * (is_a ? 512u : 256u) + 1023u) & ~1023u);
+  s.total = s.misc_off + tc_misc_bytes(Rgp, p);
+  return s;
+}
+// three ring stages where they fit in one CTA's shared memory, else two
+__host__ __device__ inline TcSmem tc_smem(int Rgp, int esz, bool split, int p, bool is_a) {
+  TcSmem s = tc_smem_n(Rgp, esz, split, p, is_a, (uint32_t)kTcStages);
+  if (s.total > kTcSmemCap) s = tc_smem_n(Rgp, esz, split, p, is_a, 2u);
+  return s;
+}
+__host__ __device__ inline uint32_t tc_smem_max(int Rgp, int esz, bool split, int p) {
+  const uint32_t a = tc_smem(Rgp, esz, split, p, true).total, b = tc_smem(Rgp, esz, split, p, false).total;
+  return a > b ? a : b;
+}
 
 // Largest padded run-group width (a multiple of 16): TMEM holds C (Rgp
 // columns) and one Acc per 128-band tile (split operands: a per-tile Acc and
 // a running sum per band tile), with 8 spare columns so that the 8-wide TMEM
-// reads of the last run stay inside the 512 allocated; the shared memory
-// above stays within kTcSmemCap.
+// reads of the last run stay inside the 512 allocated; the shared memory of
+// both pass kinds stays within kTcSmemCap.
 __host__ __device__ inline int tc_rgp_max(int L, int esz, bool split, int p) {
   const int nbt = (L + 1 + 127) / 128;
   int r = ((512 - 8) / (1 + (split ? 2 : 1) * nbt)) & ~15;
-  while (r > 16 && tc_smem(r, esz, split, p).total > kTcSmemCap) r -= 16;
+  while (r > 16 && tc_smem_max(r, esz, split, p) > kTcSmemCap) r -= 16;
   return r;
 }
+
+// TMA tensor store shared -> global (bulk group), its commit and waits.
+__device__ __forceinline__ void tma2d_store(const CUtensorMap* m, int c0, int c1, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(m), "r"(c0),
+               "r"(c1), "r"(su32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the stores' reads of shared memory are done (the buffer may be rewritten)
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// the stores are complete in global memory
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 }  // namespace edaa

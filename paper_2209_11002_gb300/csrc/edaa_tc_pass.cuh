@@ -5,6 +5,50 @@
 
 namespace edaa {
 
+// tcgen05.st of P (1..8) consecutive 32-bit TMEM columns from v (32 lanes,
+// warp-collective), then the wait for the stores.  The callers store at
+// column r*P: for P = 1, 2, 4, 8 that is a multiple of the width and one
+// .xP store is used; other P store column by column.
+template <int P>
+__device__ __forceinline__ void tmem_st_p(uint32_t ta, const float (&v)[P]) {
+  if constexpr (P == 8) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+  } else if constexpr (P == 4) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ta), "r"(__float_as_uint(v[0])),
+                 "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3]))
+                 : "memory");
+  } else if constexpr (P == 2) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(ta), "r"(__float_as_uint(v[0])),
+                 "r"(__float_as_uint(v[1]))
+                 : "memory");
+  } else {
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(ta + (uint32_t)j), "r"(__float_as_uint(v[j]))
+                   : "memory");
+  }
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// 0.1 u for the P entries of pixel i of a run with seed `seed`: u from
+// SplitMix64 outputs i*P + j + 1, top 24 bits (eq. initB0), bit for bit the
+// values of the CUDA-core passes (the split-operand pass, which is held to
+// the FP32 path's accuracy, draws them here instead of reading the 16-bit
+// table).  Consecutive outputs differ by one gamma increment of the state.
+template <int P>
+__device__ __forceinline__ void initial_logits(uint64_t seed, uint64_t i, float (&u0)[P]) {
+  uint64_t z = seed + (i * (uint64_t)P + 1ull) * kSplitMixGamma;
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    u0[j] = 0.1f * ((float)(splitmix64_mix(z) >> 40) * (1.0f / 16777216.0f));
+    z += kSplitMixGamma;
+  }
+}
+
 // PREC: 0 TF32, 1 BF16, 2 split TF32 (x = hi + lo; products hi*hi + hi*lo + lo*hi,
 // and the element-wise steps in full FP32 as in the CUDA-core pass).
 template <int P, bool IS_A, int PREC>
@@ -12,27 +56,31 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
                                           unsigned char* smem_raw, int K1, bool init) {
   constexpr bool BF = PREC == 1, SPLIT = PREC == 2;
   constexpr int SUB = SPLIT ? 2 : 1;  // stream chunks per 128-byte K chunk (split: high part, then low part)
+  constexpr bool TWO = SPLIT || !IS_A;  // contraction 1 reads a high and a low panel part
   constexpr int PP = P * (P + 1) / 2;
   constexpr int ESZ = BF ? 2 : 4;
   constexpr int KCH = 128 / ESZ;   // elements per 128-byte row (32 tf32, 64 bf16)
   constexpr int NPC = 128 / KCH;   // pixel chunks per 128-pixel tile
   constexpr uint32_t FMT = BF ? 1u : 2u;
-  constexpr int kRB = 4;           // runs whose state is loaded together in the B epilogue
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int quarter = warp & 3, half = warp >> 2;
   const int L = cd.L, N = cd.N, Mp = cd.Mp, Rm = cd.Rm;
   const int m0 = rg * Rm, nr = min(Rm, cd.M - m0), c0 = m0 * P, nc = nr * P;
   const int Rgp = cd.tc_rgp, nkc = cd.tc_nkc, nbt = cd.tc_nbt;
   const long long tmo = bt->timeout_ns;
-  const CUtensorMap* tmX = cd.tmaps + 0;
-  const CUtensorMap* tmXT = cd.tmaps + 1;
-  const CUtensorMap* tmPan = cd.tmaps + (IS_A ? 2 : 3);
-  const CUtensorMap* tmXlo = cd.tmaps + 4;  // split operands: the low parts
-  const CUtensorMap* tmXTlo = cd.tmaps + 5;
-  const CUtensorMap* tmPanLo = cd.tmaps + (IS_A ? 6 : 7);
-  const TcSmem S = tc_smem(Rgp, ESZ, SPLIT, P);
+  const CUtensorMap* tmX = cd.tmaps + TM_X;
+  const CUtensorMap* tmXT = cd.tmaps + TM_XT;
+  const CUtensorMap* tmPan = cd.tmaps + (IS_A ? TM_E : TM_S);
+  const CUtensorMap* tmXlo = cd.tmaps + TM_XLO;  // split operands: the low parts
+  const CUtensorMap* tmXTlo = cd.tmaps + TM_XTLO;
+  const CUtensorMap* tmPanLo = cd.tmaps + (IS_A ? TM_ELO : TM_SLO);
+  const CUtensorMap* tmState = cd.tmaps + (IS_A ? TM_STATE : TM_R16);
+  const TcSmem S = tc_smem(Rgp, ESZ, SPLIT, P, IS_A);
+  const uint32_t NS = S.stages;
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* Wsm = sm + (S.w_off - 1024u);
+  float* Sst = reinterpret_cast<float*>(sm + (S.state_off - 1024u));  // A: state [column][128 pixels]
+  const uint16_t* R16 = reinterpret_cast<const uint16_t*>(Sst);       // B: uniforms [column][128 pixels]
   const uint32_t wchunk = ((uint32_t)Rgp * 128u + 1023u) & ~1023u;
   const uint32_t pnl = wchunk;  // a panel chunk (Rgp rows of 128 B), 1024-byte aligned in its stage
   unsigned char* misc = sm + (S.misc_off - 1024u);
@@ -40,16 +88,22 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   uint64_t* empty = full + kTcStages;                      // kTcStages
   uint64_t* bar_c1 = empty + kTcStages;
   uint64_t* bar_c2 = bar_c1 + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_c2 + 1);
+  uint64_t* bar_st = bar_c2 + 1;                           // A: the state tile's TMA load
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_st + 1);
   int* flags = reinterpret_cast<int*>(tmem_slot + 4);      // [0] bail, [1] rescale needed
-  float* colM = reinterpret_cast<float*>(flags + 4);       // Rgp: running power-of-two exponent (B)
-  int* colKey = reinterpret_cast<int*>(colM + 256);        // Rgp: tile maximum logit (B)
-  float* colScale = reinterpret_cast<float*>(colKey + 256);  // Rgp
-  float* colLse = colScale + 256;                          // Rgp
-  float* runEta = colLse + 256;                            // Rm (<= 128)
+  // B: every column keeps its weights as e^u 2^-F in a power-of-two frame F
+  // (exact rescales); F starts at the reference exponent k and follows the
+  // largest logit seen, one tile late
+  float* colF = reinterpret_cast<float*>(flags + 4);       // Rgp: frame F of Acc and of this tile's weights (B)
+  int* colKey = reinterpret_cast<int*>(colF + 256);        // Rgp: tile maximum logit (B)
+  float* colScale = reinterpret_cast<float*>(colKey + 256);  // Rgp: 2^(F - Fn), the pending rescale (B)
+  float* colLam = colScale + 256;                          // Rgp: Lambda, the logits' offset (B)
+  float* runEta = colLam + 256;                            // Rm (<= 128)
   int* colRef = reinterpret_cast<int*>(runEta + 128);      // Rgp: reference exponent k (B)
-  float* colRefW = reinterpret_cast<float*>(colRef + 256);  // Rgp: 2^(k - Mn), the reference weight (B)
-  float* Gs = colRefW + 256;                               // Rm x P x P (A), <= 2048
+  float* colRefW = reinterpret_cast<float*>(colRef + 256);  // Rgp: 2^(k - F), the reference weight (B)
+  float* colFn = colRefW + 256;                            // Rgp: the frame after this tile (B)
+  float* colC = colFn + 256;                               // Rgp: (kR16Scale / 2 - Lambda) log2 e - F (B)
+  float* Gs = colC + 256;                                  // Rm x P x P (A), <= 2048
   float* aaq = Gs + 2048;                                  // 4 x Rm x PP (A)
 
   // ---- set-up: barriers, TMEM (512 columns: one CTA per SM), per-run constants
@@ -64,25 +118,31 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     }
     mbar_init(bar_c1, 1);
     mbar_init(bar_c2, 1);
+    mbar_init(bar_st, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     flags[0] = 0;
     flags[1] = 0;
+    flags[2] = 0;
   }
   for (int c = tid; c < 256; c += kThreads) {
-    colM[c] = -EDAA_INF;
     colKey[c] = ord_key(-EDAA_INF);
     colScale[c] = 1.f;
-    colLse[c] = 0.f;
-    colRefW[c] = 0.f;
+    colLam[c] = 0.f;
   }
   if (!IS_A)
     for (int c = tid; c < 256; c += kThreads) {
+      // k is a lower bound of log2 of the column's mean weight, so its largest
+      // weight is at least 2^(k - 1/2): a first frame of k never underflows
       const int k = (!init && c < nc) ? ref_exponent(cd, m0 + c / P, c0 + c) : 0;
       colRef[c] = k;
+      colF[c] = (float)k;
+      colFn[c] = (float)k;
+      colRefW[c] = 1.f;
       if (c < nc) {
-        if (!init) colLse[c] = cd.lse[c0 + c];
+        if (!init) colLam[c] = (float)cd.lamd[c0 + c];
         if (pg == 0) cd.bref[c0 + c] = k;
       }
+      colC[c] = (0.5f * kR16Scale - colLam[c]) * kLog2e - (float)k;
     }
   for (int r = tid; r < Rm; r += kThreads) runEta[r] = r < nr ? (IS_A ? cd.eta1[m0 + r] : cd.eta2[m0 + r]) : 0.f;
   if (IS_A) {
@@ -104,13 +164,14 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   const uint32_t tbase = *tmem_slot;
   const uint32_t id = tc_idesc(128, Rgp, FMT);
   const bool do_c1 = !init;
+  // one TMA box of the tile's table slice: 128 pixels x the group's rows (A: float, B: uint16)
+  const uint32_t state_bytes = 128u * (IS_A ? 4u : 2u) * (uint32_t)(Rm * P);
 
   // ---- the chunk stream (thread 0).  Per tile: contraction 1 (nkc chunks of X
   // and the panel; not in the initial passes), then contraction 2 (nbt * NPC
-  // chunks of the band-major X).  Chunk k uses ring stage k % kTcStages.  Loads
-  // run up to kTcStages chunks ahead of the MMAs, so contraction 2's X streams
-  // in during the epilogue and the next tile's contraction 1 during
-  // contraction 2.
+  // chunks of the band-major X).  Chunk k uses ring stage k % NS.  Loads run
+  // up to NS chunks ahead of the MMAs, so contraction 2's X streams in during
+  // the epilogue and the next tile's contraction 1 during contraction 2.
   const int nc1 = do_c1 ? nkc * SUB : 0;
   const int nc2 = nbt * NPC * SUB;
   const int per_tile = nc1 + nc2;
@@ -118,14 +179,14 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   const uint32_t total = (uint32_t)(ntl * per_tile);
   uint32_t loaded = 0, issued = 0;
   auto load_chunk = [&](uint32_t k) -> bool {
-    const uint32_t s = k % kTcStages;
-    if (k >= kTcStages && !mbar_wait(empty + s, ((k / kTcStages) + 1) & 1, tmo)) return false;
+    const uint32_t s = k % NS;
+    if (k >= NS && !mbar_wait(empty + s, ((k / NS) + 1) & 1, tmo)) return false;
     const int q = (int)(k / (uint32_t)per_tile), j = (int)(k - (uint32_t)(q * per_tile));
     const int ti0 = (pg + q * cd.Pg) * kTcTile;
     unsigned char* dst = sm + s * S.stage_bytes;
-    if (j < nc1) {  // X chunk + panel chunk (split: [X hi | P hi | P lo], then [X lo | P hi])
+    if (j < nc1) {  // X chunk + panel chunk(s): [X | P hi | P lo] (split: then [X lo | P hi])
       const int kc = j / SUB, part = j - kc * SUB;
-      const bool two = SPLIT && part == 0;
+      const bool two = TWO && part == 0;
       mbar_expect(full + s, 128u * 128u + (two ? 2u : 1u) * (uint32_t)Rgp * 128u);
       tma2d(dst, part ? tmXlo : tmX, kc * KCH, ti0, full + s);
       tma2d(dst + 128 * 128, tmPan, kc * KCH, c0, full + s);
@@ -138,7 +199,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     return true;
   };
   auto fill = [&]() -> bool {
-    while (loaded < total && loaded < issued + kTcStages) {
+    while (loaded < total && loaded < issued + NS) {
       if (!load_chunk(loaded)) return false;
       ++loaded;
     }
@@ -146,8 +207,8 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   };
   // MMAs of the next chunk; its stage is released by the MMAs' commit
   auto consume = [&](auto&& mma) -> bool {
-    const uint32_t k = issued, s = k % kTcStages;
-    if (!mbar_wait(full + s, (k / kTcStages) & 1, tmo)) return false;
+    const uint32_t k = issued, s = k % NS;
+    if (!mbar_wait(full + s, (k / NS) & 1, tmo)) return false;
     tc_fence_after();
     mma(sm + s * S.stage_bytes);
     tc_commit(empty + s);
@@ -158,8 +219,8 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
 
   // Split operands: contraction 2 of each tile restarts a tile accumulator T
   // (TMEM columns Rgp (1 + b)), and the threads add it into the running sums
-  // S (columns Rgp (1 + nbt + b)) in FP32, S = S * scale + T, with the B-pass
-  // frame change as the exact power-of-two scale.  The tensor core's FP32
+  // S (columns Rgp (1 + nbt + b)) in FP32, S = S + T (tile and sums share the
+  // B-pass frame; frame changes rescale S).  The tensor core's FP32
   // accumulation then never runs over more than one tile: over long chains
   // (many tiles per CTA) it drifts by more than the FP32 path allows.
   const uint32_t tl0 = (uint32_t)((warp & 3) * 32) << 16;
@@ -176,23 +237,55 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
         } else {
           tmem_ld8(tS, vs);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) vs[j] = fmaf(vs[j], IS_A ? 1.f : colScale[cc + j], vt[j]);
+          for (int j = 0; j < 8; ++j) vs[j] += vt[j];
         }
         tmem_st8(tS, vs);
       }
   };
   bool folded = false;
 
-  uint32_t c1_phase = 0, c2_phase = 0;
-  bool c2_pending = false, d2_started = false;
+
+  uint32_t c1_phase = 0, c2_phase = 0, st_phase = 0;
+  bool c2_pending = false, d2_started = false, st_stored = false;
   int bail = 0;
-  float* St = IS_A ? cd.logA : cd.logB;
   const float aref = 1.f / (float)P;
   const uint32_t tl = (uint32_t)(quarter * 32) << 16;  // this warp's TMEM lane block
+
+  // B: move Acc (split: the running sums) into the frames Fn by the exact
+  // powers of two 2^(F - Fn), then F = Fn.  Callers make sure no contraction 2
+  // is in flight.
+  auto apply_frames = [&]() {
+    if (d2_started)
+      for (int b = 0; b < nbt; ++b)
+        for (int cc = half * 8; cc < Rgp; cc += 16) {
+          float v[8];
+          const uint32_t ta = tbase + tl0 + (uint32_t)(Rgp * (1 + (SPLIT ? nbt : 0) + b) + cc);
+          tmem_ld8(ta, v);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] *= colScale[cc + j];
+          tmem_st8(ta, v);
+        }
+    __syncthreads();
+    for (int c = tid; c < nc; c += kThreads) {
+      colF[c] = colFn[c];
+      colScale[c] = 1.f;
+      colRefW[c] = ldexpf(1.f, colRef[c] - (int)colF[c]);
+      colC[c] = (0.5f * kR16Scale - colLam[c]) * kLog2e - colF[c];
+    }
+    if (tid == 0) flags[1] = 0;
+    __syncthreads();
+  };
 
   for (int q = 0; q < ntl; ++q) {
     const int i0 = (pg + q * cd.Pg) * kTcTile;
     const int ni = min(kTcTile, N - i0);
+    // the tile's table slice (A: the state, B: the uniforms): one TMA load, once
+    // the previous tile's state store has read the buffer
+    if ((IS_A ? !init : !SPLIT) && tid == 0 && !flags[0]) {
+      if (st_stored) bulk_wait_read();
+      mbar_expect(bar_st, state_bytes);
+      tma2d(Sst, tmState, i0, c0, bar_st);
+    }
     // ---- 1. C = X_tile Panel^T (skipped for the initial passes: c = 0)
     if (do_c1) {
       if (tid == 0 && !flags[0]) {
@@ -205,7 +298,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
               const uint64_t da = desc_sw128(su32(st + ks * 32));
               const uint64_t db = desc_sw128(su32(st + 128 * 128 + ks * 32));
               tc_mma<BF>(tbase, da, db, id, (kc | ks | part) ? 1u : 0u);
-              if (SPLIT && part == 0)  // X hi * P lo
+              if (TWO && part == 0)  // X * P lo (split: X hi * P lo)
                 tc_mma<BF>(tbase, da, desc_sw128(su32(st + 128 * 128 + pnl + ks * 32)), id, 1u);
             }
           });
@@ -242,9 +335,6 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     // ---- 2. epilogue: warp (quarter, half) = pixels 32*quarter.., runs of parity `half`
     const int il = quarter * 32 + lane;
     const bool valid = il < ni;
-    const size_t Nst = (size_t)cd.Nst;
-    const size_t gpix = (size_t)c0 * Nst + i0 + il;  // state of column c of this pixel: gpix + c * Nst
-    const bool ld_state = !init && valid;
     unsigned char* wl = Wsm + (il / KCH) * wchunk;   // this pixel's 128-byte K chunk of W
     const int kb = (il % KCH) * ESZ;
     auto store_w = [&](int c, float w) {
@@ -260,31 +350,45 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
       }
     };
     if (IS_A) {
-      // eq. (update_A), K1 steps in base 2 (y = z log2 e); the state and the
-      // TMEM row of the next run of this warp are loaded one run ahead
-      float zn[P];
-      uint32_t cn[8];
-#pragma unroll
-      for (int j = 0; j < P; ++j) zn[j] = (ld_state && half < nr) ? St[gpix + (half * P + j) * Nst] : 0.f;
-      if (do_c1 && half < nr) tmem_ld8_issue(tbase + tl + (uint32_t)(half * P), cn);
+      if (!init) {  // the state tile has landed
+        const int to = mbar_wait(bar_st, st_phase, tmo) ? 0 : 1;
+        if (to) atomicOr(bt->status, 1 << 14);  // the A state tile's load
+        if (__syncthreads_or(to)) {
+          bail = 1;
+          break;
+        }
+        st_phase ^= 1;
+      }
+      // eq. (update_A), K1 steps per (pixel, run).  The run's G = E^T E is
+      // symmetric: its p (p + 1) / 2 distinct entries are read into registers
+      // once per run, so the K1 steps touch no shared memory.
       for (int r = half; r < nr; r += 2) {
-        float cv[P], zc[P];
+        float cv[P], zc[P], gsym[PP];
         if (do_c1) {
-          tmem_wait_ld8(cn);
+          uint32_t ca[8];
+          tmem_ld8_issue(tbase + tl + (uint32_t)(r * P), ca);
+          tmem_wait_ld8(ca);
 #pragma unroll
-          for (int j = 0; j < P; ++j) cv[j] = __uint_as_float(cn[j]);
+          for (int j = 0; j < P; ++j) cv[j] = __uint_as_float(ca[j]);
         } else {
 #pragma unroll
           for (int j = 0; j < P; ++j) cv[j] = 0.f;
         }
 #pragma unroll
-        for (int j = 0; j < P; ++j) zc[j] = zn[j];
-        if (r + 2 < nr) {
+        for (int j = 0; j < P; ++j) zc[j] = (!init && valid) ? Sst[(r * P + j) * kTcTile + il] : 0.f;
+        {
+          const float* G = Gs + r * P * P;
+          int e = 0;
 #pragma unroll
-          for (int j = 0; j < P; ++j) zn[j] = ld_state ? St[gpix + ((r + 2) * P + j) * Nst] : 0.f;
-          if (do_c1) tmem_ld8_issue(tbase + tl + (uint32_t)((r + 2) * P), cn);
+          for (int j = 0; j < P; ++j)
+#pragma unroll
+            for (int k = j; k < P; ++k) gsym[e++] = G[j * P + k];
         }
-        const float* G = Gs + r * P * P;
+        // G[j][k] from the packed upper triangle
+        auto gjk = [&](int j, int k) -> float {
+          const int lo = j < k ? j : k, hi = j < k ? k : j;
+          return gsym[lo * P - lo * (lo - 1) / 2 + (hi - lo)];
+        };
         float a[P], wdev[P], znew[P];  // new a, a - 1/p (shifted accumulation), new log frame
         if (SPLIT) {
           // FP32 throughout, as in the CUDA-core pass: a+ = softmax(log a - eta (G a - c)),
@@ -305,7 +409,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
             for (int j = 0; j < P; ++j) {
               float g = -cv[j];
 #pragma unroll
-              for (int k = 0; k < P; ++k) g = fmaf(G[j * P + k], at[k], g);
+              for (int k = 0; k < P; ++k) g = fmaf(gjk(j, k), at[k], g);
               zc[j] = fmaf(-eta, g, zc[j]);
               mx = fmaxf(mx, zc[j]);
             }
@@ -349,7 +453,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
             for (int j = 0; j < P; ++j) {
               float g = -cv[j];
 #pragma unroll
-              for (int k = 0; k < P; ++k) g = fmaf(G[j * P + k], at[k], g);
+              for (int k = 0; k < P; ++k) g = fmaf(gjk(j, k), at[k], g);
               y[j] = fmaf(-e2, g, y[j]);
               mx = fmaxf(mx, y[j]);
             }
@@ -371,7 +475,8 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
         }
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-          if (valid) St[gpix + (r * P + j) * Nst] = znew[j];
+          // the new state in place (the initial pass also zeroes the padding pixels)
+          if (valid || init) Sst[(r * P + j) * kTcTile + il] = valid ? znew[j] : 0.f;
           store_w(r * P + j, wdev[j]);
         }
         // A A^T of this tile's pixels: products in 2^-24 fixed point, summed
@@ -387,96 +492,106 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
           }
       }
     } else {
-      // eq. (update_B): u' = u - lse - eta2 g (initial pass: u = 0.1 * SplitMix64
-      // uniform).  The old logits and TMEM rows of kRB runs are loaded together.
-      for (int r0 = half; r0 < nr; r0 += 2 * kRB) {
-        float uo[kRB][P];
-        uint32_t gr[kRB][8];
-#pragma unroll
-        for (int b = 0; b < kRB; ++b)
-#pragma unroll
-          for (int j = 0; j < P; ++j)
-            uo[b][j] = (ld_state && r0 + 2 * b < nr) ? St[gpix + ((r0 + 2 * b) * P + j) * Nst] : 0.f;
-        if (do_c1) {
-#pragma unroll
-          for (int b = 0; b < kRB; ++b)
-            if (r0 + 2 * b < nr) tmem_ld8_issue(tbase + tl + (uint32_t)((r0 + 2 * b) * P), gr[b]);
-#pragma unroll
-          for (int b = 0; b < kRB; ++b)
-            if (r0 + 2 * b < nr) tmem_wait_ld8(gr[b]);
+      // eq. (update_B) without stored logits: u = 0.1 r - Lambda - x^T (S + eta2 R),
+      // the last term from contraction 1 (initial pass: u = 0.1 r), r from the
+      // table slice in shared memory, and the shifted weights
+      // e^u 2^-F - 2^(k-F) (the reference is added back in the merge), in one
+      // loop over the thread's runs, kRB at a time (their TMEM rows load
+      // together).  In base 2, u log2 e - F = q s log2 e + C - g log2 e with
+      // s = 0.1 / 2^16 and the column constant C = (s/2 - Lambda) log2 e - F.
+      // The frames stay at k unless a weight exceeds 2^96 (then sums of N
+      // weights could overflow): such a tile forms its exact column maxima
+      // and is redone in the raised frames.  Until then no column maximum is
+      // needed: at frame k every column's largest weight is at least 2^-1/2.
+      if (!SPLIT) {
+        const int to = mbar_wait(bar_st, st_phase, tmo) ? 0 : 1;  // the uniforms have landed
+        if (to) atomicOr(bt->status, 1 << 14);
+        if (__syncthreads_or(to)) {
+          bail = 1;
+          break;
         }
+        st_phase ^= 1;
+      }
+      constexpr int kRB = 2;
+      constexpr float kWmax = 79228162514264337593543950336.f;  // 2^96
+      constexpr float kQs = kR16Scale * kLog2e;
+      auto b_weights = [&](bool exact) -> float {
+        float wmax = 0.f;
+        for (int r0 = half; r0 < nr; r0 += 2 * kRB) {
+          uint32_t gr[kRB][8];
+          if (do_c1) {
 #pragma unroll
-        for (int b = 0; b < kRB; ++b) {
-          const int r = r0 + 2 * b;
-          if (r >= nr) break;
-          const float eta = runEta[r];
+            for (int b = 0; b < kRB; ++b)
+              if (r0 + 2 * b < nr) tmem_ld8_issue(tbase + tl + (uint32_t)((r0 + 2 * b) * P), gr[b]);
 #pragma unroll
-          for (int j = 0; j < P; ++j) {
-            const int c = r * P + j;
-            float u = -EDAA_INF;
-            if (valid) {
-              if (init) u = 0.1f * uniform24(cd.seeds[m0 + r], (uint64_t)(i0 + il) * P + j + 1);
-              else u = uo[b][j] - colLse[c] - eta * (do_c1 ? __uint_as_float(gr[b][j]) : 0.f);
-              St[gpix + c * Nst] = u;  // the new logits (read back below for the weights)
+            for (int b = 0; b < kRB; ++b)
+              if (r0 + 2 * b < nr) tmem_wait_ld8(gr[b]);
+          }
+#pragma unroll
+          for (int b = 0; b < kRB; ++b) {
+            const int r = r0 + 2 * b;
+            const bool live = r < nr;  // warp-uniform; a missing run recomputes run r0 and stores nothing
+            const bool act = valid && live;
+            const int rc = live ? r : r0;
+            float u24[P];  // split operands: the exact 24-bit draw
+            if (SPLIT) initial_logits<P>(__ldg(cd.seeds + m0 + rc), (uint64_t)(i0 + il), u24);
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              const int c = rc * P + j;
+              const float g = (do_c1 && live) ? __uint_as_float(gr[b][j]) : 0.f;
+              const float q = SPLIT ? 0.f : (float)R16[c * kTcTile + il];
+              const float u0 = SPLIT ? u24[j] : (q + 0.5f) * kR16Scale;
+              float w = 0.f, e;
+              if (SPLIT) {  // FP32, expm1 near the reference
+                const float u = act ? (u0 - colLam[c]) - g : -EDAA_INF;
+                e = ex2_approx(fmaf(u, kLog2e, -colF[c]));
+                if (act) w = shifted_weight(u, colF[c], colRef[c]);
+              } else {
+                const float x2 = act ? fmaf(-g, kLog2e, fmaf(q, kQs, colC[c])) : -EDAA_INF;  // u log2 e - F
+                e = ex2_approx(x2);  // 0 where inactive
+                if (act) w = e - colRefW[c];
+              }
+              wmax = fmaxf(wmax, e);
+              if (live) store_w(c, w);
+              if (exact && live) {
+                const float u = act ? (u0 - colLam[c]) - g : -EDAA_INF;
+                const int key = __reduce_max_sync(0xffffffffu, ord_key(u));
+                if (lane == 0) atomicMax(&colKey[c], key);
+              }
             }
-            const int key = __reduce_max_sync(0xffffffffu, ord_key(u));
-            if (lane == 0) atomicMax(&colKey[c], key);
           }
         }
-      }
-      __syncthreads();
-      // new running exponents, rescale factors for the accumulators, reference weights
-      for (int c = tid; c < nc; c += kThreads) {
-        const float Mo = colM[c];
-        const float Mn = fmaxf(Mo, tile_exp(colKey[c]));
-        colScale[c] = (Mo == Mn || Mo == -EDAA_INF) ? 1.f : ldexpf(1.f, (int)(Mo - Mn));
-        if (Mo != Mn && Mo != -EDAA_INF) flags[1] = 1;
-        colM[c] = Mn;
-        colKey[c] = ord_key(-EDAA_INF);
-        colRefW[c] = ldexpf(1.f, colRef[c] - (int)Mn);
-      }
-      __syncthreads();
-      if (!SPLIT && flags[1] && d2_started) {  // exact power-of-two rescale of Acc in TMEM, disjoint 8-column chunks
-        for (int b = 0; b < nbt; ++b)
-          for (int cc = half * 8; cc < Rgp; cc += 16) {
-            float v[8];
-            const uint32_t ta = tbase + tl + (uint32_t)(Rgp * (1 + b) + cc);
-            tmem_ld8(ta, v);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] *= colScale[cc + j];
-            tmem_st8(ta, v);
-          }
-      }
-      // shifted weights e^u 2^-Mn - 2^(k-Mn) (the reference is added back in the merge)
-      for (int r0 = half; r0 < nr; r0 += 2 * kRB) {
-        float un[kRB][P];
-#pragma unroll
-        for (int b = 0; b < kRB; ++b)
-#pragma unroll
-          for (int j = 0; j < P; ++j) un[b][j] = (valid && r0 + 2 * b < nr) ? St[gpix + ((r0 + 2 * b) * P + j) * Nst] : 0.f;
-#pragma unroll
-        for (int b = 0; b < kRB; ++b) {
-          const int r = r0 + 2 * b;
-          if (r >= nr) break;
-#pragma unroll
-          for (int j = 0; j < P; ++j) {
-            const int c = r * P + j;
-            float w = 0.f;
-            if (valid)
-              w = SPLIT ? shifted_weight(un[b][j], colM[c], colRef[c])  // FP32, expm1 near the reference
-                        : ex2_approx(fmaf(un[b][j], kLog2e, -colM[c])) - colRefW[c];
-            store_w(c, w);
-          }
+        return wmax;
+      };
+      const float wmax = b_weights(false);
+      if (__syncthreads_or(!(wmax <= kWmax))) {
+        // weights too large for the frames: exact maxima, raised frames
+        // (Acc rescaled: the previous contraction 2 has finished), redo
+        b_weights(true);
+        __syncthreads();
+        for (int c = tid; c < nc; c += kThreads) {
+          const float te = tile_exp(colKey[c]);
+          colKey[c] = ord_key(-EDAA_INF);
+          const float Fn = fmaxf(colF[c], te);
+          colFn[c] = Fn;
+          colScale[c] = ldexpf(1.f, (int)(colF[c] - Fn));
         }
+        __syncthreads();
+        apply_frames();
+        b_weights(false);
       }
     }
-    // ---- 3. Acc += X_bands W^T (W from generic-proxy stores -> async proxy)
+    // ---- 3. Acc += X_bands W^T (W and the A state from generic-proxy stores -> async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {
-      flags[1] = 0;
       tc_fence_after();
+      if (IS_A) {  // the new state tile back to global memory
+        tma2d_store(tmState, i0, c0, Sst);
+        bulk_commit();
+        st_stored = true;
+      }
       if (!flags[0]) {
         const bool first = !d2_started;
         bool ok = true;
@@ -547,6 +662,12 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     float* part = cd.part + (size_t)pg * (L + 1) * Mp;
     for (int e = tid; e < (L + 1) * nc; e += kThreads) part[(size_t)c0 * (L + 1) + e] = 0.f;
   }
+  // the state stores complete in global memory before the phase ends (they
+  // never wait on other CTAs, so this wait is not bounded)
+  if (IS_A && tid == 0 && st_stored) {
+    bulk_wait_all();
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+  }
   __syncthreads();
   if (!bail) {
     if (IS_A) {
@@ -565,7 +686,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
         dst[k * P + j] = v;
       }
     } else {
-      for (int c = tid; c < nc; c += kThreads) cd.pmax[(size_t)pg * Mp + c0 + c] = colM[c];
+      for (int c = tid; c < nc; c += kThreads) cd.pmax[(size_t)pg * Mp + c0 + c] = colF[c];
     }
   }
   tc_fence_before();
@@ -573,7 +694,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512) : "memory");
   // the barriers' shared memory is reused by the next phase: invalidate them first
   if (tid == 0) {
-    for (int b = 0; b < 2 * kTcStages + 2; ++b)
+    for (int b = 0; b < 2 * kTcStages + 3; ++b)
       asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(su32(full + b)) : "memory");
   }
   __syncthreads();
