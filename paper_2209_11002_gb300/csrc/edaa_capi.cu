@@ -245,7 +245,7 @@ static size_t pass_item_smem(const CubeHost& h) {
     const int rb = std::min(h.tile.Rm, (8 / h.tile.WP1) * rq1_max(h.p));
     s = (size_t)pass_smem(h.L, h.Ls, h.Lr, h.p, rb, 128).total * 4;  // fit pass in run blocks
     const int rgp = round_up(h.tile.Rm * h.p, 16);  // the widest group this cube can take (smaller ones need less)
-    s = std::max(s, (size_t)tc_smem_max(rgp, h.esz, h.tc == 3, h.p));
+    s = std::max(s, (size_t)tc_smem_max(rgp, h.esz, h.tc == 3, h.p, h.L, kTcSmemCap));
   }
   return s;
 }
@@ -706,6 +706,9 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
   }
   smem = std::max(smem, (size_t)32 * 1024);
   c->smem = smem;
+  // every tensor-core pass lays out its ring in this many bytes (narrower run
+  // groups, e.g. the autotuner's candidates, take more stages, never more room)
+  c->hb.smem_bytes = (unsigned)smem;
   auto bail = [&](edaa_status st) {
     edaa_destroy(c);
     return st;

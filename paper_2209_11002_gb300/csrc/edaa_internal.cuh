@@ -163,6 +163,7 @@ struct Batch {
   int K1, K2;
   int coh_mode;
   long long timeout_ns;
+  unsigned int smem_bytes;  // dynamic shared memory of every launch of the program kernel
   int* status;
   unsigned int* bar;  // [0] arrivals, [1] generation
   // phase trace (null when off): [mode][phase] first-start / last-end global-timer ns

@@ -143,8 +143,19 @@ __device__ __forceinline__ void mbar_inval(uint64_t* b) {
 __device__ __forceinline__ void mbar_expect(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
 }
-// bounded wait for phase `par` of the barrier; false on time-out
+// bounded wait for phase `par` of the barrier; false on time-out.  The clock
+// is read only once the barrier is found incomplete (completed barriers are
+// the common case on the critical path).
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t par, long long timeout_ns) {
+  {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(par)
+        : "memory");
+    if (ok) return true;
+  }
   const unsigned long long t0 = global_ns();
   while (true) {
     uint32_t ok;
@@ -156,6 +167,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t par, long long t
     if (ok) return true;
     if ((long long)(global_ns() - t0) > timeout_ns) return false;
   }
+}
+// non-blocking probe of phase `par` of the barrier: true if it has completed
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t par) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(par)
+      : "memory");
+  return ok != 0;
 }
 // One bulk (TMA) copy of `bytes` contiguous bytes global -> shared, completing
 // on barrier b; both addresses 16-byte aligned, bytes a multiple of 16.

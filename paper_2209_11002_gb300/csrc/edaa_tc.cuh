@@ -35,11 +35,6 @@
 
 namespace edaa {
 
-// Ring stages of a tensor-core pass.  Three keep contraction 2's X streaming
-// in during the epilogue; deeper rings (tried up to the shared-memory limit)
-// measured slower, the larger carve-out leaving less L1 for the epilogue's
-// state lines.
-constexpr int kTcStages = 3;
 constexpr int kTcTile = 128;
 
 // su32, mbar_init, mbar_expect and the bounded mbar_wait live in edaa_pass.cuh
@@ -49,6 +44,10 @@ __device__ __forceinline__ void tma2d(void* dst, const CUtensorMap* m, int c0, i
           su32(dst)),
       "l"(m), "r"(c0), "r"(c1), "r"(su32(b))
       : "memory");
+}
+// brings a tensor map (in global memory) into the TMA unit's descriptor cache
+__device__ __forceinline__ void tmap_prefetch(const CUtensorMap* m) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(m) : "memory");
 }
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 B apart
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
@@ -139,50 +138,67 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-// 226 KB: one CTA's 227 KB of shared memory less 1 KB for the program
-// kernel's static shared memory
-constexpr uint32_t kTcSmemCap = 232448u - 1024u;
 
 struct TcSmem {
-  uint32_t stages, stage_bytes, w_off, state_off, misc_off, total;
+  uint32_t stages, panel_off, w_off, state_off, misc_off, total;
 };
-// Shared memory of a tensor-core pass, per pass kind.  A ring stage holds one
-// 128 x 128-byte chunk of X and the panel chunks (Rgp x 128 B each): the
-// A-pass's panel E (split operands: its high and low part), the B-pass's
-// panel S + eta2 R as a high and a low part.  W holds the weights of one
-// 128-pixel tile in 128-byte pixel chunks (split: high and low part).  The
-// tile's slice of a per-pixel table follows (Rgp rows of 128 pixels): the
-// A-pass's log-abundance state, the B-pass's B^0 uniforms.  The misc region
-// holds the barriers and flags (256 B), eight 256-entry column arrays, the
-// step sizes (128), G (2048) and the A A^T sums (4 x Rm x PP with
-// Rm <= Rgp / p); 1 KB alignment slack.
+// Shared memory of a tensor-core pass, per pass kind.  The run group's panel
+// is resident for the whole pass (nkc K chunks of Rgp rows x 128 B): the
+// A-pass's E (split operands: its high and low part), the B-pass's
+// S + eta2 R as a high and a low part.  The ring stages hold one
+// 128 x 128-byte chunk of X each (contraction 1: pixel-major, contraction 2:
+// band-major).  W holds the weights of one 128-pixel tile in 128-byte pixel
+// chunks (split: high and low part).  The tile's slice of a per-pixel table
+// follows (Rgp rows of 128 pixels): the A-pass's log-abundance state, the
+// B-pass's B^0 uniforms.  The misc region holds the barriers and flags
+// (256 B), eight 256-entry column arrays, the step sizes (128), G (2048) and
+// the A A^T sums (4 x Rm x PP with Rm <= Rgp / p); 1 KB alignment slack.
+constexpr uint32_t kTcStageBytes = 128u * 128u;
+constexpr int kTcMaxStages = 8;
 __host__ __device__ inline uint32_t tc_misc_bytes(int Rgp, int p) {
   const uint32_t rm = (uint32_t)(Rgp / p), pp = (uint32_t)(p * (p + 1) / 2);
   return (256u + 8u * 256u * 4u + 128u * 4u + 2048u * 4u + 4u * rm * pp * 4u + 1023u) & ~1023u;
 }
-__host__ __device__ inline TcSmem tc_smem_n(int Rgp, int esz, bool split, int p, bool is_a, uint32_t stages) {
+__host__ __device__ inline int tc_nkc(int L, int esz) { return (L + 128 / esz - 1) / (128 / esz); }
+// `stages` ring stages; 0 = as many as fit in `cap` bytes (at most
+// kTcMaxStages, at least 2: a layout that does not fit says so by its total)
+__host__ __device__ inline TcSmem tc_smem_n(int Rgp, int esz, bool split, int p, bool is_a, int L, uint32_t stages,
+                                           uint32_t cap) {
   TcSmem s;
   const uint32_t pnl = ((uint32_t)Rgp * 128u + 1023u) & ~1023u;
   const uint32_t pparts = (split || !is_a) ? 2u : 1u;
   const uint32_t wparts = split ? 2u : 1u;
   const uint32_t npc = (uint32_t)esz;  // 128-byte pixel chunks per 128-pixel tile (128 / (128 / esz))
+  s.panel_off = 1024u;
+  const uint32_t ring_off = s.panel_off + pparts * (uint32_t)tc_nkc(L, esz) * pnl;
+  const uint32_t fixed = wparts * npc * pnl + (((uint32_t)Rgp * (is_a ? 512u : 256u) + 1023u) & ~1023u) +
+                         tc_misc_bytes(Rgp, p);
+  if (stages == 0) {
+    const uint32_t room = cap > ring_off + fixed ? cap - ring_off - fixed : 0u;
+    stages = room / kTcStageBytes;
+    if (stages > (uint32_t)kTcMaxStages) stages = kTcMaxStages;
+    if (stages < 2u) stages = 2u;  // does not fit: the total says so
+  }
   s.stages = stages;
-  s.stage_bytes = 128u * 128u + pparts * pnl;
-  s.w_off = 1024u + stages * s.stage_bytes;
+  s.w_off = ring_off + stages * kTcStageBytes;
   s.state_off = s.w_off + wparts * npc * pnl;
   // the per-tile slice of a per-pixel table: A the state (float), B the B^0 uniforms (uint16)
   s.misc_off = s.state_off + (((uint32_t)Rgp * (is_a ? 512u : 256u) + 1023u) & ~1023u);
   s.total = s.misc_off + tc_misc_bytes(Rgp, p);
   return s;
 }
-// three ring stages where they fit in one CTA's shared memory, else two
-__host__ __device__ inline TcSmem tc_smem(int Rgp, int esz, bool split, int p, bool is_a) {
-  TcSmem s = tc_smem_n(Rgp, esz, split, p, is_a, (uint32_t)kTcStages);
-  if (s.total > kTcSmemCap) s = tc_smem_n(Rgp, esz, split, p, is_a, 2u);
-  return s;
+// 226 KB: one CTA's 227 KB of shared memory less 1 KB for the program
+// kernel's static shared memory
+constexpr uint32_t kTcSmemCap = 232448u - 1024u;
+
+// The layout a pass uses: as many stages as fit in the dynamic shared memory
+// the kernel was launched with (`cap`, the same for every pass of a batch).
+__host__ __device__ inline TcSmem tc_smem(int Rgp, int esz, bool split, int p, bool is_a, int L, uint32_t cap) {
+  return tc_smem_n(Rgp, esz, split, p, is_a, L, 0u, cap);
 }
-__host__ __device__ inline uint32_t tc_smem_max(int Rgp, int esz, bool split, int p) {
-  const uint32_t a = tc_smem(Rgp, esz, split, p, true).total, b = tc_smem(Rgp, esz, split, p, false).total;
+__host__ __device__ inline uint32_t tc_smem_max(int Rgp, int esz, bool split, int p, int L, uint32_t cap) {
+  const uint32_t a = tc_smem(Rgp, esz, split, p, true, L, cap).total;
+  const uint32_t b = tc_smem(Rgp, esz, split, p, false, L, cap).total;
   return a > b ? a : b;
 }
 
@@ -190,11 +206,19 @@ __host__ __device__ inline uint32_t tc_smem_max(int Rgp, int esz, bool split, in
 // columns) and one Acc per 128-band tile (split operands: a per-tile Acc and
 // a running sum per band tile), with 8 spare columns so that the 8-wide TMEM
 // reads of the last run stay inside the 512 allocated; the shared memory of
-// both pass kinds stays within kTcSmemCap.
+// both pass kinds, with at least three ring stages where that is possible,
+// stays within kTcSmemCap.
 __host__ __device__ inline int tc_rgp_max(int L, int esz, bool split, int p) {
   const int nbt = (L + 1 + 127) / 128;
   int r = ((512 - 8) / (1 + (split ? 2 : 1) * nbt)) & ~15;
-  while (r > 16 && tc_smem_max(r, esz, split, p) > kTcSmemCap) r -= 16;
+  auto fits = [&](int rg, uint32_t st) {
+    return tc_smem_n(rg, esz, split, p, true, L, st, kTcSmemCap).total <= kTcSmemCap &&
+           tc_smem_n(rg, esz, split, p, false, L, st, kTcSmemCap).total <= kTcSmemCap;
+  };
+  int r3 = r;
+  while (r3 > 16 && !fits(r3, 3u)) r3 -= 16;
+  if (fits(r3, 3u)) return r3;
+  while (r > 16 && !fits(r, 2u)) r -= 16;
   return r;
 }
 

@@ -75,21 +75,24 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   const CUtensorMap* tmXTlo = cd.tmaps + TM_XTLO;
   const CUtensorMap* tmPanLo = cd.tmaps + (IS_A ? TM_ELO : TM_SLO);
   const CUtensorMap* tmState = cd.tmaps + (IS_A ? TM_STATE : TM_R16);
-  const TcSmem S = tc_smem(Rgp, ESZ, SPLIT, P, IS_A);
+  const TcSmem S = tc_smem(Rgp, ESZ, SPLIT, P, IS_A, L, bt->smem_bytes);
   const uint32_t NS = S.stages;
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* Wsm = sm + (S.w_off - 1024u);
   float* Sst = reinterpret_cast<float*>(sm + (S.state_off - 1024u));  // A: state [column][128 pixels]
   const uint16_t* R16 = reinterpret_cast<const uint16_t*>(Sst);       // B: uniforms [column][128 pixels]
   const uint32_t wchunk = ((uint32_t)Rgp * 128u + 1023u) & ~1023u;
-  const uint32_t pnl = wchunk;  // a panel chunk (Rgp rows of 128 B), 1024-byte aligned in its stage
+  const uint32_t pnl = wchunk;  // a panel chunk (Rgp rows of 128 B), 1024-byte aligned
+  unsigned char* Psm = sm + (S.panel_off - 1024u);  // resident panel: [part][K chunk] chunks of pnl bytes
+  unsigned char* ring = Psm + (TWO ? 2u : 1u) * (uint32_t)nkc * pnl;
   unsigned char* misc = sm + (S.misc_off - 1024u);
-  uint64_t* full = reinterpret_cast<uint64_t*>(misc);      // kTcStages
-  uint64_t* empty = full + kTcStages;                      // kTcStages
-  uint64_t* bar_c1 = empty + kTcStages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(misc);      // kTcMaxStages
+  uint64_t* empty = full + kTcMaxStages;                   // kTcMaxStages
+  uint64_t* bar_c1 = empty + kTcMaxStages;
   uint64_t* bar_c2 = bar_c1 + 1;
-  uint64_t* bar_st = bar_c2 + 1;                           // A: the state tile's TMA load
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_st + 1);
+  uint64_t* bar_st = bar_c2 + 1;                           // the tile's table slice (A state, B uniforms)
+  uint64_t* bar_pn = bar_st + 1;                           // the resident panel
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_pn + 1);
   int* flags = reinterpret_cast<int*>(tmem_slot + 4);      // [0] bail, [1] rescale needed
   // B: every column keeps its weights as e^u 2^-F in a power-of-two frame F
   // (exact rescales); F starts at the reference exponent k and follows the
@@ -112,13 +115,14 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
                  : "memory");
   }
   if (tid == 0) {
-    for (int s = 0; s < kTcStages; ++s) {
+    for (int s = 0; s < kTcMaxStages; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
     mbar_init(bar_c1, 1);
     mbar_init(bar_c2, 1);
     mbar_init(bar_st, 1);
+    mbar_init(bar_pn, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     flags[0] = 0;
     flags[1] = 0;
@@ -167,55 +171,102 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   // one TMA box of the tile's table slice: 128 pixels x the group's rows (A: float, B: uint16)
   const uint32_t state_bytes = 128u * (IS_A ? 4u : 2u) * (uint32_t)(Rm * P);
 
-  // ---- the chunk stream (thread 0).  Per tile: contraction 1 (nkc chunks of X
-  // and the panel; not in the initial passes), then contraction 2 (nbt * NPC
-  // chunks of the band-major X).  Chunk k uses ring stage k % NS.  Loads run
-  // up to NS chunks ahead of the MMAs, so contraction 2's X streams in during
-  // the epilogue and the next tile's contraction 1 during contraction 2.
+  // ---- the chunk stream (thread 0).  The panel is loaded once, before the
+  // first tile.  Per tile: contraction 1 (nkc chunks of the pixel-major X; not
+  // in the initial passes), then contraction 2 (nbt * NPC chunks of the
+  // band-major X).  Chunk k uses ring stage k % NS.  Loads run up to NS
+  // chunks ahead of the MMAs, so contraction 2's X streams in during the
+  // epilogue and the next tile's contraction 1 after it.
   const int nc1 = do_c1 ? nkc * SUB : 0;
   const int nc2 = nbt * NPC * SUB;
   const int per_tile = nc1 + nc2;
   const int ntl = pg < cd.ntiles ? (cd.ntiles - pg + cd.Pg - 1) / cd.Pg : 0;
   const uint32_t total = (uint32_t)(ntl * per_tile);
+  // Ring bookkeeping of thread 0, all incremental (no divisions: this code
+  // runs on one lane on the critical path of every tile).  Chunk k uses
+  // stage k % NS in round k / NS; a load waits for the previous round's
+  // release of its stage (empty barrier), an issue for its own round's
+  // arrival (full barrier).
+  constexpr int SUBS = SPLIT ? 1 : 0, NPCS = ESZ == 2 ? 1 : 2;  // log2 SUB, log2 NPC
   uint32_t loaded = 0, issued = 0;
-  auto load_chunk = [&](uint32_t k) -> bool {
-    const uint32_t s = k % NS;
-    if (k >= NS && !mbar_wait(empty + s, ((k / NS) + 1) & 1, tmo)) return false;
-    const int q = (int)(k / (uint32_t)per_tile), j = (int)(k - (uint32_t)(q * per_tile));
-    const int ti0 = (pg + q * cd.Pg) * kTcTile;
-    unsigned char* dst = sm + s * S.stage_bytes;
-    if (j < nc1) {  // X chunk + panel chunk(s): [X | P hi | P lo] (split: then [X lo | P hi])
-      const int kc = j / SUB, part = j - kc * SUB;
-      const bool two = TWO && part == 0;
-      mbar_expect(full + s, 128u * 128u + (two ? 2u : 1u) * (uint32_t)Rgp * 128u);
-      tma2d(dst, part ? tmXlo : tmX, kc * KCH, ti0, full + s);
-      tma2d(dst + 128 * 128, tmPan, kc * KCH, c0, full + s);
-      if (two) tma2d(dst + 128 * 128 + pnl, tmPanLo, kc * KCH, c0, full + s);
+  uint32_t ld_s = 0, ld_round = 0, is_s = 0, is_round = 0;
+  int ld_j = 0, ld_ti0 = pg * kTcTile;  // chunk within its tile, first pixel of that tile
+  const int ti_step = cd.Pg * kTcTile;
+  // Load the next chunk once the MMAs that read its stage's previous chunk
+  // are done: `block` waits for them (bounded), otherwise a busy stage
+  // returns 0 and nothing is issued.  Returns 1 loaded, 0 busy, -1 timed out.
+  auto load_chunk = [&](bool block) -> int {
+    if (ld_round > 0) {
+      const uint32_t par = (ld_round & 1u) ^ 1u;
+      if (block ? !mbar_wait(empty + ld_s, par, tmo) : !mbar_test(empty + ld_s, par)) return block ? -1 : 0;
+    }
+    unsigned char* dst = ring + ld_s * kTcStageBytes;
+    uint64_t* fb = full + ld_s;
+    mbar_expect(fb, kTcStageBytes);
+    if (ld_j < nc1) {  // X chunk (split: high part, then low part)
+      const int kc = ld_j >> SUBS, part = ld_j & SUBS;
+      tma2d(dst, part ? tmXlo : tmX, kc * KCH, ld_ti0, fb);
     } else {  // band-major X chunk (split: high part, then low part)
-      const int jj = j - nc1, kc = jj / SUB, part = jj - kc * SUB, bti = kc / NPC, pc = kc - bti * NPC;
-      mbar_expect(full + s, 128u * 128u);
-      tma2d(dst, part ? tmXTlo : tmXT, ti0 + pc * KCH, bti * 128, full + s);
+      const int jj = ld_j - nc1, kc = jj >> SUBS, part = jj & SUBS, bti = kc >> NPCS, pc = kc & (NPC - 1);
+      tma2d(dst, part ? tmXTlo : tmXT, ld_ti0 + pc * KCH, bti * 128, fb);
     }
-    return true;
-  };
-  auto fill = [&]() -> bool {
-    while (loaded < total && loaded < issued + NS) {
-      if (!load_chunk(loaded)) return false;
-      ++loaded;
+    if (++ld_s == NS) {
+      ld_s = 0;
+      ++ld_round;
     }
-    return true;
+    if (++ld_j == per_tile) {
+      ld_j = 0;
+      ld_ti0 += ti_step;
+    }
+    ++loaded;
+    return 1;
   };
-  // MMAs of the next chunk; its stage is released by the MMAs' commit
+  // Top the ring up without waiting: stops at the first stage still read by
+  // MMAs in flight (the just-issued ones, typically), so issuing is never
+  // held up by the tensor core's progress.
+  auto fill = [&]() {
+    while (loaded < total && loaded < issued + NS && load_chunk(false) == 1) {
+    }
+  };
+  // MMAs of the next chunk (loading it first if the ring has not yet); its
+  // stage is released by the MMAs' commit
   auto consume = [&](auto&& mma) -> bool {
-    const uint32_t k = issued, s = k % NS;
-    if (!mbar_wait(full + s, (k / NS) & 1, tmo)) return false;
+    while (loaded <= issued)
+      if (load_chunk(true) != 1) return false;
+    if (!mbar_wait(full + is_s, is_round & 1u, tmo)) return false;
     tc_fence_after();
-    mma(sm + s * S.stage_bytes);
-    tc_commit(empty + s);
+    mma(ring + is_s * kTcStageBytes);
+    tc_commit(empty + is_s);
+    if (++is_s == NS) {
+      is_s = 0;
+      ++is_round;
+    }
     ++issued;
-    return fill();
+    fill();
+    return true;
   };
-  if (tid == 0 && !fill()) flags[0] = 1;
+  if (tid == 0) {  // the maps this pass uses, into the descriptor cache before the first copy
+    tmap_prefetch(tmX);
+    tmap_prefetch(tmXT);
+    tmap_prefetch(tmState);
+    if (do_c1) {
+      tmap_prefetch(tmPan);
+      if (TWO) tmap_prefetch(tmPanLo);
+    }
+    if (SPLIT) {
+      tmap_prefetch(tmXlo);
+      tmap_prefetch(tmXTlo);
+    }
+  }
+  if (tid == 0 && do_c1 && total > 0) {  // the resident panel (high part, then low part)
+    mbar_expect(bar_pn, (TWO ? 2u : 1u) * (uint32_t)nkc * (uint32_t)Rgp * 128u);
+    for (int kc = 0; kc < nkc; ++kc) {
+      tma2d(Psm + kc * pnl, tmPan, kc * KCH, c0, bar_pn);
+      if (TWO) tma2d(Psm + (nkc + kc) * pnl, tmPanLo, kc * KCH, c0, bar_pn);
+    }
+  }
+  if (tid == 0) fill();
+  bool panel_ready = !do_c1;
 
   // Split operands: contraction 2 of each tile restarts a tile accumulator T
   // (TMEM columns Rgp (1 + b)), and the threads add it into the running sums
@@ -290,16 +341,25 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     if (do_c1) {
       if (tid == 0 && !flags[0]) {
         bool ok = true;
+        if (!panel_ready) {
+          ok = mbar_wait(bar_pn, 0, tmo);
+          panel_ready = true;
+          tc_fence_after();
+        }
         for (int j = 0; j < nc1 && ok; ++j) {
-          const int kc = j / SUB, part = j - kc * SUB;
+          const int kc = j >> SUBS, part = j & SUBS;
           ok = consume([&](unsigned char* st) {
+            // descriptors of the chunk's first K step; each further 32-byte K
+            // step adds 2 to the start-address field (address / 16)
+            const uint64_t da0 = desc_sw128(su32(st));
+            const uint64_t dh0 = desc_sw128(su32(Psm + kc * pnl));  // the resident panel's K chunk kc
+            const uint64_t dl0 = desc_sw128(su32(Psm + (nkc + kc) * pnl));
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
-              const uint64_t da = desc_sw128(su32(st + ks * 32));
-              const uint64_t db = desc_sw128(su32(st + 128 * 128 + ks * 32));
-              tc_mma<BF>(tbase, da, db, id, (kc | ks | part) ? 1u : 0u);
+              const uint64_t da = da0 + 2u * ks;
+              tc_mma<BF>(tbase, da, dh0 + 2u * ks, id, (kc | ks | part) ? 1u : 0u);
               if (TWO && part == 0)  // X * P lo (split: X hi * P lo)
-                tc_mma<BF>(tbase, da, desc_sw128(su32(st + 128 * 128 + pnl + ks * 32)), id, 1u);
+                tc_mma<BF>(tbase, da, dl0 + 2u * ks, id, 1u);
             }
           });
         }
@@ -315,6 +375,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
       }
       c1_phase ^= 1;
       tc_fence_after();
+      if (tid == 0) fill();  // contraction 1's stages are free: stream the next chunks during the epilogue
     }
     // the previous tile's contraction 2 must finish before W is rewritten or Acc rescaled
     if (c2_pending) {
@@ -327,6 +388,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
       c2_phase ^= 1;
       c2_pending = false;
       tc_fence_after();
+      if (tid == 0) fill();  // the previous contraction 2's stages are free as well
       if (SPLIT) {
         fold_tile(!folded);
         folded = true;
@@ -596,16 +658,19 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
         const bool first = !d2_started;
         bool ok = true;
         for (int j = 0; j < nc2 && ok; ++j) {
-          const int kc = j / SUB, part = j - kc * SUB, bti = kc / NPC, pc = kc - bti * NPC;
+          const int kc = j >> SUBS, part = j & SUBS, bti = kc >> NPCS, pc = kc & (NPC - 1);
           ok = consume([&](unsigned char* st) {
             const uint32_t dcol = tbase + (uint32_t)(Rgp * (1 + bti));
+            const uint64_t da0 = desc_sw128(su32(st));
+            const uint64_t db0 = desc_sw128(su32(Wsm + pc * wchunk));
+            const uint64_t dl0 = desc_sw128(su32(Wsm + (NPC + pc) * wchunk));
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
-              const uint64_t da = desc_sw128(su32(st + ks * 32));
-              const uint64_t db = desc_sw128(su32(Wsm + pc * wchunk + ks * 32));
-              tc_mma<BF>(dcol, da, db, id, ((SPLIT || first) && pc == 0 && part == 0 && ks == 0) ? 0u : 1u);
+              const uint64_t da = da0 + 2u * ks;
+              tc_mma<BF>(dcol, da, db0 + 2u * ks, id,
+                         ((SPLIT || first) && pc == 0 && part == 0 && ks == 0) ? 0u : 1u);
               if (SPLIT && part == 0)  // X hi * W lo
-                tc_mma<BF>(dcol, da, desc_sw128(su32(Wsm + (NPC + pc) * wchunk + ks * 32)), id, 1u);
+                tc_mma<BF>(dcol, da, dl0 + 2u * ks, id, 1u);
             }
           });
         }
@@ -694,7 +759,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512) : "memory");
   // the barriers' shared memory is reused by the next phase: invalidate them first
   if (tid == 0) {
-    for (int b = 0; b < 2 * kTcStages + 3; ++b)
+    for (int b = 0; b < 2 * kTcMaxStages + 4; ++b)
       asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(su32(full + b)) : "memory");
   }
   __syncthreads();
