@@ -90,6 +90,10 @@ typedef struct {
                          On tensor-core cubes tile[0] alone applies (1..M, the
                          other entries unchecked): the runs per CTA group, capped
                          by what tensor memory holds.                             */
+  int record_loss;    /* 1: every outer iteration ends with the fit pass (one more
+                         stream of X per outer iteration) and logs each run's
+                         loss ||X - X B A||_F^2 (read with edaa_loss_history);
+                         0 (default): no log.                                       */
 } edaa_config;
 
 typedef struct {
@@ -157,6 +161,29 @@ edaa_status edaa_grad(edaa_ctx* ctx, int cube, int run, float* gA, float* gB);
  * every run of cube `cube` at the current state (host array, length M). */
 edaa_status edaa_loss(edaa_ctx* ctx, int cube, double* loss);
 
+/* The loss log (needs config.record_loss = 1): row t (0-based) holds every
+ * run's loss ||X - X B A||_F^2 (FP64 accumulation) after outer iteration
+ * t + 1 of Algorithm 1 since the last init/reset, for t < T.  Writes up to
+ * `cap` rows of M doubles to the host array `hist` (NULL skips) and the
+ * number of rows recorded to *n.  Synchronises; EDAA_ERR_STATE when the log
+ * is off. */
+edaa_status edaa_loss_history(edaa_ctx* ctx, int cube, int cap, double* hist, int* n);
+
+/* Checkpoint and resume (the paper has none).  edaa_checkpoint synchronises
+ * and copies the iteration state of every run of every cube -- A and B (for
+ * tensor-core cubes: the running sums S, R and Lambda that regenerate B),
+ * E, the merges' sums, the step sizes, fits, coherences and the loss log --
+ * and the count of outer iterations done into the host buffer `buf`
+ * (capacity `cap` bytes); *bytes receives the size needed (buf = NULL only
+ * queries it).  edaa_restore loads such a buffer into a context created with
+ * cubes of the same shapes, runs and precision and the same loss-log
+ * setting, holding the same data X (checked through its FP64 band sums);
+ * anything else returns EDAA_ERR_ARG before any state changes.  Later
+ * edaa_step / edaa_solve calls continue from the restored iteration and give
+ * the results the checkpointed context would have given. */
+edaa_status edaa_checkpoint(edaa_ctx* ctx, void* buf, size_t cap, size_t* bytes);
+edaa_status edaa_restore(edaa_ctx* ctx, const void* buf, size_t bytes);
+
 /* Step sizes in use for cube `cube` (host arrays of length M; NULL skips). */
 edaa_status edaa_step_sizes(edaa_ctx* ctx, int cube, double* eta1, double* eta2);
 
@@ -200,6 +227,13 @@ void edaa_destroy(edaa_ctx* ctx);
 
 /* Thread-local text of the last error on this thread ("" if none). */
 const char* edaa_last_error(void);
+
+/* Failure injection for tests of the out-of-memory path (the paper has no
+ * counterpart): with k >= 0 the k-th device allocation the library makes from
+ * now on (0: the next one) fails with EDAA_ERR_OOM, without asking the
+ * driver; k < 0 switches it off.  Process-wide.  edaa_init then releases
+ * whatever it had allocated and returns EDAA_ERR_OOM. */
+void edaa_debug_fail_alloc(int k);
 
 /* Failure-detection self-test: launches the persistent kernel's grid barrier
  * on `grid` CTAs while waiting for grid + extra arrivals, with the given

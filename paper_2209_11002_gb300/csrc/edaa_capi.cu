@@ -10,7 +10,10 @@
 #include <tuple>
 #include <vector>
 
+#include <atomic>
+
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/edaa.h"
 #include "edaa_internal.cuh"
@@ -31,6 +34,42 @@ edaa_status cuda_fail(cudaError_t e, const char* what) {
   return fail(e == cudaErrorMemoryAllocation ? EDAA_ERR_OOM : EDAA_ERR_CUDA,
               std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+// Failure injection for tests of the out-of-memory path: when the counter is
+// k >= 0, the k-th device allocation from then on fails with
+// cudaErrorMemoryAllocation without calling the runtime (-1: off).
+std::atomic<int> g_fail_alloc{-1};
+
+bool alloc_fails() {
+  int k = g_fail_alloc.load();
+  while (k >= 0) {
+    if (g_fail_alloc.compare_exchange_weak(k, k - 1)) return k == 0;
+  }
+  return false;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (alloc_fails()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+  if (alloc_fails()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(p, bytes, s);
+}
+
+// NVTX range for the duration of a scope (the library's entry points), so
+// that a profiler timeline shows which call enqueued which launches
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 #define CK(call, what)                          \
   do {                                          \
@@ -125,6 +164,7 @@ void set_last_error(const char* msg) { g_err = msg; }
 
 struct CubeHost {
   int L, N, p, M, Ls, Lr, Mp;
+  int hist_cap = 0;  // rows of the loss log (T with record_loss, else 0)
   TileCfg tile;
   bool tile_fixed = false;  // set by the caller (edaa_config.tile): not autotuned
   int RG, Pg, Nt, ntiles, lchunk, nlchunk;
@@ -275,6 +315,7 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
   size_t opart = take((size_t)Pg_cap * (L + 1) * Mp * 4), opmax = take((size_t)Pg_cap * Mp * 4);
   size_t opaa = take((size_t)Pg_cap * M * p * p * 4), opfit = take((size_t)Pg_cap * M * 3 * 8);
   size_t ofit = take(M * 8), ofitmax = take(M * 8), oloss = take(M * 8), omu = take(M * 8);
+  size_t ohist = take((size_t)h.hist_cap * M * 8);
   size_t oseeds = take(M * 8), ogam = take(M * 8);
   size_t orho = take(L * Mp * 8), obref = take(Mp * 4);  // nlchunk <= L band chunks
   size_t ogpart = take(L * M * p * p * 8);
@@ -310,6 +351,7 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
     d.fitmax = (double*)(b + ofitmax);
     d.loss2 = (double*)(b + oloss);
     d.mu = (double*)(b + omu);
+    d.loss_hist = (double*)(b + ohist);
     d.seeds = (const uint64_t*)(b + oseeds);
     d.gammas = (const double*)(b + ogam);
     d.rho = (double*)(b + orho);
@@ -411,6 +453,48 @@ static edaa_status make_tmaps(edaa_ctx* c, CubeHost& h) {
   return EDAA_OK;
 }
 
+// The device regions that hold a cube's iteration state (everything a later
+// outer iteration reads), for checkpoints: pointers into the arena and sizes.
+struct StateRegion {
+  void* ptr;
+  size_t bytes;
+};
+static std::vector<StateRegion> state_regions(const CubeHost& h) {
+  const CubeDev& d = h.dev;
+  const size_t L = h.L, Mp = h.Mp, M = h.M, p = h.p, Nst = round_up(h.N, 32);
+  std::vector<StateRegion> r = {{d.logA, Nst * Mp * 4}, {d.Ef, L * Mp * 4}, {d.Ed, L * Mp * 8},
+                                {d.Rf, L * Mp * 4},     {d.XAt, L * Mp * 8}, {d.AAt, M * p * p * 8},
+                                {d.lse, Mp * 4},        {d.eta1, M * 4},    {d.eta2, M * 4},
+                                {d.eta1d, M * 8},       {d.eta2d, M * 8},   {d.sig2, M * 8},
+                                {d.rho, L * Mp * 8},    {d.bref, Mp * 4},   {d.gpart, L * M * p * p * 8},
+                                {d.fit, M * 8},         {d.fitmax, M * 8},  {d.loss2, M * 8},
+                                {d.mu, M * 8}};
+  if (h.hist_cap > 0) r.push_back({d.loss_hist, (size_t)h.hist_cap * M * 8});
+  if (h.tc) {
+    const size_t parts = h.tc == 3 ? 2 : 1;
+    r.push_back({d.panelE, parts * Mp * h.kp * h.esz});
+    r.push_back({d.panelS, 2 * Mp * h.kp * h.esz});
+    r.push_back({d.Sd, L * Mp * 8});
+    r.push_back({d.Rd, L * Mp * 8});
+    r.push_back({d.lamd, Mp * 8});
+  } else {
+    r.push_back({d.logB, Nst * Mp * 4});
+  }
+  return r;
+}
+
+// checkpoint layout: header, then per cube its layout key and the FP64 band
+// sums of its X (sx, L + 1 values: a fingerprint of the data), then the
+// regions in state_regions order
+struct CkptHeader {
+  char magic[8];
+  int version, n_cubes, outer_done, record_loss, hist_cap, pad;
+  uint64_t payload;
+};
+struct CkptCube {
+  int L, N, p, M, tc, esz, kp, pad;
+};
+
 static edaa_status push_batch(edaa_ctx* c) {
   for (size_t i = 0; i < c->cubes.size(); ++i) c->hb.c[i] = c->cubes[i].dev;
   CK(cudaMemcpyAsync(c->d_batch, &c->hb, sizeof(Batch), cudaMemcpyHostToDevice, c->stream), "upload batch");
@@ -420,7 +504,7 @@ static edaa_status push_batch(edaa_ctx* c) {
 // Enqueue one program (a sequence of phases) either as one persistent
 // launch or as one launch per phase.
 static edaa_status enqueue(edaa_ctx* c, int mode, int n_outer, int* launches) {
-  const int nph = program_phase_count(mode, n_outer, c->cfg.K2);
+  const int nph = program_phase_count(mode, n_outer, c->cfg.K2, c->hb.record_loss);
   if (nph <= 0) return EDAA_OK;
   if (c->d_trace) {
     const size_t n = (size_t)std::min(nph, kTraceCap);
@@ -429,11 +513,13 @@ static edaa_status enqueue(edaa_ctx* c, int mode, int n_outer, int* launches) {
     c->trace_n[mode] = (int)n;
   }
   if (c->cfg.persistent && nph > 1) {
-    CK(launch_program(c->d_batch, mode, n_outer, 0, nph, c->grid, c->smem, true, c->stream), "persistent launch");
+    CK(launch_program(c->d_batch, mode, c->outer_done, 0, nph, c->grid, c->smem, true, c->stream),
+       "persistent launch");
     if (launches) *launches += 1;
   } else {
     for (int s = 0; s < nph; ++s) {
-      CK(launch_program(c->d_batch, mode, n_outer, s, s + 1, c->grid, c->smem, false, c->stream), "phase launch");
+      CK(launch_program(c->d_batch, mode, c->outer_done, s, s + 1, c->grid, c->smem, false, c->stream),
+         "phase launch");
       if (launches) *launches += 1;
     }
   }
@@ -596,6 +682,7 @@ void edaa_config_default(edaa_config* cfg) {
   cfg->center = 1;
   cfg->trace = 0;
   for (int i = 0; i < 4; ++i) cfg->tile[i] = 0;
+  cfg->record_loss = 0;
 }
 
 const char* edaa_last_error(void) { return g_err.c_str(); }
@@ -616,6 +703,7 @@ int edaa_select_rule(const double* fit, const double* mu, int M, double fit_rati
 }
 
 edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const edaa_config* cfg, void* stream) {
+  NvtxRange nvtx_range("edaa_init");
   g_err.clear();
   if (!out) return fail(EDAA_ERR_ARG, "out is NULL");
   *out = nullptr;
@@ -672,6 +760,8 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
   c->hb.K2 = conf.K2;
   c->hb.coh_mode = conf.coherence;
   c->hb.timeout_ns = (long long)(conf.barrier_timeout_ms * 1e6);
+  c->hb.record_loss = conf.record_loss ? 1 : 0;
+  c->hb.hist_cap = conf.record_loss ? std::max(conf.T, 1) : 0;
   for (int i = 0; i < n_cubes; ++i) {
     CubeHost h{};
     const edaa_cube& q = cubes[i];
@@ -679,6 +769,7 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
     h.Ls = padded_ld(q.L);
     h.Lr = round_up(q.L, 4);
     h.Mp = q.M * q.p;
+    h.hist_cap = c->hb.hist_cap;
     h.seeds.assign(q.seeds, q.seeds + q.M);
     h.gammas.assign(q.gammas, q.gammas + q.M);
     h.tile = default_tile(q.L, q.p, q.M);
@@ -726,7 +817,7 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
     const int ntiles_min = (h.N + 31) / 32;
     const int Pg_cap = std::max(1, std::min(Gcap, ntiles_min));
     h.arena_bytes = arena_layout(h, Pg_cap, false);
-    e = cudaMalloc(&h.arena, h.arena_bytes);
+    e = dev_malloc(&h.arena, h.arena_bytes);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
     e = cudaMemsetAsync(h.arena, 0, h.arena_bytes, c->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "memset"));
@@ -736,16 +827,16 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
       if (st != EDAA_OK) return bail(st);
     }
   }
-  e = cudaMalloc(&c->d_batch, sizeof(Batch));
+  e = dev_malloc((void**)&c->d_batch, sizeof(Batch));
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
-  e = cudaMalloc(&c->d_status, 64);
+  e = dev_malloc((void**)&c->d_status, 64);
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
   c->d_bar = (unsigned*)(c->d_status + 4);
   c->hb.status = c->d_status;
   c->hb.bar = c->d_bar;
   c->hb.trace_start = c->hb.trace_end = nullptr;
   if (conf.trace) {
-    e = cudaMalloc(&c->d_trace, (size_t)6 * kTraceCap * 8);
+    e = dev_malloc((void**)&c->d_trace, (size_t)6 * kTraceCap * 8);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
     c->hb.trace_start = c->d_trace;
     c->hb.trace_end = c->d_trace + 3 * kTraceCap;
@@ -772,6 +863,7 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
 }
 
 edaa_status edaa_reset(edaa_ctx* c, int cube, const float* X) {
+  NvtxRange nvtx_range("edaa_reset");
   if (!c) return fail(EDAA_ERR_ARG, "ctx is NULL");
   edaa_status st = check_status(c);
   if (st != EDAA_OK) return st;
@@ -786,6 +878,7 @@ edaa_status edaa_reset(edaa_ctx* c, int cube, const float* X) {
 }
 
 edaa_status edaa_step(edaa_ctx* c, int n_outer) {
+  NvtxRange nvtx_range("edaa_step");
   if (!c) return fail(EDAA_ERR_ARG, "ctx is NULL");
   if (n_outer < 0) return fail(EDAA_ERR_ARG, "n_outer must be >= 0");
   edaa_status st = check_status(c);
@@ -796,6 +889,7 @@ edaa_status edaa_step(edaa_ctx* c, int n_outer) {
 }
 
 edaa_status edaa_solve(edaa_ctx* c) {
+  NvtxRange nvtx_range("edaa_solve");
   if (!c) return fail(EDAA_ERR_ARG, "ctx is NULL");
   edaa_status st = check_status(c);
   if (st != EDAA_OK) return st;
@@ -854,6 +948,7 @@ edaa_status edaa_sync(edaa_ctx* c) {
 }
 
 edaa_status edaa_select(edaa_ctx* c, int cube, int* best, double* fit, double* mu) {
+  NvtxRange nvtx_range("edaa_select");
   if (!c || !best) return fail(EDAA_ERR_ARG, "ctx and best are required");
   if (cube < 0 || cube >= (int)c->cubes.size()) return fail(EDAA_ERR_ARG, "cube index out of range");
   edaa_status st = edaa_sync(c);
@@ -870,6 +965,7 @@ edaa_status edaa_select(edaa_ctx* c, int cube, int* best, double* fit, double* m
 }
 
 edaa_status edaa_get(edaa_ctx* c, int cube, int run, float* E, float* A, float* B) {
+  NvtxRange nvtx_range("edaa_get");
   if (!c) return fail(EDAA_ERR_ARG, "ctx is NULL");
   if (cube < 0 || cube >= (int)c->cubes.size()) return fail(EDAA_ERR_ARG, "cube index out of range");
   CubeHost& h = c->cubes[cube];
@@ -893,7 +989,7 @@ edaa_status edaa_get(edaa_ctx* c, int cube, int run, float* E, float* A, float* 
   }
   const size_t nE = (size_t)h.L * h.p, nA = (size_t)h.N * h.p;
   float* tmp = nullptr;
-  CK(cudaMallocAsync((void**)&tmp, (nE + 2 * nA) * 4, c->stream), "scratch");
+  CK(dev_malloc_async((void**)&tmp, (nE + 2 * nA) * 4, c->stream), "scratch");
   float* tE = E ? (dE ? E : tmp) : nullptr;
   float* tA = A ? (dA ? A : tmp + nE) : nullptr;
   float* tB = B ? (dB ? B : tmp + nE + nA) : nullptr;
@@ -915,7 +1011,7 @@ edaa_status edaa_grad(edaa_ctx* c, int cube, int run, float* gA, float* gB) {
   if (st != EDAA_OK) return st;
   const size_t n = (size_t)h.N * h.p;
   float* tmp = nullptr;
-  CK(cudaMallocAsync((void**)&tmp, 2 * n * 4, c->stream), "scratch");
+  CK(dev_malloc_async((void**)&tmp, 2 * n * 4, c->stream), "scratch");
   const CubeDev* dcube = reinterpret_cast<const CubeDev*>(reinterpret_cast<const char*>(c->d_batch) +
                                                           offsetof(Batch, c) + (size_t)cube * sizeof(CubeDev));
   CK(launch_grad(dcube, h.dev, run, gA ? tmp : nullptr, gB ? tmp + n : nullptr, c->stream), "grad");
@@ -927,6 +1023,7 @@ edaa_status edaa_grad(edaa_ctx* c, int cube, int run, float* gA, float* gB) {
 }
 
 edaa_status edaa_loss(edaa_ctx* c, int cube, double* loss) {
+  NvtxRange nvtx_range("edaa_loss");
   if (!c || !loss) return fail(EDAA_ERR_ARG, "ctx and loss are required");
   if (cube < 0 || cube >= (int)c->cubes.size()) return fail(EDAA_ERR_ARG, "cube index out of range");
   edaa_status st = check_status(c);
@@ -937,6 +1034,98 @@ edaa_status edaa_loss(edaa_ctx* c, int cube, double* loss) {
   if (st != EDAA_OK) return st;
   CubeHost& h = c->cubes[cube];
   CK(cudaMemcpy(loss, h.dev.loss2, h.M * 8, cudaMemcpyDeviceToHost), "read loss");
+  return EDAA_OK;
+}
+
+edaa_status edaa_loss_history(edaa_ctx* c, int cube, int cap, double* hist, int* n) {
+  if (!c || !n) return fail(EDAA_ERR_ARG, "ctx and n are required");
+  if (cube < 0 || cube >= (int)c->cubes.size()) return fail(EDAA_ERR_ARG, "cube index out of range");
+  if (!c->hb.record_loss) return fail(EDAA_ERR_STATE, "the loss log is off (config.record_loss = 0)");
+  edaa_status st = edaa_sync(c);
+  if (st != EDAA_OK) return st;
+  CubeHost& h = c->cubes[cube];
+  const int rows = std::min(c->outer_done, h.hist_cap);
+  *n = rows;
+  const int k = std::min(rows, std::max(cap, 0));
+  if (hist && k > 0)
+    CK(cudaMemcpy(hist, h.dev.loss_hist, (size_t)k * h.M * 8, cudaMemcpyDeviceToHost), "read loss log");
+  return EDAA_OK;
+}
+
+edaa_status edaa_checkpoint(edaa_ctx* c, void* buf, size_t cap, size_t* bytes) {
+  if (!c || !bytes) return fail(EDAA_ERR_ARG, "ctx and bytes are required");
+  edaa_status st = edaa_sync(c);
+  if (st != EDAA_OK) return st;
+  size_t total = sizeof(CkptHeader);
+  for (auto& h : c->cubes) {
+    total += sizeof(CkptCube) + (size_t)(h.L + 1) * 8;
+    for (auto& r : state_regions(h)) total += r.bytes;
+  }
+  *bytes = total;
+  if (!buf) return EDAA_OK;
+  if (cap < total) return fail(EDAA_ERR_ARG, "checkpoint buffer too small (query the size with buf = NULL)");
+  char* o = (char*)buf;
+  CkptHeader hd{};
+  memcpy(hd.magic, "EDAACKPT", 8);
+  hd.version = 1;
+  hd.n_cubes = (int)c->cubes.size();
+  hd.outer_done = c->outer_done;
+  hd.record_loss = c->hb.record_loss;
+  hd.hist_cap = c->hb.hist_cap;
+  hd.payload = total - sizeof(CkptHeader);
+  memcpy(o, &hd, sizeof hd);
+  o += sizeof hd;
+  for (auto& h : c->cubes) {
+    const CkptCube cc{h.L, h.N, h.p, h.M, h.tc, h.esz, h.kp, 0};
+    memcpy(o, &cc, sizeof cc);
+    o += sizeof cc;
+    CK(cudaMemcpy(o, h.dev.sx, (size_t)(h.L + 1) * 8, cudaMemcpyDeviceToHost), "checkpoint");
+    o += (size_t)(h.L + 1) * 8;
+    for (auto& r : state_regions(h)) {
+      CK(cudaMemcpy(o, r.ptr, r.bytes, cudaMemcpyDeviceToHost), "checkpoint");
+      o += r.bytes;
+    }
+  }
+  return EDAA_OK;
+}
+
+edaa_status edaa_restore(edaa_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf) return fail(EDAA_ERR_ARG, "ctx and buf are required");
+  edaa_status st = edaa_sync(c);
+  if (st != EDAA_OK) return st;
+  const char* o = (const char*)buf;
+  CkptHeader hd;
+  if (bytes < sizeof hd) return fail(EDAA_ERR_ARG, "not a checkpoint (too short)");
+  memcpy(&hd, o, sizeof hd);
+  if (memcmp(hd.magic, "EDAACKPT", 8) != 0 || hd.version != 1) return fail(EDAA_ERR_ARG, "not a checkpoint");
+  if (hd.payload + sizeof hd != bytes) return fail(EDAA_ERR_ARG, "checkpoint size does not match its header");
+  if (hd.n_cubes != (int)c->cubes.size() || hd.record_loss != c->hb.record_loss || hd.hist_cap != c->hb.hist_cap)
+    return fail(EDAA_ERR_ARG, "checkpoint taken on other cubes or another loss-log setting");
+  o += sizeof hd;
+  // check every cube before writing anything
+  const char* q = o;
+  for (auto& h : c->cubes) {
+    CkptCube cc;
+    memcpy(&cc, q, sizeof cc);
+    if (cc.L != h.L || cc.N != h.N || cc.p != h.p || cc.M != h.M || cc.tc != h.tc || cc.esz != h.esz || cc.kp != h.kp)
+      return fail(EDAA_ERR_ARG, "checkpoint taken on cubes of another shape or precision");
+    q += sizeof cc;
+    std::vector<double> sx(h.L + 1);
+    CK(cudaMemcpy(sx.data(), h.dev.sx, sx.size() * 8, cudaMemcpyDeviceToHost), "restore");
+    if (memcmp(sx.data(), q, sx.size() * 8) != 0)
+      return fail(EDAA_ERR_ARG, "checkpoint taken on other data X (its band sums differ)");
+    q += sx.size() * 8;
+    for (auto& r : state_regions(h)) q += r.bytes;
+  }
+  for (auto& h : c->cubes) {
+    o += sizeof(CkptCube) + (size_t)(h.L + 1) * 8;
+    for (auto& r : state_regions(h)) {
+      CK(cudaMemcpyAsync(r.ptr, o, r.bytes, cudaMemcpyHostToDevice, c->stream), "restore");
+      o += r.bytes;
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream), "restore");
+  c->outer_done = hd.outer_done;
   return EDAA_OK;
 }
 
@@ -992,7 +1181,7 @@ edaa_status edaa_trace_read(edaa_ctx* c, int which, int cap, int* n, int* phase,
   }
   const unsigned long long base = m > 0 ? t0[0] : 0;
   for (int i = 0; i < m && i < cap; ++i) {
-    if (phase) phase[i] = program_phase_id(which, i, c->cfg.K2);
+    if (phase) phase[i] = program_phase_id(which, i, c->cfg.K2, c->hb.record_loss);
     if (start_us) start_us[i] = ((double)t0[i] - (double)base) * 1e-3;
     if (dur_us) dur_us[i] = ((double)t1[i] - (double)t0[i]) * 1e-3;
   }
@@ -1043,6 +1232,8 @@ edaa_status edaa_measure_fma_peak(double* tflops, void* stream) {
   *tflops = best;
   return EDAA_OK;
 }
+
+void edaa_debug_fail_alloc(int k) { g_fail_alloc.store(k < 0 ? -1 : k); }
 
 edaa_status edaa_selftest_barrier(int grid, int extra, double timeout_ms, void* stream) {
   if (grid < 1 || grid > 4096 || extra < 0) return fail(EDAA_ERR_ARG, "grid must be 1..4096, extra >= 0");

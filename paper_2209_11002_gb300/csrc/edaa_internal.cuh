@@ -108,6 +108,7 @@ struct CubeDev {
   double* fitmax;
   double* loss2;
   double* mu;
+  double* loss_hist;  // hist_cap x M: loss after each outer iteration (with record_loss)
   double* rho;     // nlchunk x Mp: per band chunk, sum_l E[l][c] R[l][c] (FP64) for the next B-pass
   int* bref;       // Mp: reference exponent k of the B-pass just run (weights shifted by 2^k)
   double* gpart;   // nlchunk x M x p x p: per band chunk, E^T E of each run (FP64)
@@ -164,6 +165,8 @@ struct Batch {
   int coh_mode;
   long long timeout_ns;
   unsigned int smem_bytes;  // dynamic shared memory of every launch of the program kernel
+  int record_loss;          // 1: every outer iteration ends with the fit pass and logs its loss
+  int hist_cap;             // rows of each cube's loss log
   int* status;
   unsigned int* bar;  // [0] arrivals, [1] generation
   // phase trace (null when off): [mode][phase] first-start / last-end global-timer ns
@@ -230,7 +233,9 @@ inline int padded_ld(int L) {
 }
 
 // Launch helpers implemented in edaa_kernels.cu.
-cudaError_t launch_program(const Batch* d_batch, int mode, int n_outer, int ph_lo, int ph_hi, int grid,
+// outer0: outer iterations completed before this launch sequence (the loss
+// log's row of its first outer iteration)
+cudaError_t launch_program(const Batch* d_batch, int mode, int outer0, int ph_lo, int ph_hi, int grid,
                            size_t smem, bool cooperative, cudaStream_t stream);
 cudaError_t launch_normalize(const float* Xin, float* X, double* scale, double* bsum, double* xbar, double* sx,
                              int L, int Ls, int N, int normalize, int center, cudaStream_t s);
@@ -241,8 +246,8 @@ cudaError_t launch_barrier_test(unsigned int* bar, int* status, int grid, int ex
                                 cudaStream_t s);
 cudaError_t set_program_smem(size_t smem);
 cudaError_t program_occupancy(int* blocks_per_sm, size_t smem);
-int program_phase_count(int mode, int n_outer, int K2);
-int program_phase_id(int mode, int s, int K2);
+int program_phase_count(int mode, int n_outer, int K2, int record);
+int program_phase_id(int mode, int s, int K2, int record);
 cudaError_t launch_tc_prepare(const CubeDev& hc, void* Xk, void* XT, int Npad, cudaStream_t s);
 cudaError_t launch_fill_r16(const CubeDev& hc, cudaStream_t s);
 cudaError_t launch_fma_peak(float* out, int blocks, int iters, cudaStream_t s);

@@ -430,7 +430,7 @@ __device__ void eta_phase(const Batch* __restrict__ bt, float* smem) {
 }
 
 // Fit merge and coherence (Algorithm 2, eq. coherence), one warp per run.
-__device__ void fitm_phase(const Batch* __restrict__ bt, float* smem) {
+__device__ void fitm_phase(const Batch* __restrict__ bt, float* smem, int hist_t) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* Gw = reinterpret_cast<double*>(smem) + warp * kMaxP * kMaxP;
   for (int g = blockIdx.x * kWarps + warp; g < bt->total_runs; g += gridDim.x * kWarps) {
@@ -453,6 +453,8 @@ __device__ void fitm_phase(const Batch* __restrict__ bt, float* smem) {
       cd.fit[m] = a1;
       cd.fitmax[m] = am;
       cd.loss2[m] = a2;
+      // the loss log: row hist_t (the outer iteration just completed, 0-based)
+      if (hist_t >= 0 && hist_t < bt->hist_cap) cd.loss_hist[(size_t)hist_t * cd.M + m] = a2;
       double mu = -INFINITY;
       for (int j = 0; j < P; ++j)
         for (int k = j + 1; k < P; ++k) {
@@ -472,32 +474,37 @@ __device__ void fitm_phase(const Batch* __restrict__ bt, float* smem) {
 // ---------------------------------------------------------------------------
 // The program kernel.
 // ---------------------------------------------------------------------------
-__host__ __device__ inline int phase_of(int mode, int s, int K2) {
+// Phases of an outer iteration: A-pass, A-merge, K2 x (B-pass, B-merge), and
+// with the loss log the fit pass and fit merge.
+__host__ __device__ inline int phases_per_outer(int K2, int record) { return 2 + 2 * K2 + (record ? 2 : 0); }
+
+__host__ __device__ inline int phase_of(int mode, int s, int K2, int record) {
   if (mode == MODE_INIT) {
     const int seq[5] = {PH_INITB, PH_BM0, PH_ETA, PH_INITA, PH_AM};
     return seq[s];
   }
   if (mode == MODE_FIT) return s == 0 ? PH_FIT : PH_FITM;
-  const int per = 2 + 2 * K2;
+  const int per = phases_per_outer(K2, record);
   const int k = s % per;
   if (k == 0) return PH_A;
   if (k == 1) return PH_AM;
+  if (k >= 2 + 2 * K2) return k == 2 + 2 * K2 ? PH_FIT : PH_FITM;
   return (k & 1) ? PH_BM : PH_B;
 }
 
-int program_phase_id(int mode, int s, int K2) { return phase_of(mode, s, K2); }
+int program_phase_id(int mode, int s, int K2, int record) { return phase_of(mode, s, K2, record); }
 
-int program_phase_count(int mode, int n_outer, int K2) {
+int program_phase_count(int mode, int n_outer, int K2, int record) {
   if (mode == MODE_INIT) return 5;
   if (mode == MODE_FIT) return 2;
-  return n_outer * (2 + 2 * K2);
+  return n_outer * phases_per_outer(K2, record);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-k_edaa(const Batch* __restrict__ bt, int mode, int n_outer, int ph_lo, int ph_hi) {
+k_edaa(const Batch* __restrict__ bt, int mode, int outer0, int ph_lo, int ph_hi) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
-  (void)n_outer;
+  const int per = phases_per_outer(bt->K2, bt->record_loss);
   const bool tr = bt->trace_start != nullptr;
   for (int s = ph_lo; s < ph_hi; ++s) {
     if (s > ph_lo) {
@@ -505,7 +512,7 @@ k_edaa(const Batch* __restrict__ bt, int mode, int n_outer, int ph_lo, int ph_hi
     }
     const size_t ti = (size_t)mode * kTraceCap + s;
     if (tr && threadIdx.x == 0 && s < kTraceCap) atomicMin(bt->trace_start + ti, (unsigned long long)global_ns());
-    const int ph = phase_of(mode, s, bt->K2);
+    const int ph = phase_of(mode, s, bt->K2, bt->record_loss);
     switch (ph) {
       case PH_A:
       case PH_B:
@@ -516,7 +523,7 @@ k_edaa(const Batch* __restrict__ bt, int mode, int n_outer, int ph_lo, int ph_hi
       case PH_BM:
       case PH_BM0: merge_phase(bt, ph, smem); break;
       case PH_ETA: eta_phase(bt, smem); break;
-      case PH_FITM: fitm_phase(bt, smem); break;
+      case PH_FITM: fitm_phase(bt, smem, mode == MODE_OUTER ? outer0 + s / per : -1); break;
       default: break;
     }
     if (tr) {
@@ -542,7 +549,7 @@ cudaError_t program_occupancy(int* blocks_per_sm, size_t smem) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_edaa, kThreads, smem);
 }
 
-cudaError_t launch_program(const Batch* d_batch, int mode, int n_outer, int ph_lo, int ph_hi, int grid,
+cudaError_t launch_program(const Batch* d_batch, int mode, int outer0, int ph_lo, int ph_hi, int grid,
                            size_t smem, bool cooperative, cudaStream_t stream) {
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3((unsigned)grid);
@@ -554,7 +561,7 @@ cudaError_t launch_program(const Batch* d_batch, int mode, int n_outer, int ph_l
   at[0].val.cooperative = 1;
   lc.attrs = at;
   lc.numAttrs = cooperative ? 1 : 0;
-  return cudaLaunchKernelEx(&lc, k_edaa, d_batch, mode, n_outer, ph_lo, ph_hi);
+  return cudaLaunchKernelEx(&lc, k_edaa, d_batch, mode, outer0, ph_lo, ph_hi);
 }
 
 // ---------------------------------------------------------------------------

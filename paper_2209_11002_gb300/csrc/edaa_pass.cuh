@@ -392,9 +392,22 @@ __device__ __noinline__ void pass_item(const Batch* __restrict__ bt, const CubeD
       }
     }
     cp_async_wait_all();
-    if (!mbar_wait(xbar, xpar, bt->timeout_ns)) atomicOr(bt->status, kStatTimeout);
+    const int x_late = mbar_wait(xbar, xpar, bt->timeout_ns) ? 0 : 1;
     xpar ^= 1u;
-    __syncthreads();
+    if (__syncthreads_or(x_late)) {
+      // The X tile's bulk copy did not arrive in time: report it, give the
+      // copy a bounded time to land, and end the work item without touching
+      // the tile or re-arming the barrier (the host reports EDAA_ERR_TIMEOUT
+      // at its next synchronising call; this pass's partials are not written).
+      if (tid == 0) {
+        atomicOr(bt->status, kStatTimeout);
+        const unsigned long long t0 = global_ns();
+        while ((long long)(global_ns() - t0) < 50000000ll) __nanosleep(1000);
+        mbar_inval(xbar);
+      }
+      __syncthreads();
+      return;
+    }
     if (g_pending) {
       for (int e = tid; e < nr * P * P; e += kThreads) {
         const int r = e / (P * P), jk = e - r * P * P, j = jk / P, k = jk - j * P;

@@ -27,7 +27,8 @@ EXPORTS = ["edaa_config_default", "edaa_init", "edaa_reset", "edaa_step", "edaa_
            "edaa_select_rule", "edaa_get", "edaa_grad", "edaa_loss", "edaa_step_sizes", "edaa_sync",
            "edaa_outer_done", "edaa_describe", "edaa_destroy", "edaa_last_error", "edaa_selftest_barrier",
            "edaa_fit_eval_static", "edaa_unrolled_create", "edaa_unrolled_forward", "edaa_unrolled_backward",
-           "edaa_unrolled_destroy", "edaa_trace_read", "edaa_describe_tile", "edaa_measure_fma_peak"]
+           "edaa_unrolled_destroy", "edaa_trace_read", "edaa_describe_tile", "edaa_measure_fma_peak", "edaa_debug_fail_alloc",
+           "edaa_loss_history", "edaa_checkpoint", "edaa_restore"]
 
 
 class Config(ctypes.Structure):
@@ -35,7 +36,7 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("fit_norm", ctypes.c_int), ("coherence", ctypes.c_int),
                 ("fit_ratio", ctypes.c_double), ("persistent", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("barrier_timeout_ms", ctypes.c_double), ("center", ctypes.c_int), ("trace", ctypes.c_int),
-                ("tile", ctypes.c_int * 4)]
+                ("tile", ctypes.c_int * 4), ("record_loss", ctypes.c_int)]
 
 
 class CubeDesc(ctypes.Structure):
@@ -91,6 +92,10 @@ def load_library():
         "edaa_trace_read": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip, ip, dp, dp]),
         "edaa_describe_tile": (ctypes.c_int, [vp, ctypes.c_int, ip]),
         "edaa_measure_fma_peak": (ctypes.c_int, [dp, vp]),
+        "edaa_debug_fail_alloc": (None, [ctypes.c_int]),
+        "edaa_loss_history": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, ip]),
+        "edaa_checkpoint": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+        "edaa_restore": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -247,6 +252,29 @@ class Context:
         M = self.shapes[cube][3]
         out = np.zeros(M)
         _check(self.lib.edaa_loss(self.h, cube, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "edaa_loss")
+        return out
+
+    def checkpoint(self) -> bytes:
+        """The iteration state of every run (edaa_checkpoint), as bytes."""
+        n = ctypes.c_size_t()
+        _check(self.lib.edaa_checkpoint(self.h, None, 0, ctypes.byref(n)), "edaa_checkpoint")
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self.lib.edaa_checkpoint(self.h, buf, n.value, ctypes.byref(n)), "edaa_checkpoint")
+        return buf.raw
+
+    def restore(self, state: bytes):
+        """Resume from a checkpoint of a context with the same cubes and X (edaa_restore)."""
+        _check(self.lib.edaa_restore(self.h, state, len(state)), "edaa_restore")
+
+    def loss_history(self, cube: int = 0) -> np.ndarray:
+        """(outer iterations recorded) x M losses, row t after outer iteration
+        t + 1 (needs record_loss=1)."""
+        M = self.shapes[cube][3]
+        n = ctypes.c_int()
+        _check(self.lib.edaa_loss_history(self.h, cube, 0, None, ctypes.byref(n)), "edaa_loss_history")
+        out = np.zeros((n.value, M))
+        _check(self.lib.edaa_loss_history(self.h, cube, n.value, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          ctypes.byref(n)), "edaa_loss_history")
         return out
 
     def step_sizes(self, cube: int = 0):
