@@ -155,13 +155,12 @@ def unrolled_workload(args, rank, world):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # dominant kernel, from ncu captures with the kernels as they stand; keyed by
 # (workload, precision, outer iterations).  Absent entries report null.
-# Jasper: the persistent solve launch itself.  Urban: one launch per phase
-# (--persistent 0) of one outer iteration, scaled to the T outer iterations
-# of the persistent launch (the passes of every outer iteration move the same
-# data).
+# Urban: one launch per phase (--persistent 0) of one outer iteration, scaled
+# to the T outer iterations of the persistent launch (the passes of every
+# outer iteration move the same data; the fit launch, one more X pass, is
+# not included).
 SOLVE_DRAM_BYTES = {
-    ("jasper", "fp32", 100): 26544640 + 443870464,
-    ("jasper", "bf16", 100): 26184448 + 29152000,
+    ("urban", "bf16", 100): 100 * 1120424192,
 }
 
 
