@@ -319,7 +319,9 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
   size_t oseeds = take(M * 8), ogam = take(M * 8);
   size_t orho = take(L * Mp * 8), obref = take(Mp * 4);  // nlchunk <= L band chunks
   size_t ogpart = take(L * M * p * p * 8);
-  size_t oXk = take(tcb * parts * N * h.kp * h.esz), oXT = take(tcb * parts * (L + 1) * h.Npad * h.esz);
+  // the band-major copy of X only for TF32 (BF16 passes read the pixel-major tiles both ways)
+  const size_t xtb = (h.tc == 1 || h.tc == 3) ? 1 : 0;
+  size_t oXk = take(tcb * parts * N * h.kp * h.esz), oXT = take(xtb * parts * (L + 1) * h.Npad * h.esz);
   size_t opE = take(tcb * parts * Mp * h.kp * h.esz), opS = take(tcb * 2 * Mp * h.kp * h.esz);
   size_t oSd = take(tcb * L * Mp * 8), oRd = take(tcb * L * Mp * 8), olam = take(tcb * Mp * 8);
   size_t or16 = take(tcb * Nst * Mp * 2);
@@ -363,7 +365,7 @@ static size_t arena_layout(CubeHost& h, int Pg_cap, bool assign) {
     h.scale = (double*)(b + oscale);
     if (h.tc) {
       h.Xk = b + oXk;
-      h.XT = b + oXT;
+      h.XT = xtb ? b + oXT : nullptr;
       d.Xk = h.Xk;
       d.panelE = b + opE;
       d.panelS = b + opS;
@@ -416,7 +418,7 @@ static edaa_status make_tmaps(edaa_ctx* c, CubeHost& h) {
   const size_t nP = (size_t)h.Mp * h.kp * h.esz;
   struct Spec { void* ptr; cuuint64_t inner, outer; cuuint32_t box_outer; bool used; } spec[TM_STATE] = {
       {h.Xk, (cuuint64_t)h.kp, (cuuint64_t)h.N, 128, true},
-      {h.XT, (cuuint64_t)h.Npad, (cuuint64_t)(h.L + 1), 128, true},
+      {h.XT, (cuuint64_t)h.Npad, (cuuint64_t)(h.L + 1), 128, h.tc != 2},
       {h.dev.panelE, (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp, true},
       {h.dev.panelS, (cuuint64_t)h.kp, (cuuint64_t)h.Mp, (cuuint32_t)rgp, true},
       {(char*)h.Xk + nXk, (cuuint64_t)h.kp, (cuuint64_t)h.N, 128, h.tc == 3},
@@ -780,7 +782,9 @@ edaa_status edaa_init(edaa_ctx** out, const edaa_cube* cubes, int n_cubes, const
     if (conf.precision != EDAA_FP32 && h.Mp >= 64) {
       h.tc = conf.precision == EDAA_BF16 ? 2 : (conf.precision == EDAA_TF32X3 ? 3 : 1);
       h.esz = h.tc == 2 ? 2 : 4;
-      h.kp = round_up(q.L + 1, 128 / h.esz);
+      // bands per pixel row of the compute-type X (BF16: whole 64-band chunks,
+      // at least two, as contraction 2 reads 128 bands per MMA)
+      h.kp = h.tc == 2 ? 64 * tc_nkx(q.L) : round_up(q.L + 1, 128 / h.esz);
       h.Npad = round_up(q.N, 8);
       tc_tile(h);
     }

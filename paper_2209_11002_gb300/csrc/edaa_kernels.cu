@@ -795,8 +795,9 @@ cudaError_t launch_gather(const CubeDev& hc, int run, float* E, float* A, float*
 }
 
 // Compute-type copies of the centred X for the tensor-core passes:
-// Xk: N x kp pixel-major (bands >= L+1 zero), XT: (L+1) x Npad band-major
-// (row L is the ones band), TF32 rounded to nearest or BF16.
+// Xk: N x kp pixel-major (band L is the ones band, bands > L zero), XT
+// (TF32 only; null for BF16): (L+1) x Npad band-major, TF32 rounded to
+// nearest or BF16.
 // mode 1: TF32, 2: BF16, 3: split TF32 (high part, then the low part
 // tf32(x - high) in a second copy of each array right after the first)
 __global__ void k_tc_prepare(const float* __restrict__ X, int L, int Ls, int N, int kp, int Npad, int mode,
@@ -809,7 +810,7 @@ __global__ void k_tc_prepare(const float* __restrict__ X, int L, int Ls, int N, 
     if (mode == 2) {
       const __nv_bfloat16 h = __float2bfloat16_rn(v);
       reinterpret_cast<__nv_bfloat16*>(Xk)[e] = h;
-      if (l <= L) reinterpret_cast<__nv_bfloat16*>(XT)[t] = h;
+      if (XT != nullptr && l <= L) reinterpret_cast<__nv_bfloat16*>(XT)[t] = h;
     } else {
       const float hi = tf32_rna(v);
       reinterpret_cast<float*>(Xk)[e] = hi;

@@ -3,30 +3,40 @@
 //
 // Per CTA: one run group (Rg = Rm*p columns, padded to Rgp, a multiple of
 // 16) and the pixel tiles pg, pg + Pg, ... of 128 pixels.  Per tile:
-//   1. C (128 px x Rgp) = X_tile (128 x L) * Panel^T: the tile's pixel-major
-//      rows and the panel stream through a ring of TMA stages (128-byte
-//      swizzle, K-major) into tcgen05.mma with the accumulator in TMEM columns
-//      [0, Rgp).  The A-pass's panel is E.  The B-pass's is S + eta2 R, the
-//      running sum of eta2 times the B-gradient factors R of every B-step so
-//      far (eq. update_B), as a high and a low part (two MMAs per K chunk).
+//   1. C (128 px x Rgp) = X_tile (128 x L) * Panel^T by tcgen05.mma (128-byte
+//      swizzle, K-major operands), the accumulator in TMEM columns [0, Rgp).
+//      The panel stays in shared memory for the whole pass: E for the A-pass;
+//      for the B-pass S + eta2 R, the running sum of eta2 times the
+//      B-gradient factors R of every B-step so far (eq. update_B), as a high
+//      and a low part (two MMAs per K step).
 //   2. Epilogue (8 warps; warp w reads TMEM lanes 32*(w%4).. = its pixels and
 //      handles the runs of parity w/4):
 //      A: the tile's log-abundance state arrives in shared memory by one TMA
-//         load issued before contraction 1; the K1 fused A-steps update it in
-//         place and one TMA store writes it back.
+//         load; the K1 fused A-steps update it in place and one TMA store
+//         writes it back.
 //      B: no per-pixel state.  The logits are u = 0.1 r - Lambda - C, with r
-//         the SplitMix64 uniforms of B^0 regenerated in registers (eq.
-//         initB0); u goes back into C's TMEM columns while the column maxima
-//         are formed, and the weights are computed from there.
+//         the B^0 uniforms (eq. initB0) from a 16-bit table slice loaded by
+//         TMA with the tile (split operands: the exact 24-bit draw from
+//         SplitMix64 in registers); the weights are formed in a fixed
+//         power-of-two frame per column.
 //      Both write W = weights - reference (shifted accumulation) into shared
 //      memory in the swizzled K-major layout the MMA reads.
 //   3. Acc (bands x Rgp) += X_bands (128 bands x 128 px) * W^T for each
-//      128-band tile, the band-major copy of X streaming through the same TMA
-//      ring; Acc lives in TMEM columns [Rgp*(1+bt), Rgp*(2+bt)) across all tiles.
-// The B-pass rescales Acc in TMEM (tcgen05.ld/st, exact powers of two) when a
-// tile raises a column's running maximum.  At the end the accumulators are
-// written as the same per-CTA partials the CUDA-core pass writes, so the FP64
-// merges are shared.  Every mbarrier wait is bounded.
+//      128-band tile; Acc lives in TMEM columns [Rgp*(1+bt), Rgp*(2+bt))
+//      across all tiles of the CTA.
+// X reaches shared memory in one of two ways:
+//   TF32 (and split TF32): a ring of 16 KB stages streams the tile's
+//     pixel-major chunks for contraction 1, then the chunks of a band-major
+//     copy of X for contraction 2.
+//   BF16: the whole pixel-major tile (tc_nkx 64-band chunks) is loaded once
+//     into one of two tile buffers, and contraction 2 reads the same chunks
+//     as an MN-major operand (bands are the M index: two consecutive 64-band
+//     chunks per MMA), so no band-major copy exists.  The next tile's X
+//     streams into the other buffer during this tile's epilogue, and the next
+//     tile's contraction 1 is issued right behind this tile's contraction 2.
+// At the end the accumulators are written as the same per-CTA partials the
+// CUDA-core pass writes, so the FP64 merges are shared.  Every mbarrier wait
+// is bounded.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -54,10 +64,20 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
+// The same for an MN-major operand with 128-byte swizzle: each 128-byte row
+// holds 128 B of consecutive M (or N) indices at one K index, 8 K rows form a
+// 1024-byte atom and the atoms follow each other along K (stride 1024 B);
+// the next 128 B of M indices start `mn_stride` bytes further on (the
+// leading-byte-offset field).
+__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr, uint32_t mn_stride) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((mn_stride >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
 // instruction descriptor: FP32 accumulator, A and B of format fmt (tf32: 2, bf16: 1), K-major
-__host__ __device__ constexpr uint32_t tc_idesc(int M, int N, int fmt) {
-  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
+// (a_mn: A is MN-major instead)
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N, int fmt, bool a_mn = false) {
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((a_mn ? 1u : 0u) << 15) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 template <bool BF>
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
@@ -142,26 +162,51 @@ __device__ __forceinline__ float to_tf32(float x) {
 struct TcSmem {
   uint32_t stages, panel_off, w_off, state_off, misc_off, total;
 };
+// BF16 X tiles: 128 pixels x kp bands in 64-band (128-byte) chunks, at least
+// two (contraction 2 reads two consecutive chunks, 128 bands, per MMA)
+__host__ __device__ inline int tc_nkx(int L) {
+  const int n = (L + 1 + 63) / 64;
+  return n < 2 ? 2 : n;
+}
+// The misc region: barriers and flags (256 B), eight column arrays of cs
+// floats (cs = Rgp rounded up to 32), the run step sizes (128 floats), and for
+// the A-pass G = E^T E (Rm x p x p) and the A A^T sums (4 x Rm x p(p+1)/2).
+struct TcMisc {
+  uint32_t cs, cols, eta, g, aaq, total;
+};
+__host__ __device__ inline TcMisc tc_misc(int Rgp, int p, bool is_a) {
+  TcMisc m;
+  const uint32_t rm = (uint32_t)(Rgp / p), pp = (uint32_t)(p * (p + 1) / 2);
+  m.cs = ((uint32_t)Rgp + 31u) & ~31u;
+  m.cols = 256u;
+  m.eta = m.cols + 8u * m.cs * 4u;
+  m.g = m.eta + 128u * 4u;
+  m.aaq = m.g + (is_a ? rm * (uint32_t)(p * p) * 4u : 0u);
+  m.total = (m.aaq + (is_a ? 4u * rm * pp * 4u : 0u) + 1023u) & ~1023u;
+  return m;
+}
 // Shared memory of a tensor-core pass, per pass kind.  The run group's panel
 // is resident for the whole pass (nkc K chunks of Rgp rows x 128 B): the
 // A-pass's E (split operands: its high and low part), the B-pass's
-// S + eta2 R as a high and a low part.  The ring stages hold one
-// 128 x 128-byte chunk of X each (contraction 1: pixel-major, contraction 2:
-// band-major).  W holds the weights of one 128-pixel tile in 128-byte pixel
-// chunks (split: high and low part).  The tile's slice of a per-pixel table
-// follows (Rgp rows of 128 pixels): the A-pass's log-abundance state, the
-// B-pass's B^0 uniforms.  The misc region holds the barriers and flags
-// (256 B), eight 256-entry column arrays, the step sizes (128), G (2048) and
-// the A A^T sums (4 x Rm x PP with Rm <= Rgp / p); 1 KB alignment slack.
+// S + eta2 R as a high and a low part.  Then the X staging area, in units:
+//   TF32 (and split): a ring of stages, each one 128 x 128-byte chunk of X
+//     (contraction 1: pixel-major, contraction 2: band-major);
+//   BF16: one or two whole 128-pixel X tiles (tc_nkx chunks each), read by
+//     both contractions (contraction 2 as an MN-major operand).
+// W holds the weights of one 128-pixel tile in 128-byte pixel chunks (split:
+// high and low part).  The tile's slice of a per-pixel table follows (Rgp
+// rows of 128 pixels): the A-pass's log-abundance state, the B-pass's B^0
+// uniforms.  Then the misc region (tc_misc); 1 KB alignment slack first.
 constexpr uint32_t kTcStageBytes = 128u * 128u;
 constexpr int kTcMaxStages = 8;
-__host__ __device__ inline uint32_t tc_misc_bytes(int Rgp, int p) {
-  const uint32_t rm = (uint32_t)(Rgp / p), pp = (uint32_t)(p * (p + 1) / 2);
-  return (256u + 8u * 256u * 4u + 128u * 4u + 2048u * 4u + 4u * rm * pp * 4u + 1023u) & ~1023u;
-}
 __host__ __device__ inline int tc_nkc(int L, int esz) { return (L + 128 / esz - 1) / (128 / esz); }
-// `stages` ring stages; 0 = as many as fit in `cap` bytes (at most
-// kTcMaxStages, at least 2: a layout that does not fit says so by its total)
+// bytes of one unit of the X staging area and the most units used
+__host__ __device__ inline uint32_t tc_x_unit(int L, int esz) {
+  return esz == 2 ? (uint32_t)tc_nkx(L) * kTcStageBytes : kTcStageBytes;
+}
+// `stages` units of X staging; 0 = as many as fit in `cap` bytes (ring: at
+// most kTcMaxStages, at least 2; BF16 tiles: at most 2, at least 1; a layout
+// that does not fit says so by its total)
 __host__ __device__ inline TcSmem tc_smem_n(int Rgp, int esz, bool split, int p, bool is_a, int L, uint32_t stages,
                                            uint32_t cap) {
   TcSmem s;
@@ -169,22 +214,24 @@ __host__ __device__ inline TcSmem tc_smem_n(int Rgp, int esz, bool split, int p,
   const uint32_t pparts = (split || !is_a) ? 2u : 1u;
   const uint32_t wparts = split ? 2u : 1u;
   const uint32_t npc = (uint32_t)esz;  // 128-byte pixel chunks per 128-pixel tile (128 / (128 / esz))
+  const uint32_t unit = tc_x_unit(L, esz);
+  const uint32_t umax = esz == 2 ? 2u : (uint32_t)kTcMaxStages, umin = esz == 2 ? 1u : 2u;
   s.panel_off = 1024u;
   const uint32_t ring_off = s.panel_off + pparts * (uint32_t)tc_nkc(L, esz) * pnl;
   const uint32_t fixed = wparts * npc * pnl + (((uint32_t)Rgp * (is_a ? 512u : 256u) + 1023u) & ~1023u) +
-                         tc_misc_bytes(Rgp, p);
+                         tc_misc(Rgp, p, is_a).total;
   if (stages == 0) {
     const uint32_t room = cap > ring_off + fixed ? cap - ring_off - fixed : 0u;
-    stages = room / kTcStageBytes;
-    if (stages > (uint32_t)kTcMaxStages) stages = kTcMaxStages;
-    if (stages < 2u) stages = 2u;  // does not fit: the total says so
+    stages = room / unit;
+    if (stages > umax) stages = umax;
+    if (stages < umin) stages = umin;  // does not fit: the total says so
   }
   s.stages = stages;
-  s.w_off = ring_off + stages * kTcStageBytes;
+  s.w_off = ring_off + stages * unit;
   s.state_off = s.w_off + wparts * npc * pnl;
   // the per-tile slice of a per-pixel table: A the state (float), B the B^0 uniforms (uint16)
   s.misc_off = s.state_off + (((uint32_t)Rgp * (is_a ? 512u : 256u) + 1023u) & ~1023u);
-  s.total = s.misc_off + tc_misc_bytes(Rgp, p);
+  s.total = s.misc_off + tc_misc(Rgp, p, is_a).total;
   return s;
 }
 // 226 KB: one CTA's 227 KB of shared memory less 1 KB for the program
@@ -206,8 +253,8 @@ __host__ __device__ inline uint32_t tc_smem_max(int Rgp, int esz, bool split, in
 // columns) and one Acc per 128-band tile (split operands: a per-tile Acc and
 // a running sum per band tile), with 8 spare columns so that the 8-wide TMEM
 // reads of the last run stay inside the 512 allocated; the shared memory of
-// both pass kinds, with at least three ring stages where that is possible,
-// stays within kTcSmemCap.
+// both pass kinds stays within kTcSmemCap with, where that is possible, at
+// least three ring stages (TF32) or two X tiles (BF16).
 __host__ __device__ inline int tc_rgp_max(int L, int esz, bool split, int p) {
   const int nbt = (L + 1 + 127) / 128;
   int r = ((512 - 8) / (1 + (split ? 2 : 1) * nbt)) & ~15;
@@ -215,10 +262,11 @@ __host__ __device__ inline int tc_rgp_max(int L, int esz, bool split, int p) {
     return tc_smem_n(rg, esz, split, p, true, L, st, kTcSmemCap).total <= kTcSmemCap &&
            tc_smem_n(rg, esz, split, p, false, L, st, kTcSmemCap).total <= kTcSmemCap;
   };
+  const uint32_t want = esz == 2 ? 2u : 3u, least = esz == 2 ? 1u : 2u;
   int r3 = r;
-  while (r3 > 16 && !fits(r3, 3u)) r3 -= 16;
-  if (fits(r3, 3u)) return r3;
-  while (r > 16 && !fits(r, 2u)) r -= 16;
+  while (r3 > 16 && !fits(r3, want)) r3 -= 16;
+  if (fits(r3, want)) return r3;
+  while (r > 16 && !fits(r, least)) r -= 16;
   return r;
 }
 

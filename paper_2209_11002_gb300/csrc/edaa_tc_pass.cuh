@@ -62,6 +62,9 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   constexpr int KCH = 128 / ESZ;   // elements per 128-byte row (32 tf32, 64 bf16)
   constexpr int NPC = 128 / KCH;   // pixel chunks per 128-pixel tile
   constexpr uint32_t FMT = BF ? 1u : 2u;
+  // BF16: whole X tiles, contraction 2 reads them as an MN-major operand
+  // (TF32 keeps the stage ring and the band-major copy of X)
+  constexpr bool MNX = BF;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int quarter = warp & 3, half = warp >> 2;
   const int L = cd.L, N = cd.N, Mp = cd.Mp, Rm = cd.Rm;
@@ -86,7 +89,9 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   unsigned char* Psm = sm + (S.panel_off - 1024u);  // resident panel: [part][K chunk] chunks of pnl bytes
   unsigned char* ring = Psm + (TWO ? 2u : 1u) * (uint32_t)nkc * pnl;
   unsigned char* misc = sm + (S.misc_off - 1024u);
-  uint64_t* full = reinterpret_cast<uint64_t*>(misc);      // kTcMaxStages
+  const TcMisc ML = tc_misc(Rgp, P, IS_A);
+  const int cs = (int)ML.cs;                               // column-array length
+  uint64_t* full = reinterpret_cast<uint64_t*>(misc);      // kTcMaxStages (BF16: one per X tile buffer)
   uint64_t* empty = full + kTcMaxStages;                   // kTcMaxStages
   uint64_t* bar_c1 = empty + kTcMaxStages;
   uint64_t* bar_c2 = bar_c1 + 1;
@@ -97,17 +102,17 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   // B: every column keeps its weights as e^u 2^-F in a power-of-two frame F
   // (exact rescales); F starts at the reference exponent k and follows the
   // largest logit seen, one tile late
-  float* colF = reinterpret_cast<float*>(flags + 4);       // Rgp: frame F of Acc and of this tile's weights (B)
-  int* colKey = reinterpret_cast<int*>(colF + 256);        // Rgp: tile maximum logit (B)
-  float* colScale = reinterpret_cast<float*>(colKey + 256);  // Rgp: 2^(F - Fn), the pending rescale (B)
-  float* colLam = colScale + 256;                          // Rgp: Lambda, the logits' offset (B)
-  float* runEta = colLam + 256;                            // Rm (<= 128)
-  int* colRef = reinterpret_cast<int*>(runEta + 128);      // Rgp: reference exponent k (B)
-  float* colRefW = reinterpret_cast<float*>(colRef + 256);  // Rgp: 2^(k - F), the reference weight (B)
-  float* colFn = colRefW + 256;                            // Rgp: the frame after this tile (B)
-  float* colC = colFn + 256;                               // Rgp: (kR16Scale / 2 - Lambda) log2 e - F (B)
-  float* Gs = colC + 256;                                  // Rm x P x P (A), <= 2048
-  float* aaq = Gs + 2048;                                  // 4 x Rm x PP (A)
+  float* colF = reinterpret_cast<float*>(misc + ML.cols);  // frame F of Acc and of this tile's weights (B)
+  int* colKey = reinterpret_cast<int*>(colF + cs);         // tile maximum logit (B)
+  float* colScale = reinterpret_cast<float*>(colKey + cs);  // 2^(F - Fn), the pending rescale (B)
+  float* colLam = colScale + cs;                           // Lambda, the logits' offset (B)
+  int* colRef = reinterpret_cast<int*>(colLam + cs);       // reference exponent k (B)
+  float* colRefW = reinterpret_cast<float*>(colRef + cs);  // 2^(k - F), the reference weight (B)
+  float* colFn = colRefW + cs;                             // the frame after this tile (B)
+  float* colC = colFn + cs;                                // (kR16Scale / 2 - Lambda) log2 e - F (B)
+  float* runEta = reinterpret_cast<float*>(misc + ML.eta);  // Rm (<= 128)
+  float* Gs = reinterpret_cast<float*>(misc + ML.g);       // Rm x P x P (A)
+  float* aaq = reinterpret_cast<float*>(misc + ML.aaq);    // 4 x Rm x PP (A)
 
   // ---- set-up: barriers, TMEM (512 columns: one CTA per SM), per-run constants
   if (warp == 0) {
@@ -128,13 +133,13 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     flags[1] = 0;
     flags[2] = 0;
   }
-  for (int c = tid; c < 256; c += kThreads) {
+  for (int c = tid; c < cs; c += kThreads) {
     colKey[c] = ord_key(-EDAA_INF);
     colScale[c] = 1.f;
     colLam[c] = 0.f;
   }
   if (!IS_A)
-    for (int c = tid; c < 256; c += kThreads) {
+    for (int c = tid; c < cs; c += kThreads) {
       // k is a lower bound of log2 of the column's mean weight, so its largest
       // weight is at least 2^(k - 1/2): a first frame of k never underflows
       const int k = (!init && c < nc) ? ref_exponent(cd, m0 + c / P, c0 + c) : 0;
@@ -247,7 +252,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   };
   if (tid == 0) {  // the maps this pass uses, into the descriptor cache before the first copy
     tmap_prefetch(tmX);
-    tmap_prefetch(tmXT);
+    if (!MNX) tmap_prefetch(tmXT);
     tmap_prefetch(tmState);
     if (do_c1) {
       tmap_prefetch(tmPan);
@@ -265,7 +270,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
       if (TWO) tma2d(Psm + (nkc + kc) * pnl, tmPanLo, kc * KCH, c0, bar_pn);
     }
   }
-  if (tid == 0) fill();
+  if (!MNX && tid == 0) fill();
   bool panel_ready = !do_c1;
 
   // Split operands: contraction 2 of each tile restarts a tile accumulator T
@@ -327,74 +332,9 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     __syncthreads();
   };
 
-  for (int q = 0; q < ntl; ++q) {
-    const int i0 = (pg + q * cd.Pg) * kTcTile;
-    const int ni = min(kTcTile, N - i0);
-    // the tile's table slice (A: the state, B: the uniforms): one TMA load, once
-    // the previous tile's state store has read the buffer
-    if ((IS_A ? !init : !SPLIT) && tid == 0 && !flags[0]) {
-      if (st_stored) bulk_wait_read();
-      mbar_expect(bar_st, state_bytes);
-      tma2d(Sst, tmState, i0, c0, bar_st);
-    }
-    // ---- 1. C = X_tile Panel^T (skipped for the initial passes: c = 0)
-    if (do_c1) {
-      if (tid == 0 && !flags[0]) {
-        bool ok = true;
-        if (!panel_ready) {
-          ok = mbar_wait(bar_pn, 0, tmo);
-          panel_ready = true;
-          tc_fence_after();
-        }
-        for (int j = 0; j < nc1 && ok; ++j) {
-          const int kc = j >> SUBS, part = j & SUBS;
-          ok = consume([&](unsigned char* st) {
-            // descriptors of the chunk's first K step; each further 32-byte K
-            // step adds 2 to the start-address field (address / 16)
-            const uint64_t da0 = desc_sw128(su32(st));
-            const uint64_t dh0 = desc_sw128(su32(Psm + kc * pnl));  // the resident panel's K chunk kc
-            const uint64_t dl0 = desc_sw128(su32(Psm + (nkc + kc) * pnl));
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              const uint64_t da = da0 + 2u * ks;
-              tc_mma<BF>(tbase, da, dh0 + 2u * ks, id, (kc | ks | part) ? 1u : 0u);
-              if (TWO && part == 0)  // X * P lo (split: X hi * P lo)
-                tc_mma<BF>(tbase, da, dl0 + 2u * ks, id, 1u);
-            }
-          });
-        }
-        if (ok) tc_commit(bar_c1);
-        else flags[0] = 1;
-      }
-      __syncthreads();
-      const int to = flags[0] ? 1 : (mbar_wait(bar_c1, c1_phase, tmo) ? 0 : 2);
-      if (to) atomicOr(bt->status, 1 << (8 + to));  // 9: contraction-1 pipeline, 10: its commit
-      if (__syncthreads_or(to)) {
-        bail = 1;
-        break;
-      }
-      c1_phase ^= 1;
-      tc_fence_after();
-      if (tid == 0) fill();  // contraction 1's stages are free: stream the next chunks during the epilogue
-    }
-    // the previous tile's contraction 2 must finish before W is rewritten or Acc rescaled
-    if (c2_pending) {
-      const int to = mbar_wait(bar_c2, c2_phase, tmo) ? 0 : 1;
-      if (to) atomicOr(bt->status, 1 << 11);  // contraction 2 of the previous tile
-      if (__syncthreads_or(to)) {
-        bail = 1;
-        break;
-      }
-      c2_phase ^= 1;
-      c2_pending = false;
-      tc_fence_after();
-      if (tid == 0) fill();  // the previous contraction 2's stages are free as well
-      if (SPLIT) {
-        fold_tile(!folded);
-        folded = true;
-      }
-    }
-    // ---- 2. epilogue: warp (quarter, half) = pixels 32*quarter.., runs of parity `half`
+  // ---- 2. the epilogue of one tile (pixels i0 .. i0 + ni - 1): warp (quarter,
+  // half) = pixels 32*quarter.., runs of parity `half`.  False: a wait timed out.
+  auto epilogue = [&](int i0, int ni) -> bool {
     const int il = quarter * 32 + lane;
     const bool valid = il < ni;
     unsigned char* wl = Wsm + (il / KCH) * wchunk;   // this pixel's 128-byte K chunk of W
@@ -415,10 +355,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
       if (!init) {  // the state tile has landed
         const int to = mbar_wait(bar_st, st_phase, tmo) ? 0 : 1;
         if (to) atomicOr(bt->status, 1 << 14);  // the A state tile's load
-        if (__syncthreads_or(to)) {
-          bail = 1;
-          break;
-        }
+        if (__syncthreads_or(to)) return false;
         st_phase ^= 1;
       }
       // eq. (update_A), K1 steps per (pixel, run).  The run's G = E^T E is
@@ -568,10 +505,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
       if (!SPLIT) {
         const int to = mbar_wait(bar_st, st_phase, tmo) ? 0 : 1;  // the uniforms have landed
         if (to) atomicOr(bt->status, 1 << 14);
-        if (__syncthreads_or(to)) {
-          bail = 1;
-          break;
-        }
+        if (__syncthreads_or(to)) return false;
         st_phase ^= 1;
       }
       constexpr int kRB = 2;
@@ -643,50 +577,272 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
         b_weights(false);
       }
     }
-    // ---- 3. Acc += X_bands W^T (W and the A state from generic-proxy stores -> async proxy)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
+    return true;
+  };
+
+  if constexpr (MNX) {
+    // ---- BF16: whole X tiles in NB (1 or 2) buffers.  Tile q uses buffer
+    // q % NB; its X is loaded once and read by both contractions.  Thread 0,
+    // after tile q's epilogue: the state store (A) or the next uniforms (B),
+    // contraction 2 of tile q, the next state slice (A), contraction 1 of
+    // tile q + 1.  The other buffer's next X is loaded at the start of the
+    // epilogue, once contraction 2 of the previous tile has read it.
+    const uint32_t NB = S.stages;
+    const int nkx = tc_nkx(L);
+    const uint32_t xtb = (uint32_t)nkx * kTcStageBytes;
+    const uint32_t id2 = tc_idesc(128, Rgp, FMT, true);  // contraction 2: A = X^T, MN-major
+    const bool need_slice = IS_A ? !init : true;
+    auto xbuf = [&](int q) -> uint32_t { return NB == 2 ? (uint32_t)(q & 1) : 0u; };
+    auto xpar = [&](int q) -> uint32_t { return (uint32_t)(NB == 2 ? (q >> 1) : q) & 1u; };
+    auto load_x = [&](int q) {
+      const uint32_t b = xbuf(q);
+      unsigned char* dst = ring + b * xtb;
+      mbar_expect(full + b, xtb);
+      const int ti0 = (pg + q * cd.Pg) * kTcTile;
+      for (int kc = 0; kc < nkx; ++kc) tma2d(dst + kc * kTcStageBytes, tmX, kc * KCH, ti0, full + b);
+    };
+    auto load_slice = [&](int q) {
+      mbar_expect(bar_st, state_bytes);
+      tma2d(Sst, tmState, (pg + q * cd.Pg) * kTcTile, c0, bar_st);
+    };
+    // C = X_q Panel^T (B: high and low panel parts)
+    auto issue_c1 = [&](int q) -> bool {
+      if (!mbar_wait(full + xbuf(q), xpar(q), tmo)) return false;
       tc_fence_after();
-      if (IS_A) {  // the new state tile back to global memory
-        tma2d_store(tmState, i0, c0, Sst);
-        bulk_commit();
-        st_stored = true;
-      }
-      if (!flags[0]) {
-        const bool first = !d2_started;
-        bool ok = true;
-        for (int j = 0; j < nc2 && ok; ++j) {
-          const int kc = j >> SUBS, part = j & SUBS, bti = kc >> NPCS, pc = kc & (NPC - 1);
-          ok = consume([&](unsigned char* st) {
-            const uint32_t dcol = tbase + (uint32_t)(Rgp * (1 + bti));
-            const uint64_t da0 = desc_sw128(su32(st));
-            const uint64_t db0 = desc_sw128(su32(Wsm + pc * wchunk));
-            const uint64_t dl0 = desc_sw128(su32(Wsm + (NPC + pc) * wchunk));
+      unsigned char* xb = ring + xbuf(q) * xtb;
+      for (int kc = 0; kc < nkc; ++kc) {
+        const uint64_t da0 = desc_sw128(su32(xb + kc * kTcStageBytes));
+        const uint64_t dh0 = desc_sw128(su32(Psm + kc * pnl));
+        const uint64_t dl0 = desc_sw128(su32(Psm + (nkc + kc) * pnl));
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              const uint64_t da = da0 + 2u * ks;
-              tc_mma<BF>(dcol, da, db0 + 2u * ks, id,
-                         ((SPLIT || first) && pc == 0 && part == 0 && ks == 0) ? 0u : 1u);
-              if (SPLIT && part == 0)  // X hi * W lo
-                tc_mma<BF>(dcol, da, dl0 + 2u * ks, id, 1u);
-            }
-          });
+        for (int ks = 0; ks < 4; ++ks) {
+          tc_mma<BF>(tbase, da0 + 2u * ks, dh0 + 2u * ks, id, (kc | ks) ? 1u : 0u);
+          if (TWO) tc_mma<BF>(tbase, da0 + 2u * ks, dl0 + 2u * ks, id, 1u);
         }
-        if (ok) tc_commit(bar_c2);
-        else {
+      }
+      tc_commit(bar_c1);
+      return true;
+    };
+    // Acc_b += X_q^T W for each 128-band tile b: A is the X tile read MN-major,
+    // two consecutive 64-band chunks from chunk cb (the last band tile starts
+    // one chunk early when the chunk count is odd: its first 64 rows repeat
+    // bands of the tile before and are not written out); K = 16 pixels per MMA
+    // (2048 bytes of X, 32 bytes of a W row)
+    auto issue_c2 = [&](int q, bool first) -> bool {
+      if (!do_c1 && !mbar_wait(full + xbuf(q), xpar(q), tmo)) return false;
+      tc_fence_after();
+      unsigned char* xb = ring + xbuf(q) * xtb;
+      for (int b = 0; b < nbt; ++b) {
+        const int cb = min(2 * b, nkx - 2);
+        const uint32_t dcol = tbase + (uint32_t)(Rgp * (1 + b));
+        const uint64_t da0 = desc_sw128_mn(su32(xb + cb * kTcStageBytes), kTcStageBytes);
+        for (int pc = 0; pc < NPC; ++pc) {
+          const uint64_t db0 = desc_sw128(su32(Wsm + pc * wchunk));
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            tc_mma<BF>(dcol, da0 + (uint64_t)(pc * 512 + ks * 128), db0 + 2u * ks, id2,
+                       (first && pc == 0 && ks == 0) ? 0u : 1u);
+        }
+      }
+      tc_commit(bar_c2);
+      return true;
+    };
+    if (tid == 0 && ntl > 0) {
+      load_x(0);
+      if (need_slice) load_slice(0);
+      if (do_c1) {
+        bool ok = mbar_wait(bar_pn, 0, tmo);
+        tc_fence_after();
+        if (ok) ok = issue_c1(0);
+        if (!ok) {
           flags[0] = 1;
-          atomicOr(bt->status, 1 << 12);  // contraction-2 pipeline
+          atomicOr(bt->status, 1 << 9);  // contraction-1 pipeline
         }
       }
     }
-    if (__syncthreads_or(flags[0])) {
-      bail = 1;
-      break;
+    __syncthreads();
+    for (int q = 0; q < ntl; ++q) {
+      const int i0 = (pg + q * cd.Pg) * kTcTile;
+      const int ni = min(kTcTile, N - i0);
+      // contraction 2 of the previous tile (W and its X buffer are free), then
+      // contraction 1 of this tile
+      int to = flags[0] ? 1 : 0;
+      if (!to && c2_pending) to = mbar_wait(bar_c2, c2_phase, tmo) ? 0 : 2;
+      if (!to && do_c1) to = mbar_wait(bar_c1, c1_phase, tmo) ? 0 : 3;
+      if (to > 1) atomicOr(bt->status, 1 << (to == 2 ? 11 : 10));
+      if (__syncthreads_or(to)) {
+        bail = 1;
+        break;
+      }
+      if (c2_pending) {
+        c2_phase ^= 1;
+        c2_pending = false;
+      }
+      if (do_c1) c1_phase ^= 1;
+      tc_fence_after();
+      if (tid == 0 && NB == 2 && q + 1 < ntl) load_x(q + 1);
+      if (!epilogue(i0, ni)) {
+        bail = 1;
+        break;
+      }
+      // W and the A state from generic-proxy stores -> async proxy
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const bool more = q + 1 < ntl;
+        if (IS_A) {  // the new state tile back to global memory
+          tma2d_store(tmState, i0, c0, Sst);
+          bulk_commit();
+          st_stored = true;
+        } else if (more) {
+          load_slice(q + 1);  // the uniforms have been read
+        }
+        bool ok = issue_c2(q, !d2_started);
+        if (!ok) atomicOr(bt->status, 1 << 12);  // contraction-2 X tile
+        if (ok && more) {
+          if (IS_A) {
+            bulk_wait_read();  // the store has read the state buffer
+            if (need_slice) load_slice(q + 1);
+          }
+          if (NB == 1) {  // one buffer: contraction 2 must have read it
+            ok = mbar_wait(bar_c2, c2_phase, tmo);
+            if (ok) load_x(q + 1);
+            else atomicOr(bt->status, 1 << 11);
+          }
+          if (ok && do_c1) {
+            ok = issue_c1(q + 1);
+            if (!ok) atomicOr(bt->status, 1 << 9);
+          }
+        }
+        if (!ok) flags[0] = 1;
+      }
+      d2_started = true;
+      c2_pending = true;
+      if (__syncthreads_or(flags[0])) {
+        bail = 1;
+        break;
+      }
     }
-    d2_started = true;
-    c2_pending = true;
+  } else {
+    for (int q = 0; q < ntl; ++q) {
+      const int i0 = (pg + q * cd.Pg) * kTcTile;
+      const int ni = min(kTcTile, N - i0);
+      // the previous tile's state store must have read the buffer before it is
+      // rewritten; then the tile's table slice (A: the state, B: the uniforms)
+      // by one TMA load
+      if (IS_A && tid == 0 && st_stored) bulk_wait_read();
+      if ((IS_A ? !init : !SPLIT) && tid == 0 && !flags[0]) {
+        mbar_expect(bar_st, state_bytes);
+        tma2d(Sst, tmState, i0, c0, bar_st);
+      }
+      // ---- 1. C = X_tile Panel^T (skipped for the initial passes: c = 0)
+      if (do_c1) {
+        if (tid == 0 && !flags[0]) {
+          bool ok = true;
+          if (!panel_ready) {
+            ok = mbar_wait(bar_pn, 0, tmo);
+            panel_ready = true;
+            tc_fence_after();
+          }
+          for (int j = 0; j < nc1 && ok; ++j) {
+            const int kc = j >> SUBS, part = j & SUBS;
+            ok = consume([&](unsigned char* st) {
+              // descriptors of the chunk's first K step; each further 32-byte K
+              // step adds 2 to the start-address field (address / 16)
+              const uint64_t da0 = desc_sw128(su32(st));
+              const uint64_t dh0 = desc_sw128(su32(Psm + kc * pnl));  // the resident panel's K chunk kc
+              const uint64_t dl0 = desc_sw128(su32(Psm + (nkc + kc) * pnl));
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t da = da0 + 2u * ks;
+                tc_mma<BF>(tbase, da, dh0 + 2u * ks, id, (kc | ks | part) ? 1u : 0u);
+                if (TWO && part == 0)  // X * P lo (split: X hi * P lo)
+                  tc_mma<BF>(tbase, da, dl0 + 2u * ks, id, 1u);
+              }
+            });
+          }
+          if (ok) tc_commit(bar_c1);
+          else flags[0] = 1;
+        }
+        __syncthreads();
+        const int to = flags[0] ? 1 : (mbar_wait(bar_c1, c1_phase, tmo) ? 0 : 2);
+        if (to) atomicOr(bt->status, 1 << (8 + to));  // 9: contraction-1 pipeline, 10: its commit
+        if (__syncthreads_or(to)) {
+          bail = 1;
+          break;
+        }
+        c1_phase ^= 1;
+        tc_fence_after();
+        if (tid == 0) fill();  // contraction 1's stages are free: stream the next chunks during the epilogue
+      }
+      // the previous tile's contraction 2 must finish before W is rewritten or Acc rescaled
+      if (c2_pending) {
+        const int to = mbar_wait(bar_c2, c2_phase, tmo) ? 0 : 1;
+        if (to) atomicOr(bt->status, 1 << 11);  // contraction 2 of the previous tile
+        if (__syncthreads_or(to)) {
+          bail = 1;
+          break;
+        }
+        c2_phase ^= 1;
+        c2_pending = false;
+        tc_fence_after();
+        if (tid == 0) fill();  // the previous contraction 2's stages are free as well
+        if (SPLIT) {
+          fold_tile(!folded);
+          folded = true;
+        }
+      }
+      if (!epilogue(i0, ni)) {
+        bail = 1;
+        break;
+      }
+      // ---- 3. Acc += X_bands W^T (W and the A state from generic-proxy stores -> async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        if (IS_A) {  // the new state tile back to global memory
+          tma2d_store(tmState, i0, c0, Sst);
+          bulk_commit();
+          st_stored = true;
+        }
+        if (!flags[0]) {
+          const bool first = !d2_started;
+          bool ok = true;
+          for (int j = 0; j < nc2 && ok; ++j) {
+            const int kc = j >> SUBS, part = j & SUBS, bti = kc >> NPCS, pc = kc & (NPC - 1);
+            ok = consume([&](unsigned char* st) {
+              const uint32_t dcol = tbase + (uint32_t)(Rgp * (1 + bti));
+              const uint64_t da0 = desc_sw128(su32(st));
+              const uint64_t db0 = desc_sw128(su32(Wsm + pc * wchunk));
+              const uint64_t dl0 = desc_sw128(su32(Wsm + (NPC + pc) * wchunk));
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t da = da0 + 2u * ks;
+                tc_mma<BF>(dcol, da, db0 + 2u * ks, id,
+                           ((SPLIT || first) && pc == 0 && part == 0 && ks == 0) ? 0u : 1u);
+                if (SPLIT && part == 0)  // X hi * W lo
+                  tc_mma<BF>(dcol, da, dl0 + 2u * ks, id, 1u);
+              }
+            });
+          }
+          if (ok) tc_commit(bar_c2);
+          else {
+            flags[0] = 1;
+            atomicOr(bt->status, 1 << 12);  // contraction-2 pipeline
+          }
+        }
+      }
+      if (__syncthreads_or(flags[0])) {
+        bail = 1;
+        break;
+      }
+      d2_started = true;
+      c2_pending = true;
+    }
   }
 
   // ---- end of the pass: wait for the last Acc update, write the partials
@@ -712,11 +868,13 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   } else if (d2_started) {
     float* part = cd.part + (size_t)pg * (L + 1) * Mp;
     for (int b = 0; b < nbt; ++b) {
-      const int l = b * 128 + quarter * 32 + lane;
+      // TMEM lane 0 of band tile b holds band lb (BF16: the tile's first X chunk)
+      const int lb = MNX ? 64 * min(2 * b, tc_nkx(L) - 2) : 128 * b;
+      const int l = lb + quarter * 32 + lane;
       for (int r = half; r < nr; r += 2) {
         float v[8];
         tmem_ld8(tbase + tl + (uint32_t)(Rgp * (1 + (SPLIT ? nbt : 0) + b) + r * P), v);  // split: the running sums
-        if (l <= L) {
+        if (l >= 128 * b && l <= L) {
 #pragma unroll
           for (int j = 0; j < P; ++j) part[(size_t)(c0 + r * P + j) * (L + 1) + l] = v[j];  // lanes: consecutive bands
         }
