@@ -107,9 +107,9 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
   float* colScale = reinterpret_cast<float*>(colKey + cs);  // 2^(F - Fn), the pending rescale (B)
   float* colLam = colScale + cs;                           // Lambda, the logits' offset (B)
   int* colRef = reinterpret_cast<int*>(colLam + cs);       // reference exponent k (B)
-  float* colRefW = reinterpret_cast<float*>(colRef + cs);  // 2^(k - F), the reference weight (B)
-  float* colFn = colRefW + cs;                             // the frame after this tile (B)
-  float* colC = colFn + cs;                                // (kR16Scale / 2 - Lambda) log2 e - F (B)
+  float* colFn = reinterpret_cast<float*>(colRef + cs);    // the frame after this tile (B)
+  // (C, 2^(k - F)) per column (B): C = (kR16Scale / 2 - Lambda) log2 e - F and the reference weight
+  float2* colCW = reinterpret_cast<float2*>(colFn + cs);
   float* runEta = reinterpret_cast<float*>(misc + ML.eta);  // Rm (<= 128)
   float* Gs = reinterpret_cast<float*>(misc + ML.g);       // Rm x P x P (A)
   float* aaq = reinterpret_cast<float*>(misc + ML.aaq);    // 4 x Rm x PP (A)
@@ -146,12 +146,12 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
       colRef[c] = k;
       colF[c] = (float)k;
       colFn[c] = (float)k;
-      colRefW[c] = 1.f;
+      colCW[c].y = 1.f;
       if (c < nc) {
         if (!init) colLam[c] = (float)cd.lamd[c0 + c];
         if (pg == 0) cd.bref[c0 + c] = k;
       }
-      colC[c] = (0.5f * kR16Scale - colLam[c]) * kLog2e - (float)k;
+      colCW[c].x = (0.5f * kR16Scale - colLam[c]) * kLog2e - (float)k;
     }
   for (int r = tid; r < Rm; r += kThreads) runEta[r] = r < nr ? (IS_A ? cd.eta1[m0 + r] : cd.eta2[m0 + r]) : 0.f;
   if (IS_A) {
@@ -325,8 +325,7 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
     for (int c = tid; c < nc; c += kThreads) {
       colF[c] = colFn[c];
       colScale[c] = 1.f;
-      colRefW[c] = ldexpf(1.f, colRef[c] - (int)colF[c]);
-      colC[c] = (0.5f * kR16Scale - colLam[c]) * kLog2e - colF[c];
+      colCW[c] = make_float2((0.5f * kR16Scale - colLam[c]) * kLog2e - colF[c], ldexpf(1.f, colRef[c] - (int)colF[c]));
     }
     if (tid == 0) flags[1] = 0;
     __syncthreads();
@@ -519,38 +518,80 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
 #pragma unroll
             for (int b = 0; b < kRB; ++b)
               if (r0 + 2 * b < nr) tmem_ld8_issue(tbase + tl + (uint32_t)((r0 + 2 * b) * P), gr[b]);
+          }
+          // Every shared-memory input of the kRB x P elements is read before
+          // any of their W stores: a load cannot be moved across a store to
+          // shared memory, and loads interleaved with the stores would chain
+          // the elements' latencies one after another.
+          float qv[kRB][P], cv[kRB][P], rv[kRB][P];  // table value, column constant, reference weight
+          int kv[kRB][P];                             // split: reference exponent
+#pragma unroll
+          for (int b = 0; b < kRB; ++b) {
+            const int rc = r0 + 2 * b < nr ? r0 + 2 * b : r0;  // a missing run recomputes run r0, stores nothing
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              const int c = rc * P + j;
+              if (SPLIT) {
+                cv[b][j] = colLam[c];
+                rv[b][j] = colF[c];
+                kv[b][j] = colRef[c];
+              } else {
+                qv[b][j] = (float)R16[c * kTcTile + il];
+                const float2 t = colCW[c];
+                cv[b][j] = t.x;
+                rv[b][j] = t.y;
+              }
+            }
+          }
+          if (do_c1) {
 #pragma unroll
             for (int b = 0; b < kRB; ++b)
               if (r0 + 2 * b < nr) tmem_wait_ld8(gr[b]);
           }
+          float wv[kRB][P];
 #pragma unroll
           for (int b = 0; b < kRB; ++b) {
             const int r = r0 + 2 * b;
-            const bool live = r < nr;  // warp-uniform; a missing run recomputes run r0 and stores nothing
+            const bool live = r < nr;  // warp-uniform
             const bool act = valid && live;
             const int rc = live ? r : r0;
             float u24[P];  // split operands: the exact 24-bit draw
             if (SPLIT) initial_logits<P>(__ldg(cd.seeds + m0 + rc), (uint64_t)(i0 + il), u24);
 #pragma unroll
             for (int j = 0; j < P; ++j) {
-              const int c = rc * P + j;
               const float g = (do_c1 && live) ? __uint_as_float(gr[b][j]) : 0.f;
-              const float q = SPLIT ? 0.f : (float)R16[c * kTcTile + il];
-              const float u0 = SPLIT ? u24[j] : (q + 0.5f) * kR16Scale;
               float w = 0.f, e;
               if (SPLIT) {  // FP32, expm1 near the reference
-                const float u = act ? (u0 - colLam[c]) - g : -EDAA_INF;
-                e = ex2_approx(fmaf(u, kLog2e, -colF[c]));
-                if (act) w = shifted_weight(u, colF[c], colRef[c]);
+                const float u = act ? (u24[j] - cv[b][j]) - g : -EDAA_INF;
+                e = ex2_approx(fmaf(u, kLog2e, -rv[b][j]));
+                if (act) w = shifted_weight(u, rv[b][j], kv[b][j]);
               } else {
-                const float x2 = act ? fmaf(-g, kLog2e, fmaf(q, kQs, colC[c])) : -EDAA_INF;  // u log2 e - F
+                const float x2 = act ? fmaf(-g, kLog2e, fmaf(qv[b][j], kQs, cv[b][j])) : -EDAA_INF;  // u log2 e - F
                 e = ex2_approx(x2);  // 0 where inactive
-                if (act) w = e - colRefW[c];
+                if (act) w = e - rv[b][j];
               }
               wmax = fmaxf(wmax, e);
-              if (live) store_w(c, w);
-              if (exact && live) {
-                const float u = act ? (u0 - colLam[c]) - g : -EDAA_INF;
+              wv[b][j] = w;
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < kRB; ++b)
+            if (r0 + 2 * b < nr)
+#pragma unroll
+              for (int j = 0; j < P; ++j) store_w((r0 + 2 * b) * P + j, wv[b][j]);
+          if (exact) {  // the tile's exact column maxima of u (rare: frames about to overflow)
+#pragma unroll
+            for (int b = 0; b < kRB; ++b) {
+              const int r = r0 + 2 * b;
+              if (r >= nr) continue;
+              float u24[P];
+              if (SPLIT) initial_logits<P>(__ldg(cd.seeds + m0 + r), (uint64_t)(i0 + il), u24);
+#pragma unroll
+              for (int j = 0; j < P; ++j) {
+                const int c = r * P + j;
+                const float u0 = SPLIT ? u24[j] : (qv[b][j] + 0.5f) * kR16Scale;
+                const float g = do_c1 ? __uint_as_float(gr[b][j]) : 0.f;
+                const float u = valid ? (u0 - colLam[c]) - g : -EDAA_INF;
                 const int key = __reduce_max_sync(0xffffffffu, ord_key(u));
                 if (lane == 0) atomicMax(&colKey[c], key);
               }
