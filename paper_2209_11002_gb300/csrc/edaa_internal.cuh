@@ -209,7 +209,7 @@ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 // Shared memory of a merge work item (one run, one chunk of lchunk bands), in doubles.
 struct MergeSmem {
-  int saat, sw, ssx, sxa, sE, sraw, sprod, sscale, total;
+  int saat, sw, ssx, sxa, sE, sraw, sprod, sscale, sEf, sSd, sRd, total;
 };
 __host__ __device__ inline MergeSmem merge_smem(int lchunk, int p, int Pg) {
   MergeSmem s;
@@ -222,6 +222,9 @@ __host__ __device__ inline MergeSmem merge_smem(int lchunk, int p, int Pg) {
   s.sraw = o; o += (lchunk + 1) * p;  // B: scaled partial sums (last row: the ones band)
   s.sprod = o; o += lchunk * p;       // E R products
   s.sscale = o; o += Pg * p;          // B: per-CTA scale factors
+  s.sEf = o; o += (lchunk * p + 1) / 2;  // B: E of the chunk (floats)
+  s.sSd = o; o += lchunk * p;         // tensor-core cubes: S and R of the chunk, loaded up front
+  s.sRd = o; o += lchunk * p;
   s.total = o;
   return s;
 }

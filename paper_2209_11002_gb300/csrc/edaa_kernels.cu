@@ -110,6 +110,22 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
   lo += e;
 }
 
+// Asynchronous copies global -> shared of 8 or 4 bytes (both addresses
+// aligned to the size): a merge issues the loads of its inputs this way, so
+// that they are all in flight together and land while it forms the partial
+// sums; cp_async_wait<n>() waits until at most n committed groups are pending.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Where element e's Pg per-CTA partials live: v[g * stride], each scaled by
 // sc[g * sstride] when sc is given (exact powers of two <= 1).
 struct PartialRow {
@@ -119,20 +135,22 @@ struct PartialRow {
   int sstride;
 };
 
-// Sums of the per-CTA partials of ne elements.  A team of lanes (a power of
-// two, as many as the block allows) shares one element: lane `sub` takes
-// g = sub, sub + team, ..., sixteen float-float chains per lane with their
-// loads in flight together, then a fixed tree over the chains and a fixed
-// butterfly over the team.  The team size and every order depend only on ne
-// and Pg, so the launch mode does not change the result.  store(e, sum)
-// receives each element's total once.
+// Sums of the per-CTA partials of ne elements, in rounds of up to kThreads
+// elements.  In a round a team of lanes (a power of two, as many as the
+// block allows for the elements left) shares one element: lane `sub` takes
+// g = sub, sub + team, ..., 16 float-float chains per lane with their loads
+// in flight together, then a fixed tree over the chains and a fixed
+// butterfly over the team.  The rounds, team sizes and every order depend
+// only on ne and Pg, so the launch mode does not change the result.  Callers
+// number the elements so that consecutive lanes read consecutive addresses.
+// store(e, sum) receives each element's total once.
 template <bool SCALED, typename Row, typename Store>
 __device__ void team_sums(int ne, int Pg, Row row, Store store) {
   constexpr int W = 16;
-  int team = 32;
-  while (team > 1 && ne * team > kThreads) team >>= 1;
-  const int per = kThreads / team, sub = (int)threadIdx.x & (team - 1);
-  for (int e0 = 0; e0 < ne; e0 += per) {
+  for (int e0 = 0; e0 < ne;) {
+    int team = 32;
+    while (team > 1 && (ne - e0) * team > kThreads) team >>= 1;
+    const int per = kThreads / team, sub = (int)threadIdx.x & (team - 1);
     const int e = e0 + (int)threadIdx.x / team;
     float hi[W], lo[W];
 #pragma unroll
@@ -169,32 +187,44 @@ __device__ void team_sums(int ne, int Pg, Row row, Store store) {
       lo[0] += l2;
     }
     if (e < ne && sub == 0) store(e, (double)hi[0] + (double)lo[0]);
+    e0 += per;
   }
 }
 
 // A-merge of run m over band chunk lc: X A^T = sum of the partials + (1/p) sum_i x_i
 // (shifted accumulation), A A^T, and R = E A A^T - X A^T for the next B-pass.
-// Every load that does not depend on another is issued in the first step.
+// The loads of E, S and the band sums are in flight during the partial sums.
 __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
   const int tid = threadIdx.x;
   const int P = cd.p, L = cd.L, Mp = cd.Mp, Pg = cd.Pg, c0 = m * P;
   const MergeSmem ms = merge_smem(cd.lchunk, P, Pg);
   double* sd = reinterpret_cast<double*>(smem);
   double *saat = sd + ms.saat, *ssx = sd + ms.ssx, *sxa = sd + ms.sxa, *sE = sd + ms.sE, *sprod = sd + ms.sprod;
+  double* sSd = sd + ms.sSd;
   const int l0 = lc * cd.lchunk, nl = min(cd.lchunk, L - l0);
-  for (int e = tid; e < nl * P; e += kThreads) sE[e] = cd.Ed[(size_t)(l0 + e / P) * Mp + c0 + e % P];
-  for (int e = tid; e < nl; e += kThreads) ssx[e] = cd.sx[l0 + e];
+  for (int e = tid; e < nl * P; e += kThreads) {
+    const size_t o = (size_t)(l0 + e / P) * Mp + c0 + e % P;
+    cp_async8(sE + e, cd.Ed + o);
+    if (cd.tc) cp_async8(sSd + e, cd.Sd + o);
+  }
+  for (int e = tid; e < nl; e += kThreads) cp_async8(ssx + e, cd.sx + l0 + e);
+  cp_async_commit();
   team_sums<false>(
       P * P + nl * P, Pg,
       [&](int e) {
         if (e < P * P) return PartialRow{cd.paa + (size_t)m * P * P + e, (size_t)cd.M * P * P, nullptr, 0};
-        const int f = e - P * P, li = f / P, j = f - li * P;
+        const int f = e - P * P, j = f / nl, li = f - j * nl;  // bands fastest: coalesced
         return PartialRow{cd.part + (size_t)(c0 + j) * (L + 1) + l0 + li, (size_t)(L + 1) * Mp, nullptr, 0};
       },
       [&](int e, double v) {
-        if (e < P * P) saat[e] = v;
-        else sxa[e - P * P] = v;
+        if (e < P * P) {
+          saat[e] = v;
+        } else {
+          const int f = e - P * P, j = f / nl, li = f - j * nl;
+          sxa[li * P + j] = v;
+        }
       });
+  cp_async_wait<0>();
   __syncthreads();
   if (lc == 0)
     for (int e = tid; e < P * P; e += kThreads) cd.AAt[(size_t)m * P * P + e] = saat[e];
@@ -209,7 +239,7 @@ __device__ void merge_a_unit(const CubeDev& cd, int m, int lc, float* smem) {
     cd.Rf[o] = (float)r;
     if (cd.tc) {  // the next B-pass contracts X with S + eta2 R
       cd.Rd[o] = r;
-      store_panel_s(cd, c0 + j, l, cd.Sd[o] + cd.eta2d[m] * r);
+      store_panel_s(cd, c0 + j, l, sSd[e] + cd.eta2d[m] * r);
     }
     sprod[e] = sE[e] * r;
   }
@@ -237,12 +267,26 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool
   double *saat = sd + ms.saat, *sw = sd + ms.sw, *ssx = sd + ms.ssx, *sxa = sd + ms.sxa, *sE = sd + ms.sE;
   double *sraw = sd + ms.sraw, *sprod = sd + ms.sprod;
   float* sscale = reinterpret_cast<float*>(sd + ms.sscale);  // Pg x P
+  float* sEf = reinterpret_cast<float*>(sd + ms.sEf);        // E of the chunk in float (the Gram sums)
+  double *sSd = sd + ms.sSd, *sRd = sd + ms.sRd;
   const int l0 = lc * cd.lchunk, nl = min(cd.lchunk, L - l0);
-  // first load step: everything that does not depend on the partial sums
-  for (int e = tid; e < Pg * P; e += kThreads) sscale[e] = cd.pmax[(size_t)(e / P) * Mp + c0 + e % P];
-  for (int e = tid; e < nl * P; e += kThreads) sxa[e] = cd.XAt[(size_t)(l0 + e / P) * Mp + c0 + e % P];
-  for (int e = tid; e < nl; e += kThreads) ssx[e] = cd.sx[l0 + e];
-  for (int e = tid; e < P * P; e += kThreads) saat[e] = cd.AAt[(size_t)m * P * P + e];
+  // every load that does not depend on the partial sums, in flight together:
+  // first the per-CTA frames, then (landing during the sums) X A^T, S, R, the
+  // band sums and A A^T
+  for (int e = tid; e < Pg * P; e += kThreads) cp_async4(sscale + e, cd.pmax + (size_t)(e / P) * Mp + c0 + e % P);
+  cp_async_commit();
+  for (int e = tid; e < nl * P; e += kThreads) {
+    const size_t o = (size_t)(l0 + e / P) * Mp + c0 + e % P;
+    cp_async8(sxa + e, cd.XAt + o);
+    if (cd.tc) {
+      cp_async8(sSd + e, cd.Sd + o);
+      cp_async8(sRd + e, cd.Rd + o);
+    }
+  }
+  for (int e = tid; e < nl; e += kThreads) cp_async8(ssx + e, cd.sx + l0 + e);
+  for (int e = tid; e < P * P; e += kThreads) cp_async8(saat + e, cd.AAt + (size_t)m * P * P + e);
+  cp_async_commit();
+  cp_async_wait<1>();
   __syncthreads();
   if (warp < P) {  // the common frame of column j and the per-CTA scale factors
     const int j = warp;
@@ -260,11 +304,15 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool
   team_sums<true>(
       (nl + 1) * P, Pg,
       [&](int e) {
-        const int li = e / P, j = e - li * P;
+        const int j = e / (nl + 1), li = e - j * (nl + 1);  // bands fastest: coalesced
         const int l = li < nl ? l0 + li : L;
         return PartialRow{cd.part + (size_t)(c0 + j) * (L + 1) + l, (size_t)(L + 1) * Mp, sscale + j, P};
       },
-      [&](int e, double v) { sraw[e] = v; });
+      [&](int e, double v) {
+        const int j = e / (nl + 1), li = e - j * (nl + 1);
+        sraw[li * P + j] = v;
+      });
+  cp_async_wait<0>();
   __syncthreads();
   if (tid < P) {
     const int j = tid, c = c0 + j;
@@ -294,6 +342,7 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool
     cd.Ef[(size_t)l * Mp + c0 + j] = (float)s;
     if (cd.tc) store_panel(cd, cd.panelE, c0 + j, l, s);
     sE[e] = s;
+    sEf[e] = (float)s;
   }
   __syncthreads();
   // G = E^T E of run m over this chunk's bands, bands in order (the tensor-core
@@ -302,7 +351,7 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool
     for (int e = warp; e < P * P; e += kWarps) {
       const int j = e / P, k = e - j * P;
       float g = 0.f;
-      for (int li = lane; li < nl; li += 32) g = fmaf((float)sE[li * P + j], (float)sE[li * P + k], g);
+      for (int li = lane; li < nl; li += 32) g = fmaf(sEf[li * P + j], sEf[li * P + k], g);
       g = warp_sum(g);
       if (lane == 0) cd.gpart[((size_t)lc * cd.M + m) * P * P + e] = g;
     }
@@ -314,9 +363,9 @@ __device__ void merge_b_unit(const CubeDev& cd, int m, int lc, float* smem, bool
     const size_t o = (size_t)l * Mp + c0 + j;
     cd.Rf[o] = (float)r;
     if (cd.tc) {
-      double sv = cd.Sd[o];
+      double sv = sSd[e];
       if (commit) {  // the step just taken used R from the previous merge
-        sv += eta2 * cd.Rd[o];
+        sv += eta2 * sRd[e];
         cd.Sd[o] = sv;
       }
       cd.Rd[o] = r;
