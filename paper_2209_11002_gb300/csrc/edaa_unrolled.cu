@@ -22,8 +22,19 @@
 //            zbar = zeta - eta a o (G zeta).
 //   A-phase inputs: Ebar = E (Gbar + Gbar^T) + X Cbar^T;
 //            Xbar += E Cbar + Ebar B^T;  lbar += B o (X^T Ebar).
-// Every reduction over pixels is per-block partials in float32 followed by a
-// fixed-order FP64 merge: results are deterministic.
+// Every reduction over pixels is per-CTA partials in float32 followed by a
+// fixed-order float-float merge: results are deterministic.
+//
+// Each sweep (the forward, the backward) is one cooperative launch of a
+// persistent kernel: CTA g owns the contiguous pixels [N g / G, N (g+1) / G)
+// and every per-pixel quantity of them, so that only reductions over pixels
+// need the whole grid.  Those are the grid barriers: a contraction over
+// pixels (E = X B, R = X D, P = X zeta, X Cbar) writes per-CTA partials,
+// one barrier, a distributed merge (each CTA a few of the L x p entries),
+// a second barrier; a small reduction (W, log-sum-exp, column sums, Gbar)
+// is merged by every CTA for itself after one barrier.  That is 18 barriers
+// per outer iteration forward and 39 backward.  d(loss)/dX is accumulated
+// in place in each CTA's own rows (rank-p updates, no barrier).
 #include <math.h>
 #include <stdint.h>
 
@@ -33,6 +44,7 @@
 #include <vector>
 
 #include "../../include/edaa.h"
+#include "edaa_pass.cuh"
 
 namespace edaa {
 void set_last_error(const char* msg);
@@ -40,11 +52,12 @@ void set_last_error(const char* msg);
 
 namespace eu {
 
-constexpr int kT = 256;     // threads per block
-constexpr int kW = kT / 32;
+constexpr int kT = 256;      // threads per CTA
+constexpr int kW = kT / 32;  // warps per CTA
 constexpr int kMaxP = 8;
-constexpr int kLT = 10;     // L <= 320
-constexpr int kBlocks = 304;
+constexpr int kLT = 10;      // L <= 320: bands per lane in the X contractions
+constexpr int kLPMax = 320 * kMaxP;
+constexpr int kSmall = 80;   // per-CTA slots of a small reduction (>= p^2 + 1, >= 2p)
 
 __device__ __forceinline__ float wsum(float v) {
 #pragma unroll
@@ -59,22 +72,114 @@ __device__ __forceinline__ uint64_t sm64(uint64_t seed, uint64_t n) {
   return z ^ (z >> 31);
 }
 
-// ---- part[blk][l*P + j] = sum_{pixels i of blk} x_i[l] * w_i[j]  (warp per pixel)
+// Float-float accumulation (Knuth's TwoSum: s + e == hi + x exactly).  This
+// GPU's FP64 rate is a small fraction of its FP32 rate; two-float sums keep
+// about 44 bits at FP32 speed.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += e;
+}
+// butterfly over the warp in a fixed order (every lane ends with the total)
+__device__ __forceinline__ double ff_warp_total(float hi, float lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    ff_add(hi, lo, h2);
+    lo += l2;
+  }
+  return (double)hi + (double)lo;
+}
+
+// Everything a sweep touches.  Per-pixel arrays are pixel-major N x p.
+struct UArgs {
+  int L, N, P, T, K1, K2, LP;  // LP = L p
+  uint64_t seed;
+  const float* X;              // N x L
+  const float* eta;            // 2T: eta_A[t], then eta_B[t]
+  float *z, *l, *b, *a, *C, *g, *d, *lbar, *zbar, *Abar, *zeta, *Dbar, *bp, *tmp;
+  float *zck, *lck;            // (T + 1) x N x p: log A, log B at the start of every outer iteration
+  float *ls, *gs, *Rs;         // backward recompute: (K2 + 1) logits, K2 B-gradients (N x p), K2 R (L x p)
+  float* Xbar;                 // N x L
+  const float *dE, *dA;        // backward inputs: L x p, p x N
+  float *Eout, *Aout;          // forward outputs: E_hat (L x p), A_hat (p x N)
+  float* part;                 // G x LP per-CTA partials of an X contraction
+  float* part2;                // G x kSmall per-CTA partials of a small reduction
+  float* peta;                 // G x 2T per-CTA partials of d eta
+  float *E32, *R32, *P32;      // merged L x p (float)
+  double *Ed, *XCd;            // merged L x p (FP64)
+  double* deta;                // 2T
+  unsigned* bar;               // arrivals at the grid barriers of this launch (zeroed before it)
+  int* status;
+  long long timeout_ns;
+  int maxpx;                   // the most pixels a CTA owns
+  int res_state, res_x;        // the per-pixel arrays / the CTA's X rows live in shared memory
+};
+constexpr int kPixArrays = 14;  // z, l, b, a, C, g, d, lbar, zbar, Abar, zeta, Dbar, bp, tmp
+
+// shared memory of a CTA
+struct Sm {
+  float p0[kLPMax], p1[kLPMax], buf[kLPMax];  // L x p panels and the partial-sum buffer
+  float red[kW * kSmall];                     // per-warp partials of a small reduction
+  float W[64], G[64], Wb[64], Wacc[64], tmp[kSmall];
+  double Gb[64], lse[kMaxP], sd[kMaxP];
+};
+
+__device__ __forceinline__ void prange(int N, int& lo, int& hi) {
+  lo = (int)((long long)N * blockIdx.x / gridDim.x);
+  hi = (int)((long long)N * (blockIdx.x + 1) / gridDim.x);
+}
+// Grid barrier on a monotonic arrival counter: the k-th barrier of a launch
+// completes when the counter reaches k G.  Thread 0 of each CTA arrives
+// (release) and polls (acquire); a wait beyond timeout_ns, or another CTA's
+// time-out, sets the status bit and returns false.  `nb` counts this CTA's
+// barriers.
+__device__ __forceinline__ bool gbar_wait(const UArgs& a, unsigned& nb) {
+  __shared__ int s_ok;
+  __syncthreads();
+  ++nb;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned target = nb * gridDim.x;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.bar) : "memory");
+    const unsigned long long t0 = edaa::global_ns();
+    for (unsigned spin = 0;; ++spin) {
+      if ((int)(edaa::ld_acquire_u32(a.bar) - target) >= 0) break;
+      if ((spin & 255u) == 255u) {
+        if (edaa::ld_volatile_i32(a.status) & edaa::kStatTimeout) { ok = 0; break; }
+        if ((long long)(edaa::global_ns() - t0) > a.timeout_ns) {
+          atomicOr(a.status, edaa::kStatTimeout);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+#define gbar(a) gbar_wait(a, nbar)
+
+// ---- a.part[g] = sum over this CTA's pixels of x_i w_i^T (L x p; warp per
+// pixel, lanes over the bands; the warps' sums in a fixed order)
 template <int P>
-__global__ void __launch_bounds__(kT) k_xw(const float* __restrict__ X, int L, int N, const float* __restrict__ w,
-                                         float* __restrict__ part) {
-  extern __shared__ float sbuf[];  // L * P
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ void xw_part(const UArgs& a, const float* __restrict__ w, Sm& S) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, L = a.L;
+  int lo, hi;
+  prange(a.N, lo, hi);
   float acc[kLT][P];
 #pragma unroll
   for (int k = 0; k < kLT; ++k)
 #pragma unroll
     for (int j = 0; j < P; ++j) acc[k][j] = 0.f;
-  for (int i = blockIdx.x * kW + warp; i < N; i += gridDim.x * kW) {
+  for (int i = lo + warp; i < hi; i += kW) {
     float wv[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) wv[j] = w[(size_t)i * P + j];
-    const float* x = X + (size_t)i * L;
+    const float* x = a.X + (size_t)i * L;
 #pragma unroll
     for (int k = 0; k < kLT; ++k) {
       const int l = lane + 32 * k;
@@ -83,7 +188,6 @@ __global__ void __launch_bounds__(kT) k_xw(const float* __restrict__ X, int L, i
       for (int j = 0; j < P; ++j) acc[k][j] = fmaf(xv, wv[j], acc[k][j]);
     }
   }
-  // fixed-order reduction over the block's warps
   for (int r = 0; r < kW; ++r) {
     if (warp == r) {
 #pragma unroll
@@ -91,36 +195,98 @@ __global__ void __launch_bounds__(kT) k_xw(const float* __restrict__ X, int L, i
         const int l = lane + 32 * k;
         if (l < L) {
 #pragma unroll
-          for (int j = 0; j < P; ++j) sbuf[l * P + j] = (r == 0) ? acc[k][j] : sbuf[l * P + j] + acc[k][j];
+          for (int j = 0; j < P; ++j) S.buf[l * P + j] = (r == 0) ? acc[k][j] : S.buf[l * P + j] + acc[k][j];
         }
       }
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < L * P; e += kT) part[(size_t)blockIdx.x * L * P + e] = sbuf[e];
+  float* dst = a.part + (size_t)blockIdx.x * a.LP;
+  for (int e = threadIdx.x; e < a.LP; e += kT) dst[e] = S.buf[e];
 }
 
-// ---- out[i*P + j] = scale * sum_l x_i[l] panel[l*P + j]  (warp per pixel)
-template <int P>
-__global__ void __launch_bounds__(kT) k_xdot(const float* __restrict__ X, int L, int N,
-                                           const float* __restrict__ panel, float scale0,
-                                           const float* __restrict__ smul, float* __restrict__ out) {
-  // scale = scale0 times the step size at smul when given (read on the device, so that a
-  // captured graph serves every call)
-  const float scale = smul ? scale0 * *smul : scale0;
-  extern __shared__ float sp[];  // L * P
-  for (int e = threadIdx.x; e < L * P; e += kT) sp[e] = panel[e];
+// ---- after a barrier: entry e of the merged L x p contraction (sum of the
+// CTAs' partials in a fixed order, float-float), a few entries per CTA
+__device__ void merge_dist(const UArgs& a, double* outd, float* outf, float* outf2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
+  for (int e = blockIdx.x * kW + warp; e < a.LP; e += G * kW) {
+    float hi = 0.f, lo = 0.f;
+    for (int b = lane; b < G; b += 32) ff_add(hi, lo, a.part[(size_t)b * a.LP + e]);
+    const double s = ff_warp_total(hi, lo);
+    if (lane == 0) {
+      if (outd) outd[e] = s;
+      if (outf) outf[e] = (float)s;
+      if (outf2) outf2[e] = (float)s;
+    }
+  }
+}
+
+// ---- after a barrier: every CTA merges the CTAs' n small partials for itself
+__device__ void merge_small(const UArgs& a, int n, float* outf, double* outd) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
+  for (int e = warp; e < n; e += kW) {
+    float hi = 0.f, lo = 0.f;
+    for (int b = lane; b < G; b += 32) ff_add(hi, lo, a.part2[(size_t)b * kSmall + e]);
+    const double s = ff_warp_total(hi, lo);
+    if (lane == 0) {
+      if (outf) outf[e] = (float)s;
+      if (outd) outd[e] = s;
+    }
+  }
   __syncthreads();
+}
+
+// ---- NV per-thread values summed over the CTA (warps in a fixed order) into
+// a.part2[g][0..NV)
+template <int NV>
+__device__ void block_part(const UArgs& a, const float (&v)[NV], Sm& S) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = blockIdx.x * kW + warp; i < N; i += gridDim.x * kW) {
-    const float* x = X + (size_t)i * L;
+#pragma unroll
+  for (int e = 0; e < NV; ++e) {
+    const float s = wsum(v[e]);
+    if (lane == 0) S.red[warp * kSmall + e] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NV; e += kT) {
+    float s = 0.f;
+    for (int w = 0; w < kW; ++w) s += S.red[w * kSmall + e];
+    a.part2[(size_t)blockIdx.x * kSmall + e] = s;
+  }
+  __syncthreads();
+}
+// the same into S.tmp (this CTA's total only)
+template <int NV>
+__device__ void block_total(const float (&v)[NV], Sm& S) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int e = 0; e < NV; ++e) {
+    const float s = wsum(v[e]);
+    if (lane == 0) S.red[warp * kSmall + e] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NV; e += kT) {
+    float s = 0.f;
+    for (int w = 0; w < kW; ++w) s += S.red[w * kSmall + e];
+    S.tmp[e] = s;
+  }
+  __syncthreads();
+}
+
+// ---- out_i = scale x_i^T panel (warp per pixel, lanes over the bands)
+template <int P>
+__device__ void xdot(const UArgs& a, const float* panel, float scale, float* __restrict__ out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, L = a.L;
+  int lo, hi;
+  prange(a.N, lo, hi);
+  for (int i = lo + warp; i < hi; i += kW) {
+    const float* x = a.X + (size_t)i * L;
     float c[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) c[j] = 0.f;
     for (int l = lane; l < L; l += 32) {
       const float xv = x[l];
 #pragma unroll
-      for (int j = 0; j < P; ++j) c[j] = fmaf(xv, sp[l * P + j], c[j]);
+      for (int j = 0; j < P; ++j) c[j] = fmaf(xv, panel[l * P + j], c[j]);
     }
 #pragma unroll
     for (int j = 0; j < P; ++j) c[j] = wsum(c[j]);
@@ -132,398 +298,558 @@ __global__ void __launch_bounds__(kT) k_xdot(const float* __restrict__ X, int L,
       out[(size_t)i * P + lane] = scale * v;
     }
   }
+  __syncthreads();
 }
 
-// ---- Xbar_i[l] += s1 sum_j L1[l,j] R1[i,j] + s2 sum_j L2[l,j] R2[i,j]  (rank-p updates of dX)
+// ---- Xbar_i[l] += s1 sum_j L1[l,j] R1[i,j] + s2 sum_j L2[l,j] R2[i,j] over this CTA's pixels
 template <int P>
-__global__ void __launch_bounds__(kT) k_rank(float* __restrict__ Xbar, int L, int N, const float* __restrict__ L1,
-                                           const float* __restrict__ R1, float s1m, const float* __restrict__ L2,
-                                           const float* __restrict__ R2, float s2m, const float* __restrict__ smul) {
-  const float s1 = smul ? s1m * *smul : s1m, s2 = smul ? s2m * *smul : s2m;
-  extern __shared__ float sp[];  // 2 * L * P
-  float* l1 = sp;
-  float* l2 = sp + L * P;
-  for (int e = threadIdx.x; e < L * P; e += kT) {
-    l1[e] = L1[e];
-    l2[e] = L2 ? L2[e] : 0.f;
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = blockIdx.x * kW + warp; i < N; i += gridDim.x * kW) {
+__device__ void rank_update(const UArgs& a, const float* L1, const float* R1, float s1, const float* L2,
+                            const float* R2, float s2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, L = a.L;
+  int lo, hi;
+  prange(a.N, lo, hi);
+  for (int i = lo + warp; i < hi; i += kW) {
     float r1[P], r2[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
       r1[j] = s1 * R1[(size_t)i * P + j];
-      r2[j] = R2 ? s2 * R2[(size_t)i * P + j] : 0.f;
+      r2[j] = L2 ? s2 * R2[(size_t)i * P + j] : 0.f;
     }
-    float* xb = Xbar + (size_t)i * L;
+    float* xb = a.Xbar + (size_t)i * L;
     for (int l = lane; l < L; l += 32) {
       float v = xb[l];
 #pragma unroll
-      for (int j = 0; j < P; ++j) v = fmaf(l1[l * P + j], r1[j], fmaf(l2[l * P + j], r2[j], v));
+      for (int j = 0; j < P; ++j) {
+        v = fmaf(L1[l * P + j], r1[j], v);
+        if (L2) v = fmaf(L2[l * P + j], r2[j], v);
+      }
       xb[l] = v;
     }
   }
+  __syncthreads();
 }
 
-// ---- reductions of per-pixel p-vectors: mode 0: sum w1 w2^T (P x P);
-// mode 1: column sums of w1 (P); mode 2: per-column sum of w1 o w2 (P)
-__global__ void __launch_bounds__(kT) k_pred(const float* __restrict__ w1, const float* __restrict__ w2, int N, int P,
-                                           int mode, float* __restrict__ part) {
-  __shared__ float red[kT];
-  const int n_out = (mode == 0) ? P * P : P;
-  float acc[kMaxP * kMaxP];
-  for (int e = 0; e < n_out; ++e) acc[e] = 0.f;
-  for (int i = blockIdx.x * kT + threadIdx.x; i < N; i += gridDim.x * kT) {
-    const float* a = w1 + (size_t)i * P;
-    const float* b = w2 ? w2 + (size_t)i * P : nullptr;
-    if (mode == 0) {
-      for (int j = 0; j < P; ++j)
-        for (int k = 0; k < P; ++k) acc[j * P + k] = fmaf(a[j], b[k], acc[j * P + k]);
-    } else if (mode == 1) {
-      for (int j = 0; j < P; ++j) acc[j] += a[j];
-    } else {
-      for (int j = 0; j < P; ++j) acc[j] = fmaf(a[j], b[j], acc[j]);
-    }
-  }
-  for (int e = 0; e < n_out; ++e) {
-    red[threadIdx.x] = acc[e];
-    __syncthreads();
-    for (int s = kT / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) part[(size_t)blockIdx.x * n_out + e] = red[0];
-    __syncthreads();
-  }
-}
-
-// fixed-order merge of per-block partials (FP64), optional scale and float copy
-// Float-float accumulation (Knuth's TwoSum: s + e == hi + x exactly).  This
-// GPU's FP64 rate is a small fraction of its FP32 rate; two-float sums keep
-// about 44 bits at FP32 speed.
-__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
-  const float s = hi + x;
-  const float bp = s - hi;
-  const float e = (hi - (s - bp)) + (x - bp);
-  hi = s;
-  lo += e;
-}
-// butterfly over the warp in a fixed order (lane 0 ends with the total)
-__device__ __forceinline__ double ff_warp_total(float hi, float lo) {
+// ---- G = E^T E (float) from the FP64 E: warp per entry, lanes over the bands
+__device__ void gram(const UArgs& a, float* G) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, P = a.P, L = a.L;
+  for (int e = warp; e < P * P; e += kW) {
+    const int j = e / P, k = e % P;
+    double s = 0.0;
+    for (int l = lane; l < L; l += 32) s += a.Ed[l * P + j] * a.Ed[l * P + k];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-    ff_add(hi, lo, h2);
-    lo += l2;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) G[e] = (float)s;
   }
-  return (double)hi + (double)lo;
+  __syncthreads();
 }
 
-// out[e] = scale * sum_b part[b][e]: one warp per output, lanes over the
-// partials (fixed order, float-float)
-__global__ void k_merge(const float* __restrict__ part, int nb, int n, double scale, double* outd, float* outf) {
-  const int lane = threadIdx.x & 31;
-  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (e >= n) return;  // whole warps leave together
-  float hi = 0.f, lo = 0.f;
-  for (int b = lane; b < nb; b += 32) ff_add(hi, lo, part[(size_t)b * n + e]);
-  const double s = ff_warp_total(hi, lo) * scale;
-  if (lane == 0) {
-    if (outd) outd[e] = s;
-    if (outf) outf[e] = (float)s;
-  }
-}
-inline int merge_blocks(int n) { return (n + 7) / 8; }  // 8 warps (outputs) per 256-thread block
-
-// ---- column log-sum-exp over pixels (online per thread, fixed-order merges)
-__global__ void __launch_bounds__(kT) k_lse_part(const float* __restrict__ u, int N, int P, float* __restrict__ part) {
-  __shared__ float sm[kT], ss[kT];
+// ---- per-column log-sum-exp of the logits v over all pixels: this CTA's
+// (max, scaled sum) pairs into part2, then (after a barrier) every CTA merges
+template <int P>
+__device__ void lse_part(const UArgs& a, const float* __restrict__ v, Sm& S) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int lo, hi;
+  prange(a.N, lo, hi);
+  float m[P], s[P];
+#pragma unroll
   for (int j = 0; j < P; ++j) {
-    float m = -INFINITY, s = 0.f;
-    for (int i = blockIdx.x * kT + threadIdx.x; i < N; i += gridDim.x * kT) {
-      const float v = u[(size_t)i * P + j];
-      if (v > m) {
-        s = s * expf(m - v) + 1.f;
-        m = v;
+    m[j] = -INFINITY;
+    s[j] = 0.f;
+  }
+  for (int i = lo + (int)threadIdx.x; i < hi; i += kT) {
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const float x = v[(size_t)i * P + j];
+      if (x > m[j]) {
+        s[j] = s[j] * expf(m[j] - x) + 1.f;
+        m[j] = x;
       } else {
-        s += expf(v - m);
+        s[j] += expf(x - m[j]);
       }
     }
-    sm[threadIdx.x] = m;
-    ss[threadIdx.x] = s;
-    __syncthreads();
-    for (int h = kT / 2; h > 0; h >>= 1) {
-      if (threadIdx.x < h) {
-        const float m1 = sm[threadIdx.x], m2 = sm[threadIdx.x + h];
-        const float mm = fmaxf(m1, m2);
-        float s1 = ss[threadIdx.x], s2 = ss[threadIdx.x + h];
-        s1 = (m1 == -INFINITY) ? 0.f : s1 * expf(m1 - mm);
-        s2 = (m2 == -INFINITY) ? 0.f : s2 * expf(m2 - mm);
-        sm[threadIdx.x] = mm;
-        ss[threadIdx.x] = s1 + s2;
-      }
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      part[((size_t)blockIdx.x * P + j) * 2 + 0] = sm[0];
-      part[((size_t)blockIdx.x * P + j) * 2 + 1] = ss[0];
-    }
-    __syncthreads();
   }
-}
-
-__global__ void k_lse_merge(const float* __restrict__ part, int nb, int P, double* __restrict__ lse) {
-  // one warp per column: m = max of the block maxima, then sum_b s_b e^(m_b - m)
-  const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
-  if (j >= P) return;
-  float m = -INFINITY;
-  for (int b = lane; b < nb; b += 32) m = fmaxf(m, part[((size_t)b * P + j) * 2]);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  float hi = 0.f, lo = 0.f;
-  for (int b = lane; b < nb; b += 32) {
-    const float mb = part[((size_t)b * P + j) * 2];
-    if (mb != -INFINITY) ff_add(hi, lo, part[((size_t)b * P + j) * 2 + 1] * expf(mb - m));
+  for (int j = 0; j < P; ++j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {  // fixed butterfly
+      const float m2 = __shfl_xor_sync(0xffffffffu, m[j], o), s2 = __shfl_xor_sync(0xffffffffu, s[j], o);
+      const float mm = fmaxf(m[j], m2);
+      const float t1 = (m[j] == -INFINITY) ? 0.f : s[j] * expf(m[j] - mm);
+      const float t2 = (m2 == -INFINITY) ? 0.f : s2 * expf(m2 - mm);
+      m[j] = mm;
+      s[j] = t1 + t2;
+    }
+    if (lane == 0) {
+      S.red[warp * kSmall + 2 * j] = m[j];
+      S.red[warp * kSmall + 2 * j + 1] = s[j];
+    }
   }
-  const double sum = ff_warp_total(hi, lo);
-  if (lane == 0) lse[j] = (double)m + log(sum);
+  __syncthreads();
+  if (threadIdx.x < P) {
+    const int j = threadIdx.x;
+    float mm = -INFINITY, ss = 0.f;
+    for (int w = 0; w < kW; ++w) {
+      const float m2 = S.red[w * kSmall + 2 * j], s2 = S.red[w * kSmall + 2 * j + 1];
+      const float mn = fmaxf(mm, m2);
+      const float t1 = (mm == -INFINITY) ? 0.f : ss * expf(mm - mn);
+      const float t2 = (m2 == -INFINITY) ? 0.f : s2 * expf(m2 - mn);
+      mm = mn;
+      ss = t1 + t2;
+    }
+    a.part2[(size_t)blockIdx.x * kSmall + 2 * j] = mm;
+    a.part2[(size_t)blockIdx.x * kSmall + 2 * j + 1] = ss;
+  }
+  __syncthreads();
 }
-
-// l -= lse (per column); b = exp(l)
-__global__ void k_shift_exp(float* __restrict__ l, const double* __restrict__ lse, int N, int P, float* __restrict__ b) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * P) return;
-  const float v = (float)((double)l[e] - lse[e % P]);
-  l[e] = v;
-  if (b) b[e] = expf(v);
-}
-
-__global__ void k_exp(const float* __restrict__ z, int n, float* __restrict__ a) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n) a[e] = expf(z[e]);
-}
-
-__global__ void k_init_logits(uint64_t seed, int N, int P, float* __restrict__ l) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * P) return;
-  l[e] = 0.1f * ((float)(sm64(seed, (uint64_t)e + 1) >> 40) * (1.0f / 16777216.0f));
-}
-
-__global__ void k_fill(float* __restrict__ z, int n, float v) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n) z[e] = v;
-}
-
-// G = E^T E (P x P) from the FP64 E, one block
-__global__ void k_gram(const double* __restrict__ E, int L, int P, float* __restrict__ G) {
-  // one warp per entry (j, k) of G = E^T E, lanes over the bands
-  const int lane = threadIdx.x & 31, e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (e >= P * P) return;
-  const int j = e / P, k = e % P;
-  double s = 0.0;
-  for (int l = lane; l < L; l += 32) s += E[l * P + j] * E[l * P + k];
+__device__ void lse_merge(const UArgs& a, double* lse) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
+  if (warp < a.P) {
+    const int j = warp;
+    float m = -INFINITY;
+    for (int b = lane; b < G; b += 32) m = fmaxf(m, a.part2[(size_t)b * kSmall + 2 * j]);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) G[e] = (float)s;
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    float hi = 0.f, lo = 0.f;
+    for (int b = lane; b < G; b += 32) {
+      const float mb = a.part2[(size_t)b * kSmall + 2 * j];
+      if (mb != -INFINITY) ff_add(hi, lo, a.part2[(size_t)b * kSmall + 2 * j + 1] * expf(mb - m));
+    }
+    const double sum = ff_warp_total(hi, lo);
+    if (lane == 0) lse[j] = (double)m + log(sum);
+  }
+  __syncthreads();
 }
 
-// one pixel's A-phase: K1 mirror steps; keeps the iterates when `rec` is set
-__device__ __forceinline__ void a_steps(float* z, const float* c, const float* G, float eta, int K1, int P,
+// one pixel's A-phase: K1 mirror steps; keeps the iterates when `zs` is given
+template <int P>
+__device__ __forceinline__ void a_steps(float* z, const float* c, const float* G, float eta, int K1,
                                         float (*zs)[kMaxP]) {
   for (int k = 0; k < K1; ++k) {
     if (zs)
+#pragma unroll
       for (int j = 0; j < P; ++j) zs[k][j] = z[j];
-    float a[kMaxP], mx = -INFINITY;
-    for (int j = 0; j < P; ++j) a[j] = expf(z[j]);
+    float av[P], mx = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < P; ++j) av[j] = expf(z[j]);
+#pragma unroll
     for (int j = 0; j < P; ++j) {
       float g = -c[j];
-      for (int q = 0; q < P; ++q) g = fmaf(G[j * P + q], a[q], g);
+#pragma unroll
+      for (int q = 0; q < P; ++q) g = fmaf(G[j * P + q], av[q], g);
       z[j] = fmaf(-eta, g, z[j]);
       mx = fmaxf(mx, z[j]);
     }
     float se = 0.f;
+#pragma unroll
     for (int j = 0; j < P; ++j) se += expf(z[j] - mx);
     const float lz = mx + logf(se);
+#pragma unroll
     for (int j = 0; j < P; ++j) z[j] -= lz;
   }
   if (zs)
+#pragma unroll
     for (int j = 0; j < P; ++j) zs[K1][j] = z[j];
 }
 
-__global__ void k_a_fwd(const float* __restrict__ C, const float* __restrict__ Gg, const float* __restrict__ etap,
-                        int K1, int N, int P, const float* zin, float* zout) {  // zin may be zout (in place)
-  const float eta = *etap;
-  __shared__ float G[kMaxP * kMaxP];
-  if (threadIdx.x < P * P) G[threadIdx.x] = Gg[threadIdx.x];
+// l <- l - lse (per column), b = exp(l); optionally a copy of l
+template <int P>
+__device__ void shift_exp(const UArgs& a, const double* lse, float* copy) {
+  int lo, hi;
+  prange(a.N, lo, hi);
+  for (int e = lo * P + (int)threadIdx.x; e < hi * P; e += kT) {
+    const float v = (float)((double)a.l[e] - lse[e % P]);
+    a.l[e] = v;
+    a.b[e] = expf(v);
+    if (copy) copy[e] = v;
+  }
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  float z[kMaxP], c[kMaxP];
-  for (int j = 0; j < P; ++j) {
-    z[j] = zin[(size_t)i * P + j];
-    c[j] = C[(size_t)i * P + j];
+}
+// dst = src over this CTA's pixels (p values each); b = exp(src) when b is given
+template <int P>
+__device__ void copy_px(const UArgs& a, const float* __restrict__ src, float* __restrict__ dst, float* __restrict__ eb) {
+  int lo, hi;
+  prange(a.N, lo, hi);
+  for (int e = lo * P + (int)threadIdx.x; e < hi * P; e += kT) {
+    const float v = src[e];
+    if (dst) dst[e] = v;
+    if (eb) eb[e] = expf(v);
   }
-  a_steps(z, c, G, eta, K1, P, nullptr);
-  for (int j = 0; j < P; ++j) zout[(size_t)i * P + j] = z[j];
-}
-
-// d_i = W b_i - a_i
-__global__ void k_dev(const float* __restrict__ b, const float* __restrict__ a, const float* __restrict__ W, int N,
-                      int P, float* __restrict__ d) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  for (int j = 0; j < P; ++j) {
-    float s = -a[(size_t)i * P + j];
-    for (int k = 0; k < P; ++k) s = fmaf(W[j * P + k], b[(size_t)i * P + k], s);
-    d[(size_t)i * P + j] = s;
-  }
-}
-
-// l' = l - eta g (unnormalised)
-__global__ void k_axpy(const float* l, const float* __restrict__ g, const float* __restrict__ etap, int n,
-                       float* o) {  // l may be o (in place)
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n) o[e] = fmaf(-*etap, g[e], l[e]);
-}
-
-// zeta = lbar - bp o s
-__global__ void k_zeta(const float* __restrict__ lbar, const float* __restrict__ bp, const double* __restrict__ s,
-                       int N, int P, float* __restrict__ zeta) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * P) return;
-  zeta[e] = (float)((double)lbar[e] - (double)bp[e] * s[e % P]);
-}
-
-// B-step adjoint, per pixel: lbar = zeta + b o (Dbar W); Abar -= Dbar
-__global__ void k_bbwd(const float* __restrict__ zeta, const float* __restrict__ b, const float* __restrict__ Dbar,
-                       const float* __restrict__ W, int N, int P, float* __restrict__ lbar, float* __restrict__ Abar) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  for (int j = 0; j < P; ++j) {
-    float s = 0.f;
-    for (int k = 0; k < P; ++k) s = fmaf(Dbar[(size_t)i * P + k], W[k * P + j], s);
-    lbar[(size_t)i * P + j] = fmaf(b[(size_t)i * P + j], s, zeta[(size_t)i * P + j]);
-    Abar[(size_t)i * P + j] -= Dbar[(size_t)i * P + j];
-  }
-}
-
-// zbar += a o (Abar + (Wbar + Wbar^T) a)
-__global__ void k_zbar(const float* __restrict__ a, const float* __restrict__ Abar, const float* __restrict__ Wb,
-                       int N, int P, float* __restrict__ zbar) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  for (int j = 0; j < P; ++j) {
-    float s = Abar[(size_t)i * P + j];
-    for (int k = 0; k < P; ++k) s = fmaf(Wb[j * P + k] + Wb[k * P + j], a[(size_t)i * P + k], s);
-    zbar[(size_t)i * P + j] = fmaf(a[(size_t)i * P + j], s, zbar[(size_t)i * P + j]);
-  }
-}
-
-// A-phase adjoint per pixel: recompute the K1 iterates from z_t, then reverse.
-// Writes zbar (adjoint of z_t), Cbar; block partials of Gbar (P*P) and d eta (1).
-__global__ void __launch_bounds__(kT) k_a_bwd(const float* __restrict__ C, const float* __restrict__ Gg,
-                                            const float* __restrict__ etap, int K1, int N, int P,
-                                            const float* __restrict__ zt, float* __restrict__ zbar,
-                                            float* __restrict__ Cbar, float* __restrict__ part) {
-  const float eta = *etap;
-  __shared__ float G[kMaxP * kMaxP];
-  __shared__ float red[kT];
-  if (threadIdx.x < P * P) G[threadIdx.x] = Gg[threadIdx.x];
   __syncthreads();
-  float gacc[kMaxP * kMaxP + 1];
-  for (int e = 0; e <= P * P; ++e) gacc[e] = 0.f;
-  for (int i = blockIdx.x * kT + threadIdx.x; i < N; i += gridDim.x * kT) {
-    float z[kMaxP], c[kMaxP], zb[kMaxP], cb[kMaxP];
-    float zs[6][kMaxP];  // K1 <= 5 recorded iterates + the result
+}
+
+// ---- one outer iteration forward from (z, l normalised, b = exp l): the
+// A-phase, then K2 B-steps.  With `rec`, keeps the logits ls[k], B-gradients
+// gs[k] and R_k (Rs[k]) for the reverse sweep.  Ends with z = z_{t+1}, a =
+// exp z, W = A A^T in S.W.
+template <int P>
+__device__ bool fwd_outer(const UArgs& a, Sm& S, int t, bool rec, unsigned& nbar) {
+  const int tid = threadIdx.x, LP = a.LP;
+  int lo, hi;
+  prange(a.N, lo, hi);
+  // E = X B (FP64 and float), G = E^T E
+  xw_part<P>(a, a.b, S);
+  if (!gbar(a)) return false;
+  merge_dist(a, a.Ed, a.E32, nullptr);
+  if (!gbar(a)) return false;
+  for (int e = tid; e < LP; e += kT) S.p0[e] = a.E32[e];
+  gram(a, S.G);
+  // c = E^T x_i, the K1 A-steps, a = exp z, and this CTA's share of W = A A^T
+  xdot<P>(a, S.p0, 1.f, a.C);
+  const float etaA = a.eta[t];
+  float w[P * P];
+#pragma unroll
+  for (int e = 0; e < P * P; ++e) w[e] = 0.f;
+  for (int i = lo + tid; i < hi; i += kT) {
+    float z[kMaxP], c[kMaxP], av[P];
+#pragma unroll
     for (int j = 0; j < P; ++j) {
-      z[j] = zt[(size_t)i * P + j];
-      c[j] = C[(size_t)i * P + j];
-      zb[j] = zbar[(size_t)i * P + j];
-      cb[j] = 0.f;
+      z[j] = a.z[(size_t)i * P + j];
+      c[j] = a.C[(size_t)i * P + j];
     }
-    a_steps(z, c, G, eta, K1, P, zs);
-    for (int k = K1 - 1; k >= 0; --k) {
-      float ak[kMaxP], ap[kMaxP], zeta[kMaxP], sz = 0.f;
-      for (int j = 0; j < P; ++j) {
-        ak[j] = expf(zs[k][j]);
-        ap[j] = expf(zs[k + 1][j]);
-        sz += zb[j];
-      }
-      for (int j = 0; j < P; ++j) zeta[j] = fmaf(-ap[j], sz, zb[j]);
-      for (int j = 0; j < P; ++j) {
-        float g = -c[j], gz = 0.f;
-        for (int q = 0; q < P; ++q) {
-          g = fmaf(G[j * P + q], ak[q], g);
-          gz = fmaf(G[j * P + q], zeta[q], gz);
-        }
-        gacc[P * P] = fmaf(-zeta[j], g, gacc[P * P]);  // d eta
-        cb[j] = fmaf(eta, zeta[j], cb[j]);
-        for (int q = 0; q < P; ++q) gacc[j * P + q] = fmaf(-eta * zeta[j], ak[q], gacc[j * P + q]);
-        zb[j] = fmaf(-eta * ak[j], gz, zeta[j]);
-      }
-    }
+    a_steps<P>(z, c, S.G, etaA, a.K1, nullptr);
+#pragma unroll
     for (int j = 0; j < P; ++j) {
-      zbar[(size_t)i * P + j] = zb[j];
-      Cbar[(size_t)i * P + j] = cb[j];
+      a.z[(size_t)i * P + j] = z[j];
+      av[j] = expf(z[j]);
+      a.a[(size_t)i * P + j] = av[j];
     }
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+#pragma unroll
+      for (int k = 0; k < P; ++k) w[j * P + k] = fmaf(av[j], av[k], w[j * P + k]);
   }
-  for (int e = 0; e <= P * P; ++e) {
-    red[threadIdx.x] = gacc[e];
+  block_part<P * P>(a, w, S);
+  if (rec) copy_px<P>(a, a.l, a.ls, nullptr);
+  if (!gbar(a)) return false;
+  merge_small(a, P * P, S.W, nullptr);
+  const float etaB = a.eta[a.T + t];
+  for (int k = 0; k < a.K2; ++k) {
+    // d_i = W b_i - a_i; R = X D (FP64 and float; kept for the reverse sweep)
+    for (int i = lo + tid; i < hi; i += kT)
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        float s = -a.a[(size_t)i * P + j];
+#pragma unroll
+        for (int q = 0; q < P; ++q) s = fmaf(S.W[j * P + q], a.b[(size_t)i * P + q], s);
+        a.d[(size_t)i * P + j] = s;
+      }
     __syncthreads();
-    for (int s = kT / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    xw_part<P>(a, a.d, S);
+    if (!gbar(a)) return false;
+    merge_dist(a, nullptr, a.R32, rec ? a.Rs + (size_t)k * LP : nullptr);
+    if (!gbar(a)) return false;
+    for (int e = tid; e < LP; e += kT) S.p0[e] = a.R32[e];
+    __syncthreads();
+    // g_i = x_i^T R; l' = l - eta g, normalised per column
+    xdot<P>(a, S.p0, 1.f, a.g);
+    for (int e = lo * P + tid; e < hi * P; e += kT) {
+      const float gv = a.g[e];
+      a.l[e] = fmaf(-etaB, gv, a.l[e]);
+      if (rec) a.gs[(size_t)k * a.N * P + e] = gv;
+    }
+    __syncthreads();
+    lse_part<P>(a, a.l, S);
+    if (!gbar(a)) return false;
+    lse_merge(a, S.lse);
+    shift_exp<P>(a, S.lse, rec ? a.ls + (size_t)(k + 1) * a.N * P : nullptr);
+  }
+  return true;
+}
+
+// ---- the forward sweep: A^0, B^0, T outer iterations with their
+// checkpoints, then E_hat = X B_T and A_hat (p x N)
+// This CTA's view of the arrays: with residency, its per-pixel arrays and its
+// X rows live in shared memory (addressed with the global pixel index, like
+// the arrays in global memory).
+__device__ UArgs local_view(const UArgs& g, float* dyn) {
+  UArgs a = g;
+  int lo, hi;
+  prange(g.N, lo, hi);
+  const int P = g.P, L = g.L;
+  float* q = dyn;
+  if (g.res_x) {
+    const float* src = g.X + (size_t)lo * L;  // (rows of L floats: not 16-byte aligned in general)
+    for (int e = threadIdx.x; e < (hi - lo) * L; e += kT) q[e] = src[e];
+    a.X = q - (size_t)lo * L;
+    q += ((size_t)g.maxpx * L + 3) & ~(size_t)3;
+  }
+  if (g.res_state) {
+    float** arr[kPixArrays] = {&a.z, &a.l, &a.b, &a.a, &a.C, &a.g, &a.d, &a.lbar, &a.zbar, &a.Abar, &a.zeta, &a.Dbar,
+                               &a.bp, &a.tmp};
+    for (int k = 0; k < kPixArrays; ++k) {
+      *arr[k] = q - (size_t)lo * P;
+      q += (size_t)g.maxpx * P;
+    }
+  }
+  __syncthreads();
+  return a;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kT, 1) k_unrolled_fwd(UArgs ag) {
+  __shared__ Sm S;
+  extern __shared__ float dyn[];
+  const UArgs a = local_view(ag, dyn);
+  unsigned nbar = 0;
+  const int tid = threadIdx.x;
+  const size_t n = (size_t)a.N * P;
+  int lo, hi;
+  prange(a.N, lo, hi);
+  // A^0 = 1/p (eq. initA0); B^0 = softmax(0.1 u), u from SplitMix64 (eq. initB0)
+  for (int e = lo * P + tid; e < hi * P; e += kT) {
+    a.z[e] = -logf((float)P);
+    a.l[e] = 0.1f * ((float)(sm64(a.seed, (uint64_t)e + 1) >> 40) * (1.0f / 16777216.0f));
+  }
+  __syncthreads();
+  lse_part<P>(a, a.l, S);
+  if (!gbar(a)) return;
+  lse_merge(a, S.lse);
+  shift_exp<P>(a, S.lse, nullptr);
+  for (int t = 0; t < a.T; ++t) {
+    copy_px<P>(a, a.z, a.zck + (size_t)t * n, nullptr);
+    copy_px<P>(a, a.l, a.lck + (size_t)t * n, nullptr);
+    if (!fwd_outer<P>(a, S, t, false, nbar)) return;
+  }
+  copy_px<P>(a, a.z, a.zck + (size_t)a.T * n, nullptr);
+  copy_px<P>(a, a.l, a.lck + (size_t)a.T * n, nullptr);
+  xw_part<P>(a, a.b, S);
+  if (!gbar(a)) return;
+  merge_dist(a, a.Ed, a.E32, a.Eout);
+  for (int i = lo + tid; i < hi; i += kT)
+#pragma unroll
+    for (int j = 0; j < P; ++j) a.Aout[(size_t)j * a.N + i] = expf(a.z[(size_t)i * P + j]);
+}
+
+// ---- the reverse sweep: from d(loss)/dE_hat (dE) and d(loss)/dA_hat (dA),
+// d(loss)/dX (Xbar) and d(loss)/d eta (deta)
+template <int P>
+__global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
+  __shared__ Sm S;
+  extern __shared__ float dyn[];
+  const UArgs a = local_view(ag, dyn);
+  unsigned nbar = 0;
+  const int tid = threadIdx.x, L = a.L, LP = a.LP, T = a.T;
+  const size_t n = (size_t)a.N * P;
+  int lo, hi;
+  prange(a.N, lo, hi);
+  float* peta = a.peta + (size_t)blockIdx.x * 2 * T;  // this CTA's d eta partials
+  for (int e = tid; e < 2 * T; e += kT) peta[e] = 0.f;
+  for (size_t e = (size_t)lo * L + tid; e < (size_t)hi * L; e += kT) a.Xbar[e] = 0.f;
+  for (int e = lo * P + tid; e < hi * P; e += kT) {
+    a.zbar[e] = 0.f;
+    const int i = e / P, j = e - i * P;
+    a.Abar[e] = a.dA[(size_t)j * a.N + i];  // A_hat = exp(z_T): its adjoint starts at dA
+  }
+  // E_hat = X B_T: Xbar += dE B^T; lbar = B o (X^T dE)
+  copy_px<P>(a, a.lck + (size_t)T * n, a.l, a.b);
+  for (int e = tid; e < LP; e += kT) S.p0[e] = a.dE[e];
+  __syncthreads();
+  rank_update<P>(a, S.p0, a.b, 1.f, nullptr, nullptr, 0.f);
+  xdot<P>(a, S.p0, 1.f, a.tmp);
+  for (int e = lo * P + tid; e < hi * P; e += kT) a.lbar[e] = a.b[e] * a.tmp[e];
+  __syncthreads();
+  for (int t = T - 1; t >= 0; --t) {
+    // ---- recompute outer iteration t from its checkpoint
+    copy_px<P>(a, a.zck + (size_t)t * n, a.z, nullptr);
+    copy_px<P>(a, a.lck + (size_t)t * n, a.l, a.b);
+    if (!fwd_outer<P>(a, S, t, true, nbar)) return;
+    // now z = z_{t+1}, a = exp z_{t+1}, S.W = A A^T; ls[k], gs[k], Rs[k]
+    const float etaB = a.eta[T + t], etaA = a.eta[t];
+    for (int e = tid; e < P * P; e += kT) S.Wacc[e] = 0.f;
+    // ---- reverse the B-steps
+    for (int k = a.K2 - 1; k >= 0; --k) {
+      copy_px<P>(a, a.ls + (size_t)(k + 1) * n, nullptr, a.bp);
+      copy_px<P>(a, a.ls + (size_t)k * n, nullptr, a.b);
+      // s = column sums of lbar; zeta = lbar - B' diag(s)
+      {
+        float cs[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) cs[j] = 0.f;
+        for (int i = lo + tid; i < hi; i += kT)
+#pragma unroll
+          for (int j = 0; j < P; ++j) cs[j] += a.lbar[(size_t)i * P + j];
+        block_part<P>(a, cs, S);
+      }
+      if (!gbar(a)) return;
+      merge_small(a, P, nullptr, S.sd);
+      // zeta; d eta_B += -<zeta, g_k>
+      {
+        float de[1] = {0.f};
+        const float* gk = a.gs + (size_t)k * n;
+        for (int e = lo * P + tid; e < hi * P; e += kT) {
+          const float zt = (float)((double)a.lbar[e] - (double)a.bp[e] * S.sd[e % P]);
+          a.zeta[e] = zt;
+          de[0] = fmaf(-zt, gk[e], de[0]);
+        }
+        block_total<1>(de, S);
+        if (tid == 0) peta[T + t] += S.tmp[0];
+      }
+      // P = X zeta; Dbar = -eta X^T P
+      xw_part<P>(a, a.zeta, S);
+      if (!gbar(a)) return;
+      merge_dist(a, nullptr, a.P32, nullptr);
+      if (!gbar(a)) return;
+      for (int e = tid; e < LP; e += kT) {
+        S.p0[e] = a.P32[e];
+        S.p1[e] = a.Rs[(size_t)k * LP + e];
+      }
+      __syncthreads();
+      xdot<P>(a, S.p0, -etaB, a.Dbar);
+      // D = B W - A^T (per pixel); Xbar += -eta (R zeta^T + P D^T); Wbar += B^T Dbar;
+      // lbar = zeta + B o (Dbar W); Abar -= Dbar
+      float wb[P * P];
+#pragma unroll
+      for (int e = 0; e < P * P; ++e) wb[e] = 0.f;
+      for (int i = lo + tid; i < hi; i += kT) {
+        float bv[P], av[P], db[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          bv[j] = a.b[(size_t)i * P + j];
+          av[j] = a.a[(size_t)i * P + j];
+          db[j] = a.Dbar[(size_t)i * P + j];
+        }
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          float s = -av[j], sw = 0.f;
+#pragma unroll
+          for (int q = 0; q < P; ++q) {
+            s = fmaf(S.W[j * P + q], bv[q], s);
+            sw = fmaf(db[q], S.W[q * P + j], sw);
+            wb[j * P + q] = fmaf(bv[j], db[q], wb[j * P + q]);
+          }
+          a.d[(size_t)i * P + j] = s;
+          a.lbar[(size_t)i * P + j] = fmaf(bv[j], sw, a.zeta[(size_t)i * P + j]);
+          a.Abar[(size_t)i * P + j] -= db[j];
+        }
+      }
+      __syncthreads();
+      rank_update<P>(a, S.p1, a.zeta, -etaB, S.p0, a.d, -etaB);
+      block_total<P * P>(wb, S);
+      for (int e = tid; e < P * P; e += kT) S.Wacc[e] += S.tmp[e];
       __syncthreads();
     }
-    if (threadIdx.x == 0) part[(size_t)blockIdx.x * (P * P + 1) + e] = red[0];
+    // ---- Wbar over all pixels; zbar(z_{t+1}) += a o (Abar + (Wbar + Wbar^T) a); Abar = 0
+    for (int e = tid; e < P * P; e += kT) a.part2[(size_t)blockIdx.x * kSmall + e] = S.Wacc[e];
     __syncthreads();
+    if (!gbar(a)) return;
+    merge_small(a, P * P, S.Wb, nullptr);
+    for (int i = lo + tid; i < hi; i += kT) {
+      float av[P];
+#pragma unroll
+      for (int j = 0; j < P; ++j) av[j] = a.a[(size_t)i * P + j];
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        float s = a.Abar[(size_t)i * P + j];
+#pragma unroll
+        for (int q = 0; q < P; ++q) s = fmaf(S.Wb[j * P + q] + S.Wb[q * P + j], av[q], s);
+        a.zbar[(size_t)i * P + j] = fmaf(av[j], s, a.zbar[(size_t)i * P + j]);
+        a.Abar[(size_t)i * P + j] = 0.f;
+      }
+    }
+    __syncthreads();
+    // ---- reverse the A-steps from z_t with E_t = X B_t, its Gram, and c = E_t^T x
+    copy_px<P>(a, a.lck + (size_t)t * n, a.l, a.b);
+    xw_part<P>(a, a.b, S);
+    if (!gbar(a)) return;
+    merge_dist(a, a.Ed, a.E32, nullptr);
+    if (!gbar(a)) return;
+    for (int e = tid; e < LP; e += kT) S.p0[e] = a.E32[e];
+    gram(a, S.G);
+    xdot<P>(a, S.p0, 1.f, a.C);
+    {
+      float gacc[P * P + 1];
+#pragma unroll
+      for (int e = 0; e <= P * P; ++e) gacc[e] = 0.f;
+      for (int i = lo + tid; i < hi; i += kT) {
+        float z[kMaxP], c[kMaxP], zb[P], cb[P];
+        float zs[6][kMaxP];  // K1 <= 5 recorded iterates + the result
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          z[j] = a.zck[(size_t)t * n + (size_t)i * P + j];
+          c[j] = a.C[(size_t)i * P + j];
+          zb[j] = a.zbar[(size_t)i * P + j];
+          cb[j] = 0.f;
+        }
+        a_steps<P>(z, c, S.G, etaA, a.K1, zs);
+        for (int k = a.K1 - 1; k >= 0; --k) {
+          float ak[P], ap[P], zeta[P], sz = 0.f;
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            ak[j] = expf(zs[k][j]);
+            ap[j] = expf(zs[k + 1][j]);
+            sz += zb[j];
+          }
+#pragma unroll
+          for (int j = 0; j < P; ++j) zeta[j] = fmaf(-ap[j], sz, zb[j]);
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            float g = -c[j], gz = 0.f;
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+              g = fmaf(S.G[j * P + q], ak[q], g);
+              gz = fmaf(S.G[j * P + q], zeta[q], gz);
+            }
+            gacc[P * P] = fmaf(-zeta[j], g, gacc[P * P]);  // d eta_A
+            cb[j] = fmaf(etaA, zeta[j], cb[j]);
+#pragma unroll
+            for (int q = 0; q < P; ++q) gacc[j * P + q] = fmaf(-etaA * zeta[j], ak[q], gacc[j * P + q]);
+            zb[j] = fmaf(-etaA * ak[j], gz, zeta[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          a.zbar[(size_t)i * P + j] = zb[j];
+          a.tmp[(size_t)i * P + j] = cb[j];  // Cbar
+        }
+      }
+      block_part<P * P + 1>(a, gacc, S);
+      if (tid == 0) peta[t] += a.part2[(size_t)blockIdx.x * kSmall + P * P];
+    }
+    if (!gbar(a)) return;
+    merge_small(a, P * P, nullptr, S.Gb);
+    // Ebar = E (Gbar + Gbar^T) + X Cbar^T ; Xbar += E Cbar + Ebar B^T ; lbar += B o (X^T Ebar)
+    xw_part<P>(a, a.tmp, S);
+    if (!gbar(a)) return;
+    merge_dist(a, a.XCd, nullptr, nullptr);
+    if (!gbar(a)) return;
+    for (int e = tid; e < LP; e += kT) {
+      const int l = e / P, j = e - l * P;
+      double s = a.XCd[e];
+#pragma unroll
+      for (int k = 0; k < P; ++k) s += a.Ed[l * P + k] * (S.Gb[k * P + j] + S.Gb[j * P + k]);
+      S.p1[e] = (float)s;
+    }
+    __syncthreads();
+    rank_update<P>(a, S.p0, a.tmp, 1.f, S.p1, a.b, 1.f);
+    xdot<P>(a, S.p1, 1.f, a.d);
+    for (int e = lo * P + tid; e < hi * P; e += kT) a.lbar[e] = fmaf(a.b[e], a.d[e], a.lbar[e]);
+    __syncthreads();
+  }
+  // d eta: the CTAs' partials in a fixed order
+  if (!gbar(a)) return;
+  if (blockIdx.x == 0) {
+    const int lane = tid & 31, warp = tid >> 5, G = gridDim.x;
+    for (int e = warp; e < 2 * T; e += kW) {
+      float hi2 = 0.f, lo2 = 0.f;
+      for (int b = lane; b < G; b += 32) ff_add(hi2, lo2, a.peta[(size_t)b * 2 * T + e]);
+      const double s = ff_warp_total(hi2, lo2);
+      if (lane == 0) a.deta[e] = s;
+    }
   }
 }
 
-// Ebar = E (Gbar + Gbar^T) + XCbar^T  (L x P, FP64 inputs)
-__global__ void k_ebar(const double* __restrict__ E, const double* __restrict__ Gb, const double* __restrict__ XC, int L,
-                       int P, float* __restrict__ Ebar) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= L * P) return;
-  const int l = e / P, j = e % P;
-  double s = XC[e];
-  for (int k = 0; k < P; ++k) s += E[l * P + k] * (Gb[k * P + j] + Gb[j * P + k]);
-  Ebar[e] = (float)s;
-}
-
-// lbar += b o v (v = X^T Ebar per pixel)
-__global__ void k_fma_inplace(float* __restrict__ lbar, const float* __restrict__ b, const float* __restrict__ v, int n) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < n) lbar[e] = fmaf(b[e], v[e], lbar[e]);
-}
-
-// dst[0] += sign * sum(src[0..n)); dst and src FP64, one thread
-__global__ void k_acc_sum(double* __restrict__ dst, const double* __restrict__ src, int n, double sign) {
-  double v = 0.0;
-  for (int e = 0; e < n; ++e) v += src[e];
-  dst[0] += sign * v;
-}
-// dst += src (n doubles); also writes a float copy
-__global__ void k_add_d(double* __restrict__ dst, const double* __restrict__ src, int n, float* __restrict__ f) {
-  const int e = threadIdx.x;
-  if (e >= n) return;
-  dst[e] += src[e];
-  if (f) f[e] = (float)dst[e];
-}
-
-__global__ void k_transpose_pn(const float* __restrict__ src, int N, int P, float* __restrict__ dst) {
-  // src N x P (pixel-major) -> dst P x N
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * P) return;
-  const int i = e / P, j = e % P;
-  dst[(size_t)j * N + i] = src[e];
-}
-__global__ void k_transpose_np(const float* __restrict__ src, int N, int P, float* __restrict__ dst) {
-  // src P x N -> dst N x P
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * P) return;
-  const int i = e / P, j = e % P;
-  dst[e] = src[(size_t)j * N + i];
+template <class F>
+cudaError_t by_p(int P, F&& f) {
+  switch (P) {
+    case 1: return f(std::integral_constant<int, 1>());
+    case 2: return f(std::integral_constant<int, 2>());
+    case 3: return f(std::integral_constant<int, 3>());
+    case 4: return f(std::integral_constant<int, 4>());
+    case 5: return f(std::integral_constant<int, 5>());
+    case 6: return f(std::integral_constant<int, 6>());
+    case 7: return f(std::integral_constant<int, 7>());
+    default: return f(std::integral_constant<int, 8>());
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -548,254 +874,66 @@ struct Buf {
 }  // namespace eu
 
 struct edaa_unrolled {
-  int L, N, P, T, K1, K2;
+  int L, N, P, T, K1, K2, G = 0;
+  size_t dyn = 0;  // dynamic shared memory of the sweeps
   cudaStream_t caller = nullptr;  // the stream the caller orders our work on
-  cudaStream_t s = nullptr;       // our own stream (a captured graph needs one that is not the legacy default)
+  cudaStream_t s = nullptr;       // our own stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  cudaGraphExec_t g_fwd = nullptr, g_bwd = nullptr;
   eu::Buf buf;
-  float *X, *zck, *lck, *z, *l, *b, *a, *C, *g, *d, *part, *G, *W, *E32, *R32;
-  double *Ed, *Wd, *Rd, *lse, *scr;
-  float *ls, *gs;              // recompute storage: (K2+1) x N x P logits, K2 x N x P B-gradients
-  float *Rs;                   // K2 x L x P
-  double* deta;                // 2T: d eta_A, d eta_B
-  float* eta;                  // 2T on the device: eta_A[t], then eta_B[t]
-  float* dAin;                 // p x N: d(loss)/dA_hat for the backward (zeros when absent)
-  float *lbar, *zbar, *Abar, *Xbar, *zeta, *Dbar, *bp, *tmp, *P32, *Eb32, *Wb32, *Gb32;
-  double *sd, *XCd, *Gbd, *Pd, *Wbd, *eta_scr;
+  eu::UArgs a{};
+  float* eta_d = nullptr;
+  float *dE_d = nullptr, *dA_d = nullptr;
   bool have_forward = false;
 };
 
 namespace eu {
 
-inline int nb_pix(int N) { return std::min(kBlocks, (N + kW - 1) / kW); }
-inline int nb_thr(int N) { return std::min(kBlocks, (N + kT - 1) / kT); }
-inline int g1(int n) { return (n + 255) / 256; }
-
-template <class F>
-cudaError_t by_p(int P, F&& f) {
-  switch (P) {
-    case 1: return f(std::integral_constant<int, 1>());
-    case 2: return f(std::integral_constant<int, 2>());
-    case 3: return f(std::integral_constant<int, 3>());
-    case 4: return f(std::integral_constant<int, 4>());
-    case 5: return f(std::integral_constant<int, 5>());
-    case 6: return f(std::integral_constant<int, 6>());
-    case 7: return f(std::integral_constant<int, 7>());
-    default: return f(std::integral_constant<int, 8>());
-  }
+// one cooperative launch of the sweep kernel over every SM
+template <int P>
+cudaError_t launch_sweep(edaa_unrolled* u, bool forward) {
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)u->G);
+  lc.blockDim = dim3(kT);
+  lc.dynamicSmemBytes = u->dyn;
+  lc.stream = u->s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  cudaError_t e = cudaMemsetAsync(u->a.bar, 0, sizeof(unsigned), u->s);  // the barrier counter starts at 0
+  if (e != cudaSuccess) return e;
+  return forward ? cudaLaunchKernelEx(&lc, k_unrolled_fwd<P>, u->a) : cudaLaunchKernelEx(&lc, k_unrolled_bwd<P>, u->a);
 }
-
-// out (FP64 and float) = X^T-contraction sum_i x_i w_i^T, L x P
-cudaError_t xw(edaa_unrolled* u, const float* w, double* outd, float* outf, double scale = 1.0) {
-  const int nb = nb_pix(u->N);
-  cudaError_t e = by_p(u->P, [&](auto pc) {
+// the sweeps' dynamic shared memory (the per-pixel arrays, then also the X
+// rows, where they fit next to the static part)
+template <int P>
+cudaError_t set_dyn(size_t dyn) {
+  cudaError_t e = cudaFuncSetAttribute(k_unrolled_fwd<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_unrolled_bwd<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  return e;
+}
+cudaError_t sweep(edaa_unrolled* u, bool forward) {
+  return by_p(u->P, [&](auto pc) { return launch_sweep<decltype(pc)::value>(u, forward); });
+}
+// the largest grid a cooperative launch of the sweeps can take: every SM, one CTA each
+cudaError_t grid_size(int P, size_t dyn, int* G) {
+  int dev = 0, sms = 0, bps = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = by_p(P, [&](auto pc) {
     constexpr int PP = decltype(pc)::value;
-    k_xw<PP><<<nb, kT, u->L * PP * sizeof(float), u->s>>>(u->X, u->L, u->N, w, u->part);
-    return cudaGetLastError();
+    int b1 = 0, b2 = 0;
+    cudaError_t r = set_dyn<PP>(dyn);
+    if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_unrolled_fwd<PP>, kT, dyn);
+    if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_unrolled_bwd<PP>, kT, dyn);
+    bps = std::min(b1, b2);
+    return r;
   });
   if (e != cudaSuccess) return e;
-  k_merge<<<merge_blocks(u->L * u->P), 256, 0, u->s>>>(u->part, nb, u->L * u->P, scale, outd, outf);
-  return cudaGetLastError();
-}
-
-// out = scale * X panel, times the step size at smul when given
-cudaError_t xdot(edaa_unrolled* u, const float* panel, float scale, float* out, const float* smul = nullptr) {
-  const int nb = nb_pix(u->N);
-  return by_p(u->P, [&](auto pc) {
-    constexpr int PP = decltype(pc)::value;
-    k_xdot<PP><<<nb, kT, u->L * PP * sizeof(float), u->s>>>(u->X, u->L, u->N, panel, scale, smul, out);
-    return cudaGetLastError();
-  });
-}
-
-cudaError_t rank(edaa_unrolled* u, const float* L1, const float* R1, float s1, const float* L2, const float* R2,
-                 float s2, const float* smul = nullptr) {
-  const int nb = nb_pix(u->N);
-  return by_p(u->P, [&](auto pc) {
-    constexpr int PP = decltype(pc)::value;
-    k_rank<PP><<<nb, kT, 2 * u->L * PP * sizeof(float), u->s>>>(u->Xbar, u->L, u->N, L1, R1, s1, L2, R2, s2, smul);
-    return cudaGetLastError();
-  });
-}
-
-cudaError_t pred(edaa_unrolled* u, const float* w1, const float* w2, int mode, double* outd, float* outf,
-                 double scale = 1.0) {
-  const int nb = nb_thr(u->N);
-  const int n_out = mode == 0 ? u->P * u->P : u->P;
-  k_pred<<<nb, kT, 0, u->s>>>(w1, w2, u->N, u->P, mode, u->part);
-  k_merge<<<merge_blocks(n_out), 256, 0, u->s>>>(u->part, nb, n_out, scale, outd, outf);
-  return cudaGetLastError();
-}
-
-// l <- l - lse(l) per column; b = exp(l)
-cudaError_t normalise_logits(edaa_unrolled* u, float* l, float* b) {
-  const int nb = nb_thr(u->N);
-  k_lse_part<<<nb, kT, 0, u->s>>>(l, u->N, u->P, u->part);
-  k_lse_merge<<<1, 32 * u->P, 0, u->s>>>(u->part, nb, u->P, u->lse);
-  k_shift_exp<<<g1(u->N * u->P), 256, 0, u->s>>>(l, u->lse, u->N, u->P, b);
-  return cudaGetLastError();
-}
-
-// E (FP64 Ed, float E32) = X exp(l) (b must hold exp(l))
-cudaError_t make_E(edaa_unrolled* u, const float* b) { return xw(u, b, u->Ed, u->E32); }
-
-// W = A A^T (float W, FP64 Wd) from a = exp(z)
-cudaError_t make_W(edaa_unrolled* u, const float* a) { return pred(u, a, a, 0, u->Wd, u->W); }
-
-// R = X (B W - A^T), float R32 (FP64 Rd)
-cudaError_t make_R(edaa_unrolled* u, const float* b, const float* a) {
-  k_dev<<<g1(u->N), 256, 0, u->s>>>(b, a, u->W, u->N, u->P, u->d);
-  return xw(u, u->d, u->Rd, u->R32);
-}
-
-// one outer iteration forward from (z, l normalised, b = exp l): A-phase then K2 B-steps.
-// When rec is set, stores logits ls[k], B-gradients gs[k] and R_k.
-cudaError_t outer_forward(edaa_unrolled* u, int t, bool rec) {
-  cudaError_t e;
-  const int n = u->N * u->P;
-  if ((e = make_E(u, u->b)) != cudaSuccess) return e;
-  k_gram<<<(u->P * u->P + 7) / 8, 256, 0, u->s>>>(u->Ed, u->L, u->P, u->G);
-  if ((e = xdot(u, u->E32, 1.f, u->C)) != cudaSuccess) return e;
-  k_a_fwd<<<g1(u->N), 256, 0, u->s>>>(u->C, u->G, u->eta + t, u->K1, u->N, u->P, u->z, u->z);
-  k_exp<<<g1(n), 256, 0, u->s>>>(u->z, n, u->a);
-  if ((e = make_W(u, u->a)) != cudaSuccess) return e;
-  if (rec) cudaMemcpyAsync(u->ls, u->l, n * 4, cudaMemcpyDeviceToDevice, u->s);
-  for (int k = 0; k < u->K2; ++k) {
-    if ((e = make_R(u, u->b, u->a)) != cudaSuccess) return e;
-    if ((e = xdot(u, u->R32, 1.f, u->g)) != cudaSuccess) return e;
-    if (rec) {
-      cudaMemcpyAsync(u->Rs + (size_t)k * u->L * u->P, u->R32, u->L * u->P * 4, cudaMemcpyDeviceToDevice, u->s);
-      cudaMemcpyAsync(u->gs + (size_t)k * n, u->g, n * 4, cudaMemcpyDeviceToDevice, u->s);
-    }
-    k_axpy<<<g1(n), 256, 0, u->s>>>(u->l, u->g, u->eta + u->T + t, n, u->l);
-    if ((e = normalise_logits(u, u->l, u->b)) != cudaSuccess) return e;
-    if (rec) cudaMemcpyAsync(u->ls + (size_t)(k + 1) * n, u->l, n * 4, cudaMemcpyDeviceToDevice, u->s);
-  }
-  return cudaGetLastError();
-}
-
-// The T outer iterations with their checkpoints, then E_hat (E32) and A_hat
-// (tmp, p x N).  Every input lives in the engine's buffers, so the sequence
-// is captured once and replayed.
-cudaError_t forward_body(edaa_unrolled* u) {
-  const int N = u->N, P = u->P, n = N * P;
-  cudaError_t e;
-  for (int t = 0; t < u->T; ++t) {
-    cudaMemcpyAsync(u->zck + (size_t)t * n, u->z, n * 4, cudaMemcpyDeviceToDevice, u->s);
-    cudaMemcpyAsync(u->lck + (size_t)t * n, u->l, n * 4, cudaMemcpyDeviceToDevice, u->s);
-    if ((e = outer_forward(u, t, false)) != cudaSuccess) return e;
-  }
-  cudaMemcpyAsync(u->zck + (size_t)u->T * n, u->z, n * 4, cudaMemcpyDeviceToDevice, u->s);
-  cudaMemcpyAsync(u->lck + (size_t)u->T * n, u->l, n * 4, cudaMemcpyDeviceToDevice, u->s);
-  if ((e = make_E(u, u->b)) != cudaSuccess) return e;
-  k_exp<<<g1(n), 256, 0, u->s>>>(u->z, n, u->a);
-  k_transpose_pn<<<g1(n), 256, 0, u->s>>>(u->a, N, P, u->tmp);
-  return cudaGetLastError();
-}
-
-// The reverse sweep: from d(loss)/dE_hat (Eb32) and d(loss)/dA_hat (dAin),
-// accumulates Xbar (dX) and deta (d eta_A, d eta_B).
-cudaError_t backward_body(edaa_unrolled* u) {
-  const int N = u->N, P = u->P, L = u->L, n = N * P, lp = L * P;
-  cudaError_t e;
-  cudaMemsetAsync(u->Xbar, 0, (size_t)N * L * 4, u->s);
-  cudaMemsetAsync(u->zbar, 0, n * 4, u->s);
-  // final state: b_T, a_T
-  cudaMemcpyAsync(u->l, u->lck + (size_t)u->T * n, n * 4, cudaMemcpyDeviceToDevice, u->s);
-  k_exp<<<g1(n), 256, 0, u->s>>>(u->l, n, u->b);
-  // E_hat = X B_T: Xbar += dE B^T; lbar = B o (X^T dE)
-  if ((e = rank(u, u->Eb32, u->b, 1.f, nullptr, nullptr, 0.f)) != cudaSuccess) return e;
-  if ((e = xdot(u, u->Eb32, 1.f, u->tmp)) != cudaSuccess) return e;
-  cudaMemsetAsync(u->lbar, 0, n * 4, u->s);
-  k_fma_inplace<<<g1(n), 256, 0, u->s>>>(u->lbar, u->b, u->tmp, n);
-  // A_hat = exp(z_T): the A-adjoint accumulator (pixel-major) starts at dA (p x N)
-  k_transpose_np<<<g1(n), 256, 0, u->s>>>(u->dAin, N, P, u->Abar);
-  cudaMemsetAsync(u->deta, 0, 2 * u->T * sizeof(double), u->s);
-  for (int t = u->T - 1; t >= 0; --t) {
-    // ---- recompute outer iteration t from its checkpoint
-    cudaMemcpyAsync(u->z, u->zck + (size_t)t * n, n * 4, cudaMemcpyDeviceToDevice, u->s);
-    cudaMemcpyAsync(u->l, u->lck + (size_t)t * n, n * 4, cudaMemcpyDeviceToDevice, u->s);
-    k_exp<<<g1(n), 256, 0, u->s>>>(u->l, n, u->b);
-    if ((e = outer_forward(u, t, true)) != cudaSuccess) return e;
-    // after it: z = z_{t+1}, a = exp(z_{t+1}), W = A A^T; ls[k], gs[k], Rs[k]
-    const float* etaA = u->eta + t;
-    const float* etaB = u->eta + u->T + t;
-    cudaMemsetAsync(u->Wbd, 0, 64 * 8, u->s);
-    cudaMemsetAsync(u->Wb32, 0, 64 * 4, u->s);
-    // ---- reverse the B-steps
-    for (int k = u->K2 - 1; k >= 0; --k) {
-      const float* lk = u->ls + (size_t)k * n;
-      const float* lk1 = u->ls + (size_t)(k + 1) * n;
-      k_exp<<<g1(n), 256, 0, u->s>>>(lk1, n, u->bp);
-      k_exp<<<g1(n), 256, 0, u->s>>>(lk, n, u->b);
-      // s = column sums of lbar; zeta = lbar - B' diag(s)
-      if ((e = pred(u, u->lbar, nullptr, 1, u->sd, nullptr)) != cudaSuccess) return e;
-      k_zeta<<<g1(n), 256, 0, u->s>>>(u->lbar, u->bp, u->sd, N, P, u->zeta);
-      // d eta_B += -<zeta, g>
-      if ((e = pred(u, u->zeta, u->gs + (size_t)k * n, 2, u->eta_scr, nullptr)) != cudaSuccess) return e;
-      k_acc_sum<<<1, 1, 0, u->s>>>(u->deta + u->T + t, u->eta_scr, P, -1.0);
-      // P = X zeta; Dbar = -eta X^T P
-      if ((e = xw(u, u->zeta, u->Pd, u->P32)) != cudaSuccess) return e;
-      if ((e = xdot(u, u->P32, -1.f, u->Dbar, etaB)) != cudaSuccess) return e;
-      // D = B W - A^T (per pixel), Xbar += -eta (R zeta^T + P D^T)
-      k_dev<<<g1(N), 256, 0, u->s>>>(u->b, u->a, u->W, N, P, u->d);
-      if ((e = rank(u, u->Rs + (size_t)k * lp, u->zeta, -1.f, u->P32, u->d, -1.f, etaB)) != cudaSuccess) return e;
-      // Wbar += B^T Dbar
-      if ((e = pred(u, u->b, u->Dbar, 0, u->scr, nullptr)) != cudaSuccess) return e;
-      k_add_d<<<1, 64, 0, u->s>>>(u->Wbd, u->scr, P * P, u->Wb32);
-      // lbar = zeta + B o (Dbar W); Abar -= Dbar
-      k_bbwd<<<g1(N), 256, 0, u->s>>>(u->zeta, u->b, u->Dbar, u->W, N, P, u->lbar, u->Abar);
-    }
-    // ---- A-phase: zbar(z_{t+1}) += a o (Abar + (Wbar + Wbar^T) a)
-    k_zbar<<<g1(N), 256, 0, u->s>>>(u->a, u->Abar, u->Wb32, N, P, u->zbar);
-    cudaMemsetAsync(u->Abar, 0, n * 4, u->s);
-    // ---- reverse the A-steps from z_t with E_t = X B_t, its Gram, and c = E_t^T x
-    cudaMemcpyAsync(u->l, u->lck + (size_t)t * n, n * 4, cudaMemcpyDeviceToDevice, u->s);
-    k_exp<<<g1(n), 256, 0, u->s>>>(u->l, n, u->b);  // B_t
-    if ((e = make_E(u, u->b)) != cudaSuccess) return e;
-    k_gram<<<(u->P * u->P + 7) / 8, 256, 0, u->s>>>(u->Ed, L, P, u->G);
-    if ((e = xdot(u, u->E32, 1.f, u->C)) != cudaSuccess) return e;
-    {
-      const int nb = nb_thr(N);
-      k_a_bwd<<<nb, kT, 0, u->s>>>(u->C, u->G, etaA, u->K1, N, P, u->zck + (size_t)t * n, u->zbar, u->tmp, u->part);
-      k_merge<<<merge_blocks(P * P + 1), 256, 0, u->s>>>(u->part, nb, P * P + 1, 1.0, u->Gbd, nullptr);
-      k_acc_sum<<<1, 1, 0, u->s>>>(u->deta + t, u->Gbd + P * P, 1, 1.0);
-    }
-    // Ebar = E (Gbar + Gbar^T) + X Cbar^T ; Xbar += E Cbar + Ebar B^T ; lbar += B o (X^T Ebar)
-    if ((e = xw(u, u->tmp, u->XCd, nullptr)) != cudaSuccess) return e;
-    k_ebar<<<g1(lp), 256, 0, u->s>>>(u->Ed, u->Gbd, u->XCd, L, P, u->Eb32);
-    if ((e = rank(u, u->E32, u->tmp, 1.f, u->Eb32, u->b, 1.f)) != cudaSuccess) return e;
-    if ((e = xdot(u, u->Eb32, 1.f, u->d)) != cudaSuccess) return e;
-    k_fma_inplace<<<g1(n), 256, 0, u->s>>>(u->lbar, u->b, u->d, n);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  *G = bps >= 1 ? sms : 0;
   return cudaSuccess;
-}
-
-// Runs body on the engine's stream: captured into *g on the first call,
-// replayed afterwards.
-template <class F>
-cudaError_t run_captured(edaa_unrolled* u, cudaGraphExec_t* g, F&& body) {
-  if (!*g) {
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(u->s, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return e;
-    const cudaError_t eb = body();
-    e = cudaStreamEndCapture(u->s, &graph);
-    if (eb != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      return eb;
-    }
-    if (e != cudaSuccess) return e;
-    e = cudaGraphInstantiate(g, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-      *g = nullptr;
-      return e;
-    }
-  }
-  return cudaGraphLaunch(*g, u->s);
 }
 
 }  // namespace eu
@@ -832,29 +970,56 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
     edaa_unrolled_destroy(u);
     return ufail(EDAA_ERR_CUDA, "stream or event creation failed in edaa_unrolled_create");
   }
-  const size_t n = (size_t)N * p, lp = (size_t)L * p;
+  {
+    // one CTA per SM; the per-pixel arrays and then the X rows of a CTA go to
+    // shared memory where they fit beside the static part (227 KB per CTA)
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      edaa_unrolled_destroy(u);
+      return ufail(EDAA_ERR_CUDA, "edaa_unrolled_create: no device");
+    }
+    const size_t maxpx = (size_t)(N + sms - 1) / sms + 1;
+    const size_t room = 232448 - sizeof(Sm) - 1024;
+    const size_t st = maxpx * p * kPixArrays * 4, xs = ((maxpx * L + 3) & ~(size_t)3) * 4;
+    u->a.maxpx = (int)maxpx;
+    u->a.res_state = st <= room;
+    u->a.res_x = u->a.res_state && st + xs <= room;
+    u->dyn = (u->a.res_state ? st : 0) + (u->a.res_x ? xs : 0);
+    if (grid_size(p, u->dyn, &u->G) != cudaSuccess || u->G < 1) {
+      edaa_unrolled_destroy(u);
+      return ufail(EDAA_ERR_CUDA, "edaa_unrolled_create: the sweep kernels do not fit on an SM");
+    }
+  }
+  const size_t n = (size_t)N * p, lp = (size_t)L * p, G = (size_t)u->G;
   Buf& B = u->buf;
-  u->X = B.get<float>((size_t)N * L);
-  u->zck = B.get<float>((size_t)(T + 1) * n);
-  u->lck = B.get<float>((size_t)(T + 1) * n);
-  u->z = B.get<float>(n); u->l = B.get<float>(n); u->b = B.get<float>(n); u->a = B.get<float>(n);
-  u->C = B.get<float>(n); u->g = B.get<float>(n); u->d = B.get<float>(n);
-  u->part = B.get<float>((size_t)kBlocks * std::max<size_t>(lp, (size_t)2 * p * p + 2 * p + 1) + 64);
-  u->G = B.get<float>(64); u->W = B.get<float>(64); u->E32 = B.get<float>(lp); u->R32 = B.get<float>(lp);
-  u->Ed = B.get<double>(lp); u->Wd = B.get<double>(64); u->Rd = B.get<double>(lp); u->lse = B.get<double>(8);
-  u->scr = B.get<double>(lp);
-  u->ls = B.get<float>((size_t)(K2 + 1) * n); u->gs = B.get<float>((size_t)std::max(K2, 1) * n);
-  u->Rs = B.get<float>((size_t)std::max(K2, 1) * lp); u->deta = B.get<double>((size_t)2 * T);
-  u->eta = B.get<float>((size_t)2 * T); u->dAin = B.get<float>(n);
-  u->lbar = B.get<float>(n); u->zbar = B.get<float>(n); u->Abar = B.get<float>(n);
-  u->Xbar = B.get<float>((size_t)N * L); u->zeta = B.get<float>(n); u->Dbar = B.get<float>(n);
-  u->bp = B.get<float>(n); u->tmp = B.get<float>(n); u->P32 = B.get<float>(lp); u->Eb32 = B.get<float>(lp);
-  u->Wb32 = B.get<float>(64); u->Gb32 = B.get<float>(72);
-  u->sd = B.get<double>(8); u->XCd = B.get<double>(lp); u->Gbd = B.get<double>(72); u->Pd = B.get<double>(lp);
-  u->Wbd = B.get<double>(64); u->eta_scr = B.get<double>(8);
+  UArgs& a = u->a;
+  a.L = L; a.N = N; a.P = p; a.T = T; a.K1 = K1; a.K2 = K2; a.LP = (int)lp;  // (maxpx, res_* set above)
+  a.timeout_ns = 2000000000ll;
+  a.X = B.get<float>((size_t)N * L);
+  u->eta_d = B.get<float>((size_t)2 * T);
+  a.eta = u->eta_d;
+  a.z = B.get<float>(n); a.l = B.get<float>(n); a.b = B.get<float>(n); a.a = B.get<float>(n);
+  a.C = B.get<float>(n); a.g = B.get<float>(n); a.d = B.get<float>(n);
+  a.lbar = B.get<float>(n); a.zbar = B.get<float>(n); a.Abar = B.get<float>(n); a.zeta = B.get<float>(n);
+  a.Dbar = B.get<float>(n); a.bp = B.get<float>(n); a.tmp = B.get<float>(n);
+  a.zck = B.get<float>((T + 1) * n); a.lck = B.get<float>((T + 1) * n);
+  a.ls = B.get<float>((size_t)(K2 + 1) * n); a.gs = B.get<float>((size_t)std::max(K2, 1) * n);
+  a.Rs = B.get<float>((size_t)std::max(K2, 1) * lp);
+  a.Xbar = B.get<float>((size_t)N * L);
+  u->dE_d = B.get<float>(lp); u->dA_d = B.get<float>(n);
+  a.dE = u->dE_d; a.dA = u->dA_d;
+  a.Eout = B.get<float>(lp); a.Aout = B.get<float>(n);
+  a.part = B.get<float>(G * lp); a.part2 = B.get<float>(G * kSmall); a.peta = B.get<float>(G * 2 * T);
+  a.E32 = B.get<float>(lp); a.R32 = B.get<float>(lp); a.P32 = B.get<float>(lp);
+  a.Ed = B.get<double>(lp); a.XCd = B.get<double>(lp); a.deta = B.get<double>((size_t)2 * T);
+  a.bar = B.get<unsigned>(2); a.status = B.get<int>(1);
   if (B.err != cudaSuccess) {
     edaa_unrolled_destroy(u);
     return ufail(EDAA_ERR_OOM, "cudaMalloc failed in edaa_unrolled_create");
+  }
+  if (cudaMemset(a.bar, 0, 2 * sizeof(unsigned)) != cudaSuccess || cudaMemset(a.status, 0, sizeof(int)) != cudaSuccess) {
+    edaa_unrolled_destroy(u);
+    return ufail(EDAA_ERR_CUDA, "edaa_unrolled_create: memset failed");
   }
   *out = u;
   return EDAA_OK;
@@ -863,8 +1028,6 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
 void edaa_unrolled_destroy(edaa_unrolled* u) {
   if (!u) return;
   if (u->s) cudaStreamSynchronize(u->s);
-  if (u->g_fwd) cudaGraphExecDestroy(u->g_fwd);
-  if (u->g_bwd) cudaGraphExecDestroy(u->g_bwd);
   if (u->ev_in) cudaEventDestroy(u->ev_in);
   if (u->ev_out) cudaEventDestroy(u->ev_out);
   if (u->s) cudaStreamDestroy(u->s);
@@ -880,18 +1043,15 @@ edaa_status edaa_unrolled_forward(edaa_unrolled* u, const float* X, uint64_t see
     eta[t] = (float)eta_A[t];
     eta[u->T + t] = (float)eta_B[t];
   }
+  u->a.seed = seed;
   // our stream follows the caller's
   UCK(cudaEventRecord(u->ev_in, u->caller), "order after the caller's stream");
   UCK(cudaStreamWaitEvent(u->s, u->ev_in, 0), "order after the caller's stream");
-  UCK(cudaMemcpyAsync(u->eta, eta.data(), eta.size() * sizeof(float), cudaMemcpyHostToDevice, u->s), "copy eta");
-  UCK(cudaMemcpyAsync(u->X, X, (size_t)N * L * 4, cudaMemcpyDefault, u->s), "copy X");
-  // A^0 = 1/p (eq. initA0): z = -log p; B^0 = softmax(0.1 u) (eq. initB0)
-  k_fill<<<g1(n), 256, 0, u->s>>>(u->z, n, -logf((float)P));
-  k_init_logits<<<g1(n), 256, 0, u->s>>>(seed, N, P, u->l);
-  UCK(normalise_logits(u, u->l, u->b), "init logits");
-  UCK(run_captured(u, &u->g_fwd, [&] { return forward_body(u); }), "forward");
-  if (E_out) UCK(cudaMemcpyAsync(E_out, u->E32, (size_t)L * P * 4, cudaMemcpyDefault, u->s), "copy E");
-  if (A_out) UCK(cudaMemcpyAsync(A_out, u->tmp, (size_t)n * 4, cudaMemcpyDefault, u->s), "copy A");
+  UCK(cudaMemcpyAsync(u->eta_d, eta.data(), eta.size() * sizeof(float), cudaMemcpyHostToDevice, u->s), "copy eta");
+  UCK(cudaMemcpyAsync((void*)u->a.X, X, (size_t)N * L * 4, cudaMemcpyDefault, u->s), "copy X");
+  UCK(sweep(u, true), "forward sweep");
+  if (E_out) UCK(cudaMemcpyAsync(E_out, u->a.Eout, (size_t)L * P * 4, cudaMemcpyDefault, u->s), "copy E");
+  if (A_out) UCK(cudaMemcpyAsync(A_out, u->a.Aout, (size_t)n * 4, cudaMemcpyDefault, u->s), "copy A");
   UCK(cudaEventRecord(u->ev_out, u->s), "order the caller's stream after ours");
   UCK(cudaStreamWaitEvent(u->caller, u->ev_out, 0), "order the caller's stream after ours");
   UCK(cudaGetLastError(), "forward");
@@ -903,23 +1063,29 @@ edaa_status edaa_unrolled_backward(edaa_unrolled* u, const float* dE, const floa
                                    double* d_eta_B) {
   if (!u || !u->have_forward) return ufail(EDAA_ERR_STATE, "edaa_unrolled_backward needs a forward first");
   const int N = u->N, P = u->P, L = u->L, n = N * P, lp = L * P;
-  std::vector<double> deA(u->T, 0.0), deB(u->T, 0.0);
+  std::vector<double> deta(2 * u->T, 0.0);
+  int status = 0;
   UCK(cudaEventRecord(u->ev_in, u->caller), "order after the caller's stream");
   UCK(cudaStreamWaitEvent(u->s, u->ev_in, 0), "order after the caller's stream");
   // the adjoints of the outputs (zeros when absent) go into the engine's buffers
-  if (dE) UCK(cudaMemcpyAsync(u->Eb32, dE, (size_t)lp * 4, cudaMemcpyDefault, u->s), "copy dE");
-  else UCK(cudaMemsetAsync(u->Eb32, 0, (size_t)lp * 4, u->s), "zero");
-  if (dA) UCK(cudaMemcpyAsync(u->dAin, dA, (size_t)n * 4, cudaMemcpyDefault, u->s), "copy dA");
-  else UCK(cudaMemsetAsync(u->dAin, 0, (size_t)n * 4, u->s), "zero");
-  UCK(run_captured(u, &u->g_bwd, [&] { return backward_body(u); }), "backward");
-  if (dX) UCK(cudaMemcpyAsync(dX, u->Xbar, (size_t)N * L * 4, cudaMemcpyDefault, u->s), "copy dX");
-  UCK(cudaMemcpyAsync(deA.data(), u->deta, u->T * sizeof(double), cudaMemcpyDeviceToHost, u->s), "copy");
-  UCK(cudaMemcpyAsync(deB.data(), u->deta + u->T, u->T * sizeof(double), cudaMemcpyDeviceToHost, u->s), "copy");
+  if (dE) UCK(cudaMemcpyAsync(u->dE_d, dE, (size_t)lp * 4, cudaMemcpyDefault, u->s), "copy dE");
+  else UCK(cudaMemsetAsync(u->dE_d, 0, (size_t)lp * 4, u->s), "zero");
+  if (dA) UCK(cudaMemcpyAsync(u->dA_d, dA, (size_t)n * 4, cudaMemcpyDefault, u->s), "copy dA");
+  else UCK(cudaMemsetAsync(u->dA_d, 0, (size_t)n * 4, u->s), "zero");
+  UCK(sweep(u, false), "backward sweep");
+  if (dX) UCK(cudaMemcpyAsync(dX, u->a.Xbar, (size_t)N * L * 4, cudaMemcpyDefault, u->s), "copy dX");
+  UCK(cudaMemcpyAsync(deta.data(), u->a.deta, 2 * u->T * sizeof(double), cudaMemcpyDeviceToHost, u->s), "copy");
+  UCK(cudaMemcpyAsync(&status, u->a.status, sizeof(int), cudaMemcpyDeviceToHost, u->s), "copy status");
   UCK(cudaStreamSynchronize(u->s), "sync");
   UCK(cudaEventRecord(u->ev_out, u->s), "order the caller's stream after ours");
   UCK(cudaStreamWaitEvent(u->caller, u->ev_out, 0), "order the caller's stream after ours");
-  if (d_eta_A) for (int t = 0; t < u->T; ++t) d_eta_A[t] = deA[t];
-  if (d_eta_B) for (int t = 0; t < u->T; ++t) d_eta_B[t] = deB[t];
+  if (status & edaa::kStatTimeout) {
+    cudaMemsetAsync(u->a.status, 0, sizeof(int), u->s);
+    cudaMemsetAsync(u->a.bar, 0, 2 * sizeof(unsigned), u->s);
+    return ufail(EDAA_ERR_TIMEOUT, "a grid barrier of the unrolled sweeps timed out");
+  }
+  if (d_eta_A) for (int t = 0; t < u->T; ++t) d_eta_A[t] = deta[t];
+  if (d_eta_B) for (int t = 0; t < u->T; ++t) d_eta_B[t] = deta[u->T + t];
   return EDAA_OK;
 }
 
