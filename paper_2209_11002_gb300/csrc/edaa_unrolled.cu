@@ -121,7 +121,7 @@ constexpr int kPixArrays = 14;  // z, l, b, a, C, g, d, lbar, zbar, Abar, zeta, 
 
 // shared memory of a CTA
 struct Sm {
-  float p0[kLPMax], p1[kLPMax], buf[kLPMax];  // L x p panels and the partial-sum buffer
+  float p0[kLPMax], p1[kLPMax];  // L x p panels
   float red[kW * kSmall];                     // per-warp partials of a small reduction
   float W[64], G[64], Wb[64], Wacc[64], tmp[kSmall];
   double Gb[64], lse[kMaxP], sd[kMaxP];
@@ -163,46 +163,39 @@ __device__ __forceinline__ bool gbar_wait(const UArgs& a, unsigned& nb) {
 }
 #define gbar(a) gbar_wait(a, nbar)
 
-// ---- a.part[g] = sum over this CTA's pixels of x_i w_i^T (L x p; warp per
-// pixel, lanes over the bands; the warps' sums in a fixed order)
+// Dot product of n terms x[k sx] y[k sy] in blocks of 64: four interleaved
+// FMA chains of 16 terms, each block's sum added into a float-float total
+// (the error stays that of a 16-term chain however long the dot product).
+__device__ __forceinline__ float dot_blocked(const float* x, size_t sx, const float* y, size_t sy, int n) {
+  float hi = 0.f, lo = 0.f;
+  for (int k0 = 0; k0 < n; k0 += 64) {
+    const int k1 = min(n, k0 + 64);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int k = k0;
+    for (; k + 3 < k1; k += 4) {
+      s0 = fmaf(x[k * sx], y[k * sy], s0);
+      s1 = fmaf(x[(k + 1) * sx], y[(k + 1) * sy], s1);
+      s2 = fmaf(x[(k + 2) * sx], y[(k + 2) * sy], s2);
+      s3 = fmaf(x[(k + 3) * sx], y[(k + 3) * sy], s3);
+    }
+    for (; k < k1; ++k) s0 = fmaf(x[k * sx], y[k * sy], s0);
+    ff_add(hi, lo, (s0 + s1) + (s2 + s3));
+  }
+  return hi + lo;
+}
+
+// ---- a.part[g] = sum over this CTA's pixels of x_i w_i^T (L x p): a thread
+// per entry (l, j), pixels in order
 template <int P>
 __device__ void xw_part(const UArgs& a, const float* __restrict__ w, Sm& S) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, L = a.L;
+  const int L = a.L, LP = a.LP;
   int lo, hi;
   prange(a.N, lo, hi);
-  float acc[kLT][P];
-#pragma unroll
-  for (int k = 0; k < kLT; ++k)
-#pragma unroll
-    for (int j = 0; j < P; ++j) acc[k][j] = 0.f;
-  for (int i = lo + warp; i < hi; i += kW) {
-    float wv[P];
-#pragma unroll
-    for (int j = 0; j < P; ++j) wv[j] = w[(size_t)i * P + j];
-    const float* x = a.X + (size_t)i * L;
-#pragma unroll
-    for (int k = 0; k < kLT; ++k) {
-      const int l = lane + 32 * k;
-      const float xv = (l < L) ? x[l] : 0.f;
-#pragma unroll
-      for (int j = 0; j < P; ++j) acc[k][j] = fmaf(xv, wv[j], acc[k][j]);
-    }
+  float* dst = a.part + (size_t)blockIdx.x * LP;
+  for (int e = threadIdx.x; e < LP; e += kT) {
+    const int l = e / P, j = e - l * P;
+    dst[e] = dot_blocked(a.X + (size_t)lo * L + l, (size_t)L, w + (size_t)lo * P + j, (size_t)P, hi - lo);
   }
-  for (int r = 0; r < kW; ++r) {
-    if (warp == r) {
-#pragma unroll
-      for (int k = 0; k < kLT; ++k) {
-        const int l = lane + 32 * k;
-        if (l < L) {
-#pragma unroll
-          for (int j = 0; j < P; ++j) S.buf[l * P + j] = (r == 0) ? acc[k][j] : S.buf[l * P + j] + acc[k][j];
-        }
-      }
-    }
-    __syncthreads();
-  }
-  float* dst = a.part + (size_t)blockIdx.x * a.LP;
-  for (int e = threadIdx.x; e < a.LP; e += kT) dst[e] = S.buf[e];
 }
 
 // ---- after a barrier: entry e of the merged L x p contraction (sum of the
@@ -272,31 +265,15 @@ __device__ void block_total(const float (&v)[NV], Sm& S) {
   __syncthreads();
 }
 
-// ---- out_i = scale x_i^T panel (warp per pixel, lanes over the bands)
+// ---- out_i = scale x_i^T panel: a thread per (pixel, j), bands in order
 template <int P>
 __device__ void xdot(const UArgs& a, const float* panel, float scale, float* __restrict__ out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, L = a.L;
+  const int L = a.L;
   int lo, hi;
   prange(a.N, lo, hi);
-  for (int i = lo + warp; i < hi; i += kW) {
-    const float* x = a.X + (size_t)i * L;
-    float c[P];
-#pragma unroll
-    for (int j = 0; j < P; ++j) c[j] = 0.f;
-    for (int l = lane; l < L; l += 32) {
-      const float xv = x[l];
-#pragma unroll
-      for (int j = 0; j < P; ++j) c[j] = fmaf(xv, panel[l * P + j], c[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < P; ++j) c[j] = wsum(c[j]);
-    if (lane < P) {
-      float v = c[0];
-#pragma unroll
-      for (int j = 1; j < P; ++j)
-        if (lane == j) v = c[j];
-      out[(size_t)i * P + lane] = scale * v;
-    }
+  for (int e = threadIdx.x; e < (hi - lo) * P; e += kT) {
+    const int il = e / P, j = e - il * P;
+    out[(size_t)lo * P + e] = scale * dot_blocked(a.X + (size_t)(lo + il) * L, 1, panel + j, (size_t)P, L);
   }
   __syncthreads();
 }
@@ -329,15 +306,14 @@ __device__ void rank_update(const UArgs& a, const float* L1, const float* R1, fl
   __syncthreads();
 }
 
-// ---- G = E^T E (float) from the FP64 E: warp per entry, lanes over the bands
-__device__ void gram(const UArgs& a, float* G) {
+// ---- G = E^T E from E in shared memory: warp per entry, lanes over the bands
+__device__ void gram(const UArgs& a, const float* E, float* G) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, P = a.P, L = a.L;
   for (int e = warp; e < P * P; e += kW) {
     const int j = e / P, k = e % P;
-    double s = 0.0;
-    for (int l = lane; l < L; l += 32) s += a.Ed[l * P + j] * a.Ed[l * P + k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    float hi = 0.f, lo = 0.f;
+    for (int l = lane; l < L; l += 32) ff_add(hi, lo, E[l * P + j] * E[l * P + k]);
+    const double s = ff_warp_total(hi, lo);
     if (lane == 0) G[e] = (float)s;
   }
   __syncthreads();
@@ -492,7 +468,8 @@ __device__ bool fwd_outer(const UArgs& a, Sm& S, int t, bool rec, unsigned& nbar
   merge_dist(a, a.Ed, a.E32, nullptr);
   if (!gbar(a)) return false;
   for (int e = tid; e < LP; e += kT) S.p0[e] = a.E32[e];
-  gram(a, S.G);
+  __syncthreads();
+  gram(a, S.p0, S.G);
   // c = E^T x_i, the K1 A-steps, a = exp z, and this CTA's share of W = A A^T
   xdot<P>(a, S.p0, 1.f, a.C);
   const float etaA = a.eta[t];
@@ -754,7 +731,8 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
     merge_dist(a, a.Ed, a.E32, nullptr);
     if (!gbar(a)) return;
     for (int e = tid; e < LP; e += kT) S.p0[e] = a.E32[e];
-    gram(a, S.G);
+    __syncthreads();
+    gram(a, S.p0, S.G);
     xdot<P>(a, S.p0, 1.f, a.C);
     {
       float gacc[P * P + 1];
