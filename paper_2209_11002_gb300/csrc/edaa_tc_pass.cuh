@@ -478,16 +478,28 @@ __device__ __noinline__ void tc_pass_item(const Batch* __restrict__ bt, const Cu
           store_w(r * P + j, wdev[j]);
         }
         // A A^T of this tile's pixels: products in 2^-24 fixed point, summed
-        // exactly over the warp's 32 pixels (integer warp reduction)
+        // exactly over the warp's 32 pixels (integer warp reduction); lane e
+        // keeps the sum of entry e and adds it to the run's sums (one
+        // read-modify-write per lane instead of one per entry)
+        float a24[P];
+#pragma unroll
+        for (int k = 0; k < P; ++k) a24[k] = a[k] * 16777216.f;
+        constexpr int NH = (PP + 31) / 32;  // lane words per entry set (p = 8: 36 entries)
+        int mine[NH];
+#pragma unroll
+        for (int h = 0; h < NH; ++h) mine[h] = 0;
         int e = 0;
 #pragma unroll
         for (int j = 0; j < P; ++j)
 #pragma unroll
           for (int k = j; k < P; ++k) {
-            const int v = __reduce_add_sync(0xffffffffu, __float2int_rn(a[j] * a[k] * 16777216.f));
-            if (lane == 0) aaq[(quarter * Rm + r) * PP + e] += (float)v * (1.f / 16777216.f);
+            const int v = __reduce_add_sync(0xffffffffu, __float2int_rn(a[j] * a24[k]));
+            mine[e >> 5] = (lane == (e & 31)) ? v : mine[e >> 5];
             ++e;
           }
+#pragma unroll
+        for (int h = 0; h < NH; ++h)
+          if (h * 32 + lane < PP) aaq[(quarter * Rm + r) * PP + h * 32 + lane] += (float)mine[h] * (1.f / 16777216.f);
       }
     } else {
       // eq. (update_B) without stored logits: u = 0.1 r - Lambda - x^T (S + eta2 R),
