@@ -160,7 +160,7 @@ def unrolled_workload(args, rank, world):
 # outer iteration move the same data; the fit launch, one more X pass, is
 # not included).
 SOLVE_DRAM_BYTES = {
-    ("urban", "bf16", 100): 100 * 1120424192,
+    ("urban", "bf16", 100): 100 * 930451968,
 }
 
 
