@@ -184,6 +184,31 @@ __device__ __forceinline__ float dot_blocked(const float* x, size_t sx, const fl
   return hi + lo;
 }
 
+// The same with both operands in shared memory (32-bit shared addresses and
+// byte strides): explicit shared loads instead of generic ones.
+__device__ __forceinline__ float lds(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float dot_blocked_sh(uint32_t x, uint32_t sx, uint32_t y, uint32_t sy, int n) {
+  float hi = 0.f, lo = 0.f;
+  for (int k0 = 0; k0 < n; k0 += 64) {
+    const int k1 = min(n, k0 + 64);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int k = k0;
+    for (; k + 3 < k1; k += 4) {
+      s0 = fmaf(lds(x + k * sx), lds(y + k * sy), s0);
+      s1 = fmaf(lds(x + (k + 1) * sx), lds(y + (k + 1) * sy), s1);
+      s2 = fmaf(lds(x + (k + 2) * sx), lds(y + (k + 2) * sy), s2);
+      s3 = fmaf(lds(x + (k + 3) * sx), lds(y + (k + 3) * sy), s3);
+    }
+    for (; k < k1; ++k) s0 = fmaf(lds(x + k * sx), lds(y + k * sy), s0);
+    ff_add(hi, lo, (s0 + s1) + (s2 + s3));
+  }
+  return hi + lo;
+}
+
 // ---- a.part[g] = sum over this CTA's pixels of x_i w_i^T (L x p): a thread
 // per entry (l, j), pixels in order
 template <int P>
@@ -192,9 +217,14 @@ __device__ void xw_part(const UArgs& a, const float* __restrict__ w, Sm& S) {
   int lo, hi;
   prange(a.N, lo, hi);
   float* dst = a.part + (size_t)blockIdx.x * LP;
+  const bool sh = a.res_x && a.res_state;  // X and w in shared memory
   for (int e = threadIdx.x; e < LP; e += kT) {
     const int l = e / P, j = e - l * P;
-    dst[e] = dot_blocked(a.X + (size_t)lo * L + l, (size_t)L, w + (size_t)lo * P + j, (size_t)P, hi - lo);
+    const float* xp = a.X + (size_t)lo * L + l;
+    const float* wp = w + (size_t)lo * P + j;
+    dst[e] = sh ? dot_blocked_sh((uint32_t)__cvta_generic_to_shared(xp), 4u * L, (uint32_t)__cvta_generic_to_shared(wp),
+                                 4u * P, hi - lo)
+                : dot_blocked(xp, (size_t)L, wp, (size_t)P, hi - lo);
   }
 }
 
@@ -273,34 +303,60 @@ __device__ void xdot(const UArgs& a, const float* panel, float scale, float* __r
   prange(a.N, lo, hi);
   for (int e = threadIdx.x; e < (hi - lo) * P; e += kT) {
     const int il = e / P, j = e - il * P;
-    out[(size_t)lo * P + e] = scale * dot_blocked(a.X + (size_t)(lo + il) * L, 1, panel + j, (size_t)P, L);
+    const float* xp = a.X + (size_t)(lo + il) * L;
+    out[(size_t)lo * P + e] =
+        scale * (a.res_x ? dot_blocked_sh((uint32_t)__cvta_generic_to_shared(xp), 4u,
+                                          (uint32_t)__cvta_generic_to_shared(panel + j), 4u * P, L)
+                         : dot_blocked(xp, 1, panel + j, (size_t)P, L));
   }
   __syncthreads();
 }
 
-// ---- Xbar_i[l] += s1 sum_j L1[l,j] R1[i,j] + s2 sum_j L2[l,j] R2[i,j] over this CTA's pixels
+// ---- Xbar_i[l] += s1 sum_j L1[l,j] R1[i,j] + s2 sum_j L2[l,j] R2[i,j] over this
+// CTA's pixels (Xbar in global memory): warp per pixel, two pixels at a time,
+// every load of a row issued before its updates so that the round trips overlap
 template <int P>
 __device__ void rank_update(const UArgs& a, const float* L1, const float* R1, float s1, const float* L2,
                             const float* R2, float s2) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, L = a.L;
   int lo, hi;
   prange(a.N, lo, hi);
-  for (int i = lo + warp; i < hi; i += kW) {
-    float r1[P], r2[P];
+  for (int i0 = lo + warp; i0 < hi; i0 += 2 * kW) {
+    float v[2][kLT], r1[2][P], r2[2][P];
 #pragma unroll
-    for (int j = 0; j < P; ++j) {
-      r1[j] = s1 * R1[(size_t)i * P + j];
-      r2[j] = L2 ? s2 * R2[(size_t)i * P + j] : 0.f;
-    }
-    float* xb = a.Xbar + (size_t)i * L;
-    for (int l = lane; l < L; l += 32) {
-      float v = xb[l];
+    for (int u = 0; u < 2; ++u) {
+      const int i = i0 + u * kW;
+      const bool live = i < hi;
+      const float* xb = a.Xbar + (size_t)(live ? i : i0) * L;
+#pragma unroll
+      for (int k = 0; k < kLT; ++k) {
+        const int l = lane + 32 * k;
+        v[u][k] = (live && l < L) ? xb[l] : 0.f;
+      }
 #pragma unroll
       for (int j = 0; j < P; ++j) {
-        v = fmaf(L1[l * P + j], r1[j], v);
-        if (L2) v = fmaf(L2[l * P + j], r2[j], v);
+        r1[u][j] = live ? s1 * R1[(size_t)i * P + j] : 0.f;
+        r2[u][j] = (live && L2) ? s2 * R2[(size_t)i * P + j] : 0.f;
       }
-      xb[l] = v;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = i0 + u * kW;
+      if (i >= hi) continue;
+      float* xb = a.Xbar + (size_t)i * L;
+#pragma unroll
+      for (int k = 0; k < kLT; ++k) {
+        const int l = lane + 32 * k;
+        if (l < L) {
+          float x = v[u][k];
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            x = fmaf(L1[l * P + j], r1[u][j], x);
+            if (L2) x = fmaf(L2[l * P + j], r2[u][j], x);
+          }
+          xb[l] = x;
+        }
+      }
     }
   }
   __syncthreads();
