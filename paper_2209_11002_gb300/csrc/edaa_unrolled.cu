@@ -57,6 +57,7 @@ constexpr int kW = kT / 32;  // warps per CTA
 constexpr int kMaxP = 8;
 constexpr int kLT = 10;      // L <= 320: bands per lane in the X contractions
 constexpr int kLPMax = 320 * kMaxP;
+constexpr int kMaxG = 256;   // CTAs of a sweep at most
 constexpr int kSmall = 80;   // per-CTA slots of a small reduction (>= p^2 + 1, >= 2p)
 
 __device__ __forceinline__ float wsum(float v) {
@@ -98,15 +99,18 @@ struct UArgs {
   int L, N, P, T, K1, K2, LP;  // LP = L p
   uint64_t seed;
   const float* X;              // N x L
-  const float* eta;            // 2T: eta_A[t], then eta_B[t]
-  float *z, *l, *b, *a, *C, *g, *d, *lbar, *zbar, *Abar, *zeta, *Dbar, *bp, *tmp;
-  float *zck, *lck;            // (T + 1) x N x p: log A, log B at the start of every outer iteration
-  float *ls, *gs, *Rs;         // backward recompute: (K2 + 1) logits, K2 B-gradients (N x p), K2 R (L x p)
+  const double* eta;           // 2T: eta_A[t], then eta_B[t]
+  double *z, *l;               // log A, log B (FP64: a float's rounding of a log is the sweep's largest error)
+  float *b, *a, *C, *g, *d, *lbar, *zbar, *Abar, *zeta, *Dbar, *bp, *tmp;
+  double *zck, *lck;           // (T + 1) x N x p: log A, log B at the start of every outer iteration
+  double* ls;                  // backward recompute: (K2 + 1) logits (N x p)
+  float *gs, *Rs;              // K2 B-gradients (N x p), K2 R (L x p)
   float* Xbar;                 // N x L
   const float *dE, *dA;        // backward inputs: L x p, p x N
   float *Eout, *Aout;          // forward outputs: E_hat (L x p), A_hat (p x N)
   float* part;                 // G x LP per-CTA partials of an X contraction
   float* part2;                // G x kSmall per-CTA partials of a small reduction
+  double* part2d;              // G x kSmall per-CTA FP64 partials (W = A A^T)
   float* peta;                 // G x 2T per-CTA partials of d eta
   float *E32, *R32, *P32;      // merged L x p (float)
   double *Ed, *XCd;            // merged L x p (FP64)
@@ -116,15 +120,28 @@ struct UArgs {
   long long timeout_ns;
   int maxpx;                   // the most pixels a CTA owns
   int res_state, res_x;        // the per-pixel arrays / the CTA's X rows live in shared memory
+  int Ls;                      // row stride of X as the sweeps read it (L, or padded in shared memory)
 };
-constexpr int kPixArrays = 14;  // z, l, b, a, C, g, d, lbar, zbar, Abar, zeta, Dbar, bp, tmp
+constexpr int kPixD = 2;   // per-pixel FP64 arrays: z, l
+constexpr int kPixF = 12;  // per-pixel float arrays: b, a, C, g, d, lbar, zbar, Abar, zeta, Dbar, bp, tmp
+
+// exp of an FP64 log to float accuracy: expf of the float part times
+// 1 + (the remainder), the first-order term of exp of the remainder
+__device__ __forceinline__ float exp_d(double v) {
+  const float f = (float)v;
+  const float e = expf(f);
+  return fmaf(e, (float)(v - (double)f), e);
+}
 
 // shared memory of a CTA
 struct Sm {
-  float p0[kLPMax], p1[kLPMax];  // L x p panels
+  alignas(16) float p0[kLPMax];  // L x p panels
+  alignas(16) float p1[kLPMax];
+  float xs[4 * kMaxP * kT];      // the pixel-chunk sums of an X contraction
   float red[kW * kSmall];                     // per-warp partials of a small reduction
   float W[64], G[64], Wb[64], Wacc[64], tmp[kSmall];
   double Gb[64], lse[kMaxP], sd[kMaxP];
+  float Gl[64], Wl[64];          // low parts: G + Gl = E^T E, W + Wl = A A^T, exact for the float E, A
 };
 
 __device__ __forceinline__ void prange(int N, int& lo, int& hi) {
@@ -172,6 +189,7 @@ __device__ __forceinline__ float dot_blocked(const float* x, size_t sx, const fl
     const int k1 = min(n, k0 + 64);
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
     int k = k0;
+#pragma unroll 4
     for (; k + 3 < k1; k += 4) {
       s0 = fmaf(x[k * sx], y[k * sy], s0);
       s1 = fmaf(x[(k + 1) * sx], y[(k + 1) * sy], s1);
@@ -184,47 +202,97 @@ __device__ __forceinline__ float dot_blocked(const float* x, size_t sx, const fl
   return hi + lo;
 }
 
-// The same with both operands in shared memory (32-bit shared addresses and
-// byte strides): explicit shared loads instead of generic ones.
-__device__ __forceinline__ float lds(uint32_t a) {
-  float v;
-  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ float dot_blocked_sh(uint32_t x, uint32_t sx, uint32_t y, uint32_t sy, int n) {
-  float hi = 0.f, lo = 0.f;
-  for (int k0 = 0; k0 < n; k0 += 64) {
-    const int k1 = min(n, k0 + 64);
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    int k = k0;
-    for (; k + 3 < k1; k += 4) {
-      s0 = fmaf(lds(x + k * sx), lds(y + k * sy), s0);
-      s1 = fmaf(lds(x + (k + 1) * sx), lds(y + (k + 1) * sy), s1);
-      s2 = fmaf(lds(x + (k + 2) * sx), lds(y + (k + 2) * sy), s2);
-      s3 = fmaf(lds(x + (k + 3) * sx), lds(y + (k + 3) * sy), s3);
+// row j of an L x p panel in shared memory (16-byte aligned) into registers
+template <int P>
+__device__ __forceinline__ void ld_row(const float* r, float (&v)[P]) {
+  if constexpr (P % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < P; j += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(r + j);
+      v[j] = t.x; v[j + 1] = t.y; v[j + 2] = t.z; v[j + 3] = t.w;
     }
-    for (; k < k1; ++k) s0 = fmaf(lds(x + k * sx), lds(y + k * sy), s0);
-    ff_add(hi, lo, (s0 + s1) + (s2 + s3));
+  } else if constexpr (P % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < P; j += 2) {
+      const float2 t = *reinterpret_cast<const float2*>(r + j);
+      v[j] = t.x; v[j + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < P; ++j) v[j] = r[j];
   }
-  return hi + lo;
 }
 
-// ---- a.part[g] = sum over this CTA's pixels of x_i w_i^T (L x p): a thread
-// per entry (l, j), pixels in order
+// ---- a.part[g] = sum over this CTA's pixels of x_i w_i^T (L x p).
+// X rows in shared memory (row stride Ls: a multiple of 4, zero padded): a
+// thread per (4 bands, pixel chunk); per pixel one 16-byte load of x and p
+// broadcast loads of w feed 4p FMAs; chains of 16 pixels go into float-float
+// sums; the C chunk sums of an entry are then added in chunk order.
+// X in global memory: a thread per entry (l, j), pixels in order.
 template <int P>
 __device__ void xw_part(const UArgs& a, const float* __restrict__ w, Sm& S) {
-  const int L = a.L, LP = a.LP;
+  const int L = a.L, LP = a.LP, tid = threadIdx.x;
   int lo, hi;
   prange(a.N, lo, hi);
   float* dst = a.part + (size_t)blockIdx.x * LP;
-  const bool sh = a.res_x && a.res_state;  // X and w in shared memory
-  for (int e = threadIdx.x; e < LP; e += kT) {
-    const int l = e / P, j = e - l * P;
-    const float* xp = a.X + (size_t)lo * L + l;
-    const float* wp = w + (size_t)lo * P + j;
-    dst[e] = sh ? dot_blocked_sh((uint32_t)__cvta_generic_to_shared(xp), 4u * L, (uint32_t)__cvta_generic_to_shared(wp),
-                                 4u * P, hi - lo)
-                : dot_blocked(xp, (size_t)L, wp, (size_t)P, hi - lo);
+  if (!a.res_x) {
+    for (int e = tid; e < LP; e += kT) {
+      const int l = e / P, j = e - l * P;
+      const float* xp = a.X + (size_t)lo * L + l;
+      const float* wp = w + (size_t)lo * P + j;
+      dst[e] = dot_blocked(xp, (size_t)L, wp, (size_t)P, hi - lo);
+    }
+    return;
+  }
+  const int Ls = a.Ls, Q = (L + 3) >> 2, C = min(8, max(1, kT / Q)), npx = hi - lo;
+  if (tid < Q * C) {
+    const int c = tid / Q, q = tid - c * Q;
+    const int k0 = lo + npx * c / C, k1 = lo + npx * (c + 1) / C;
+    float sh[4][P], sl[4][P], s[4][P];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int j = 0; j < P; ++j) sh[r][j] = sl[r][j] = s[r][j] = 0.f;
+    const float* xp = a.X + (size_t)k0 * Ls + 4 * q;
+    const float* wp = w + (size_t)k0 * P;
+    for (int kb = k0; kb < k1; kb += 16) {
+      const int ke = min(k1, kb + 16);
+#pragma unroll 4
+      for (int k = kb; k < ke; ++k) {
+        const float4 x4 = *reinterpret_cast<const float4*>(xp);
+        float wv[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) wv[j] = wp[j];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          s[0][j] = fmaf(x4.x, wv[j], s[0][j]);
+          s[1][j] = fmaf(x4.y, wv[j], s[1][j]);
+          s[2][j] = fmaf(x4.z, wv[j], s[2][j]);
+          s[3][j] = fmaf(x4.w, wv[j], s[3][j]);
+        }
+        xp += Ls;
+        wp += P;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          ff_add(sh[r][j], sl[r][j], s[r][j]);
+          s[r][j] = 0.f;
+        }
+    }
+    float* xs = S.xs + (size_t)c * 4 * P * Q;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int j = 0; j < P; ++j) xs[(r * P + j) * Q + q] = sh[r][j] + sl[r][j];
+  }
+  __syncthreads();
+  for (int e = tid; e < LP; e += kT) {
+    const int l = e / P, j = e - l * P, q = l >> 2, r = l & 3;
+    float h = 0.f, lw = 0.f;
+    for (int c = 0; c < C; ++c) ff_add(h, lw, S.xs[((size_t)c * 4 * P + r * P + j) * Q + q]);
+    dst[e] = h + lw;
   }
 }
 
@@ -254,6 +322,40 @@ __device__ void merge_small(const UArgs& a, int n, float* outf, double* outd) {
     if (lane == 0) {
       if (outf) outf[e] = (float)s;
       if (outd) outd[e] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// ---- W = A A^T: this CTA's share in FP64 (the products of floats are exact;
+// a warp per entry, lanes over the pixels, a fixed butterfly) into
+// a.part2d[g]; after a barrier every CTA sums the CTAs' partials in order into
+// outf + out_lo (float-float)
+template <int P>
+__device__ void aat_part(const UArgs& a) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int lo, hi;
+  prange(a.N, lo, hi);
+  for (int e = warp; e < P * P; e += kW) {
+    const int j = e / P, k = e - j * P;
+    double s = 0.0;
+    for (int i = lo + lane; i < hi; i += 32)
+      s = fma((double)a.a[(size_t)i * P + j], (double)a.a[(size_t)i * P + k], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) a.part2d[(size_t)blockIdx.x * kSmall + e] = s;
+  }
+}
+__device__ void merge_small_d(const UArgs& a, int n, float* out_lo, float* outf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
+  for (int e = warp; e < n; e += kW) {
+    double s = 0.0;
+    for (int b = lane; b < G; b += 32) s += a.part2d[(size_t)b * kSmall + e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      outf[e] = (float)s;
+      out_lo[e] = (float)(s - (double)outf[e]);
     }
   }
   __syncthreads();
@@ -295,19 +397,97 @@ __device__ void block_total(const float (&v)[NV], Sm& S) {
   __syncthreads();
 }
 
-// ---- out_i = scale x_i^T panel: a thread per (pixel, j), bands in order
+// ---- out_i = scale x_i^T panel (panel: L x p in shared memory, 16-byte aligned).
+// X rows in shared memory: a warp takes 16 pixels; lane (h, q) takes pixels
+// q and q + 8 over quarter h of the bands.  Per 4 bands two 16-byte loads of
+// x and four panel rows feed 8p FMAs; chains of 16 bands go into float-float
+// sums, and the quarters meet by shuffles.  X in global memory: a thread per
+// (pixel, j), bands in order.
 template <int P>
 __device__ void xdot(const UArgs& a, const float* panel, float scale, float* __restrict__ out) {
   const int L = a.L;
   int lo, hi;
   prange(a.N, lo, hi);
-  for (int e = threadIdx.x; e < (hi - lo) * P; e += kT) {
-    const int il = e / P, j = e - il * P;
-    const float* xp = a.X + (size_t)(lo + il) * L;
-    out[(size_t)lo * P + e] =
-        scale * (a.res_x ? dot_blocked_sh((uint32_t)__cvta_generic_to_shared(xp), 4u,
-                                          (uint32_t)__cvta_generic_to_shared(panel + j), 4u * P, L)
-                         : dot_blocked(xp, 1, panel + j, (size_t)P, L));
+  if (!a.res_x) {
+    for (int e = threadIdx.x; e < (hi - lo) * P; e += kT) {
+      const int il = e / P, j = e - il * P;
+      const float* xp = a.X + (size_t)(lo + il) * L;
+      out[(size_t)lo * P + e] = scale * dot_blocked(xp, 1, panel + j, (size_t)P, L);
+    }
+    __syncthreads();
+    return;
+  }
+  const int Ls = a.Ls, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, h = lane >> 3, pp = lane & 7;
+  const int Qf = L >> 2;
+  const int qa = Qf * h / 4, qz = Qf * (h + 1) / 4;
+  for (int ib = lo + warp * 16; ib < hi; ib += kW * 16) {
+    const int i0 = ib + pp, i1 = ib + 8 + pp;
+    const bool live0 = i0 < hi, live1 = i1 < hi;
+    const float* x0 = a.X + (size_t)(live0 ? i0 : ib) * Ls;
+    const float* x1 = a.X + (size_t)(live1 ? i1 : ib) * Ls;
+    float sh0[P], sl0[P], s0[P], sh1[P], sl1[P], s1[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) sh0[j] = sl0[j] = s0[j] = sh1[j] = sl1[j] = s1[j] = 0.f;
+    for (int q0 = qa; q0 < qz; q0 += 4) {
+      const int qe = min(qz, q0 + 4);
+      for (int q = q0; q < qe; ++q) {
+        const float4 a4 = *reinterpret_cast<const float4*>(x0 + 4 * q);
+        const float4 b4 = *reinterpret_cast<const float4*>(x1 + 4 * q);
+        const float* pr = panel + (size_t)q * 4 * P;
+        float v0[P], v1[P], v2[P], v3[P];
+        ld_row<P>(pr, v0);
+        ld_row<P>(pr + P, v1);
+        ld_row<P>(pr + 2 * P, v2);
+        ld_row<P>(pr + 3 * P, v3);
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          s0[j] = fmaf(a4.x, v0[j], s0[j]);
+          s1[j] = fmaf(b4.x, v0[j], s1[j]);
+          s0[j] = fmaf(a4.y, v1[j], s0[j]);
+          s1[j] = fmaf(b4.y, v1[j], s1[j]);
+          s0[j] = fmaf(a4.z, v2[j], s0[j]);
+          s1[j] = fmaf(b4.z, v2[j], s1[j]);
+          s0[j] = fmaf(a4.w, v3[j], s0[j]);
+          s1[j] = fmaf(b4.w, v3[j], s1[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        ff_add(sh0[j], sl0[j], s0[j]);
+        ff_add(sh1[j], sl1[j], s1[j]);
+        s0[j] = s1[j] = 0.f;
+      }
+    }
+    if (h == 3) {
+      for (int l = 4 * Qf; l < L; ++l)
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          s0[j] = fmaf(x0[l], panel[l * P + j], s0[j]);
+          s1[j] = fmaf(x1[l], panel[l * P + j], s1[j]);
+        }
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        ff_add(sh0[j], sl0[j], s0[j]);
+        ff_add(sh1[j], sl1[j], s1[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      float H0 = sh0[j], L0 = sl0[j], H1 = sh1[j], L1 = sl1[j];
+#pragma unroll
+      for (int o = 8; o <= 16; o <<= 1) {
+        const float a_ = __shfl_xor_sync(0xffffffffu, H0, o), b_ = __shfl_xor_sync(0xffffffffu, L0, o);
+        const float c_ = __shfl_xor_sync(0xffffffffu, H1, o), d_ = __shfl_xor_sync(0xffffffffu, L1, o);
+        ff_add(H0, L0, a_);
+        L0 += b_;
+        ff_add(H1, L1, c_);
+        L1 += d_;
+      }
+      if (h == 0) {
+        if (live0) out[(size_t)i0 * P + j] = scale * (H0 + L0);
+        if (live1) out[(size_t)i1 * P + j] = scale * (H1 + L1);
+      }
+    }
   }
   __syncthreads();
 }
@@ -363,22 +543,33 @@ __device__ void rank_update(const UArgs& a, const float* L1, const float* R1, fl
 }
 
 // ---- G = E^T E from E in shared memory: warp per entry, lanes over the bands
-__device__ void gram(const UArgs& a, const float* E, float* G) {
+// (each product split exactly into its rounded value and error, both summed,
+// so that G + Gl is E^T E of the float E to about 2^-44)
+__device__ void gram(const UArgs& a, const float* E, float* G, float* Gl) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, P = a.P, L = a.L;
   for (int e = warp; e < P * P; e += kW) {
     const int j = e / P, k = e % P;
     float hi = 0.f, lo = 0.f;
-    for (int l = lane; l < L; l += 32) ff_add(hi, lo, E[l * P + j] * E[l * P + k]);
+    for (int l = lane; l < L; l += 32) {
+      const float x = E[l * P + j], y = E[l * P + k];
+      const float pr = __fmul_rn(x, y);
+      ff_add(hi, lo, pr);
+      lo += fmaf(x, y, -pr);
+    }
     const double s = ff_warp_total(hi, lo);
-    if (lane == 0) G[e] = (float)s;
+    if (lane == 0) {
+      G[e] = (float)s;
+      Gl[e] = (float)(s - (double)G[e]);
+    }
   }
   __syncthreads();
 }
 
 // ---- per-column log-sum-exp of the logits v over all pixels: this CTA's
-// (max, scaled sum) pairs into part2, then (after a barrier) every CTA merges
+// (max m, sum of exp(v - m)) pairs into part2 (two passes: the column maxima
+// over the CTA, then the sums), then (after a barrier) every CTA merges
 template <int P>
-__device__ void lse_part(const UArgs& a, const float* __restrict__ v, Sm& S) {
+__device__ void lse_part(const UArgs& a, const double* __restrict__ v, Sm& S) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int lo, hi;
   prange(a.N, lo, hi);
@@ -388,123 +579,163 @@ __device__ void lse_part(const UArgs& a, const float* __restrict__ v, Sm& S) {
     m[j] = -INFINITY;
     s[j] = 0.f;
   }
-  for (int i = lo + (int)threadIdx.x; i < hi; i += kT) {
+  for (int i = lo + (int)threadIdx.x; i < hi; i += kT)
 #pragma unroll
-    for (int j = 0; j < P; ++j) {
-      const float x = v[(size_t)i * P + j];
-      if (x > m[j]) {
-        s[j] = s[j] * expf(m[j] - x) + 1.f;
-        m[j] = x;
-      } else {
-        s[j] += expf(x - m[j]);
-      }
-    }
-  }
+    for (int j = 0; j < P; ++j) m[j] = fmaxf(m[j], (float)v[(size_t)i * P + j]);
 #pragma unroll
   for (int j = 0; j < P; ++j) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {  // fixed butterfly
-      const float m2 = __shfl_xor_sync(0xffffffffu, m[j], o), s2 = __shfl_xor_sync(0xffffffffu, s[j], o);
-      const float mm = fmaxf(m[j], m2);
-      const float t1 = (m[j] == -INFINITY) ? 0.f : s[j] * expf(m[j] - mm);
-      const float t2 = (m2 == -INFINITY) ? 0.f : s2 * expf(m2 - mm);
-      m[j] = mm;
-      s[j] = t1 + t2;
-    }
-    if (lane == 0) {
-      S.red[warp * kSmall + 2 * j] = m[j];
-      S.red[warp * kSmall + 2 * j + 1] = s[j];
-    }
+    for (int o = 16; o > 0; o >>= 1) m[j] = fmaxf(m[j], __shfl_xor_sync(0xffffffffu, m[j], o));
+    if (lane == 0) S.red[warp * kSmall + j] = m[j];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    float mm = S.red[j];
+    for (int w = 1; w < kW; ++w) mm = fmaxf(mm, S.red[w * kSmall + j]);
+    m[j] = mm;  // the CTA's column maximum (-inf for a CTA without pixels: the merge skips it)
+  }
+  for (int i = lo + (int)threadIdx.x; i < hi; i += kT)
+#pragma unroll
+    for (int j = 0; j < P; ++j) s[j] += expf((float)(v[(size_t)i * P + j] - (double)m[j]));
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    s[j] = wsum(s[j]);
+    if (lane == 0) S.red[warp * kSmall + P + j] = s[j];
   }
   __syncthreads();
   if (threadIdx.x < P) {
     const int j = threadIdx.x;
-    float mm = -INFINITY, ss = 0.f;
-    for (int w = 0; w < kW; ++w) {
-      const float m2 = S.red[w * kSmall + 2 * j], s2 = S.red[w * kSmall + 2 * j + 1];
-      const float mn = fmaxf(mm, m2);
-      const float t1 = (mm == -INFINITY) ? 0.f : ss * expf(mm - mn);
-      const float t2 = (m2 == -INFINITY) ? 0.f : s2 * expf(m2 - mn);
-      mm = mn;
-      ss = t1 + t2;
-    }
-    a.part2[(size_t)blockIdx.x * kSmall + 2 * j] = mm;
+    float ss = 0.f;
+    for (int w = 0; w < kW; ++w) ss += S.red[w * kSmall + P + j];
+    a.part2[(size_t)blockIdx.x * kSmall + 2 * j] = m[j];
     a.part2[(size_t)blockIdx.x * kSmall + 2 * j + 1] = ss;
   }
   __syncthreads();
 }
+// every CTA: lse_j = M + log sum_g s_g exp(m_g - M), M the largest m_g (the
+// CTAs' pairs loaded once, a warp per column)
 __device__ void lse_merge(const UArgs& a, double* lse) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
+  constexpr int kB = kMaxG / 32;
   if (warp < a.P) {
     const int j = warp;
-    float m = -INFINITY;
-    for (int b = lane; b < G; b += 32) m = fmaxf(m, a.part2[(size_t)b * kSmall + 2 * j]);
+    float mb[kB], sb[kB], m = -INFINITY;
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int b = lane + 32 * u;
+      mb[u] = b < G ? a.part2[(size_t)b * kSmall + 2 * j] : -INFINITY;
+      sb[u] = b < G ? a.part2[(size_t)b * kSmall + 2 * j + 1] : 0.f;
+      m = fmaxf(m, mb[u]);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     float hi = 0.f, lo = 0.f;
-    for (int b = lane; b < G; b += 32) {
-      const float mb = a.part2[(size_t)b * kSmall + 2 * j];
-      if (mb != -INFINITY) ff_add(hi, lo, a.part2[(size_t)b * kSmall + 2 * j + 1] * expf(mb - m));
-    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u)
+      if (mb[u] != -INFINITY) ff_add(hi, lo, sb[u] * expf(mb[u] - m));
     const double sum = ff_warp_total(hi, lo);
-    if (lane == 0) lse[j] = (double)m + log(sum);
+    // (logf: its rounding shifts the whole column of logits alike, which the
+    // next normalisation takes out again)
+    if (lane == 0) lse[j] = (double)m + (double)logf((float)sum);
   }
   __syncthreads();
 }
 
 // one pixel's A-phase: K1 mirror steps; keeps the iterates when `zs` is given
+// z = zh + zl (float-float) through the steps, FP64 in memory; the
+// normaliser lz is a float: its rounding is common to the pixel's p entries,
+// which the next normalisation takes out again
+__device__ __forceinline__ void ff_sub(float& h, float& l, float x) {  // h + l -= x
+  const float s = h - x;
+  const float bp = s - h;
+  const float e = (h - (s - bp)) - (x + bp);
+  l += e;
+  h = s + l;  // renormalise
+  l -= h - s;
+}
+// sum_q (h_q + l_q) v_q - c for float-float weights (h, l) and float v, c:
+// every product split exactly (its rounded value and the fma remainder), the
+// sum carried as float-float; good to about 2^-44 of the largest term
 template <int P>
-__device__ __forceinline__ void a_steps(float* z, const float* c, const float* G, float eta, int K1,
-                                        float (*zs)[kMaxP]) {
+__device__ __forceinline__ float ff_dot_sub(const float* h, const float* l, const float* v, float c) {
+  float s = -c, e = 0.f;
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const float pr = __fmul_rn(h[q], v[q]);
+    const float pe = fmaf(h[q], v[q], -pr);
+    const float t = s + pr;
+    const float bp = t - s;
+    e += ((s - (t - bp)) + (pr - bp)) + fmaf(l[q], v[q], pe);
+    s = t;
+  }
+  return s + e;
+}
+
+// The gradient g = G a - c cancels near a fit: it is evaluated from G + Gl =
+// E^T E, exact for the float E, and the float a and c (ff_dot_sub).
+template <int P>
+__device__ __forceinline__ void a_steps(double* z, const float* c, const float* G, const float* Gl, double eta,
+                                        int K1, float (*zs)[kMaxP]) {
+  float zh[P], zl[P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    zh[j] = (float)z[j];
+    zl[j] = (float)(z[j] - (double)zh[j]);
+  }
+  const float et = (float)eta;
   for (int k = 0; k < K1; ++k) {
     if (zs)
 #pragma unroll
-      for (int j = 0; j < P; ++j) zs[k][j] = z[j];
+      for (int j = 0; j < P; ++j) zs[k][j] = zh[j];
     float av[P], mx = -INFINITY;
 #pragma unroll
-    for (int j = 0; j < P; ++j) av[j] = expf(z[j]);
+    for (int j = 0; j < P; ++j) {
+      const float e = expf(zh[j]);
+      av[j] = fmaf(e, zl[j], e);
+    }
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-      float g = -c[j];
-#pragma unroll
-      for (int q = 0; q < P; ++q) g = fmaf(G[j * P + q], av[q], g);
-      z[j] = fmaf(-eta, g, z[j]);
-      mx = fmaxf(mx, z[j]);
+      const float g = ff_dot_sub<P>(G + j * P, Gl + j * P, av, c[j]);
+      ff_sub(zh[j], zl[j], __fmul_rn(et, g));  // (a rounded product: not contracted into the sum)
+      mx = fmaxf(mx, zh[j]);
     }
     float se = 0.f;
 #pragma unroll
-    for (int j = 0; j < P; ++j) se += expf(z[j] - mx);
+    for (int j = 0; j < P; ++j) se += expf((zh[j] - mx) + zl[j]);
     const float lz = mx + logf(se);
 #pragma unroll
-    for (int j = 0; j < P; ++j) z[j] -= lz;
+    for (int j = 0; j < P; ++j) ff_sub(zh[j], zl[j], lz);
   }
   if (zs)
 #pragma unroll
-    for (int j = 0; j < P; ++j) zs[K1][j] = z[j];
+    for (int j = 0; j < P; ++j) zs[K1][j] = zh[j];
+#pragma unroll
+  for (int j = 0; j < P; ++j) z[j] = (double)zh[j] + (double)zl[j];
 }
 
 // l <- l - lse (per column), b = exp(l); optionally a copy of l
 template <int P>
-__device__ void shift_exp(const UArgs& a, const double* lse, float* copy) {
+__device__ void shift_exp(const UArgs& a, const double* lse, double* copy) {
   int lo, hi;
   prange(a.N, lo, hi);
   for (int e = lo * P + (int)threadIdx.x; e < hi * P; e += kT) {
-    const float v = (float)((double)a.l[e] - lse[e % P]);
+    const double v = a.l[e] - lse[e % P];
     a.l[e] = v;
-    a.b[e] = expf(v);
+    a.b[e] = exp_d(v);
     if (copy) copy[e] = v;
   }
   __syncthreads();
 }
-// dst = src over this CTA's pixels (p values each); b = exp(src) when b is given
+// dst = src (logs) over this CTA's pixels (p values each); b = exp(src) when b is given
 template <int P>
-__device__ void copy_px(const UArgs& a, const float* __restrict__ src, float* __restrict__ dst, float* __restrict__ eb) {
+__device__ void copy_px(const UArgs& a, const double* __restrict__ src, double* __restrict__ dst, float* __restrict__ eb) {
   int lo, hi;
   prange(a.N, lo, hi);
   for (int e = lo * P + (int)threadIdx.x; e < hi * P; e += kT) {
-    const float v = src[e];
+    const double v = src[e];
     if (dst) dst[e] = v;
-    if (eb) eb[e] = expf(v);
+    if (eb) eb[e] = exp_d(v);
   }
   __syncthreads();
 }
@@ -525,47 +756,42 @@ __device__ bool fwd_outer(const UArgs& a, Sm& S, int t, bool rec, unsigned& nbar
   if (!gbar(a)) return false;
   for (int e = tid; e < LP; e += kT) S.p0[e] = a.E32[e];
   __syncthreads();
-  gram(a, S.p0, S.G);
+  gram(a, S.p0, S.G, S.Gl);
   // c = E^T x_i, the K1 A-steps, a = exp z, and this CTA's share of W = A A^T
   xdot<P>(a, S.p0, 1.f, a.C);
-  const float etaA = a.eta[t];
-  float w[P * P];
-#pragma unroll
-  for (int e = 0; e < P * P; ++e) w[e] = 0.f;
+  const double etaA = a.eta[t];
   for (int i = lo + tid; i < hi; i += kT) {
-    float z[kMaxP], c[kMaxP], av[P];
+    double z[kMaxP];
+    float c[kMaxP];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
       z[j] = a.z[(size_t)i * P + j];
       c[j] = a.C[(size_t)i * P + j];
     }
-    a_steps<P>(z, c, S.G, etaA, a.K1, nullptr);
+    a_steps<P>(z, c, S.G, S.Gl, etaA, a.K1, nullptr);
 #pragma unroll
     for (int j = 0; j < P; ++j) {
       a.z[(size_t)i * P + j] = z[j];
-      av[j] = expf(z[j]);
-      a.a[(size_t)i * P + j] = av[j];
+      a.a[(size_t)i * P + j] = exp_d(z[j]);
     }
-#pragma unroll
-    for (int j = 0; j < P; ++j)
-#pragma unroll
-      for (int k = 0; k < P; ++k) w[j * P + k] = fmaf(av[j], av[k], w[j * P + k]);
   }
-  block_part<P * P>(a, w, S);
+  __syncthreads();
+  aat_part<P>(a);
   if (rec) copy_px<P>(a, a.l, a.ls, nullptr);
   if (!gbar(a)) return false;
-  merge_small(a, P * P, S.W, nullptr);
-  const float etaB = a.eta[a.T + t];
+  merge_small_d(a, P * P, S.Wl, S.W);
+  const double etaB = a.eta[a.T + t];
   for (int k = 0; k < a.K2; ++k) {
-    // d_i = W b_i - a_i; R = X D (FP64 and float; kept for the reverse sweep)
-    for (int i = lo + tid; i < hi; i += kT)
+    // d_i = W b_i - a_i (cancels near a fit: from the exact W + Wl by
+    // ff_dot_sub); R = X D (FP64 and float; kept for the reverse sweep)
+    for (int i = lo + tid; i < hi; i += kT) {
+      float bv[P];
 #pragma unroll
-      for (int j = 0; j < P; ++j) {
-        float s = -a.a[(size_t)i * P + j];
+      for (int q = 0; q < P; ++q) bv[q] = a.b[(size_t)i * P + q];
 #pragma unroll
-        for (int q = 0; q < P; ++q) s = fmaf(S.W[j * P + q], a.b[(size_t)i * P + q], s);
-        a.d[(size_t)i * P + j] = s;
-      }
+      for (int j = 0; j < P; ++j)
+        a.d[(size_t)i * P + j] = ff_dot_sub<P>(S.W + j * P, S.Wl + j * P, bv, a.a[(size_t)i * P + j]);
+    }
     __syncthreads();
     xw_part<P>(a, a.d, S);
     if (!gbar(a)) return false;
@@ -577,7 +803,7 @@ __device__ bool fwd_outer(const UArgs& a, Sm& S, int t, bool rec, unsigned& nbar
     xdot<P>(a, S.p0, 1.f, a.g);
     for (int e = lo * P + tid; e < hi * P; e += kT) {
       const float gv = a.g[e];
-      a.l[e] = fmaf(-etaB, gv, a.l[e]);
+      a.l[e] = fma(-etaB, (double)gv, a.l[e]);
       if (rec) a.gs[(size_t)k * a.N * P + e] = gv;
     }
     __syncthreads();
@@ -600,16 +826,24 @@ __device__ UArgs local_view(const UArgs& g, float* dyn) {
   prange(g.N, lo, hi);
   const int P = g.P, L = g.L;
   float* q = dyn;
-  if (g.res_x) {
-    const float* src = g.X + (size_t)lo * L;  // (rows of L floats: not 16-byte aligned in general)
-    for (int e = threadIdx.x; e < (hi - lo) * L; e += kT) q[e] = src[e];
-    a.X = q - (size_t)lo * L;
-    q += ((size_t)g.maxpx * L + 3) & ~(size_t)3;
+  if (g.res_x) {  // rows padded with zeros to the stride Ls (a multiple of 4)
+    const int Ls = g.Ls;
+    const float* src = g.X + (size_t)lo * L;
+    for (int e = threadIdx.x; e < (hi - lo) * Ls; e += kT) {
+      const int r = e / Ls, l = e - r * Ls;
+      q[e] = l < L ? src[(size_t)r * L + l] : 0.f;
+    }
+    a.X = q - (size_t)lo * Ls;
+    q += (size_t)g.maxpx * Ls;
   }
-  if (g.res_state) {
-    float** arr[kPixArrays] = {&a.z, &a.l, &a.b, &a.a, &a.C, &a.g, &a.d, &a.lbar, &a.zbar, &a.Abar, &a.zeta, &a.Dbar,
-                               &a.bp, &a.tmp};
-    for (int k = 0; k < kPixArrays; ++k) {
+  if (g.res_state) {  // the FP64 arrays first (q is 16-byte aligned here)
+    double** ard[kPixD] = {&a.z, &a.l};
+    for (int k = 0; k < kPixD; ++k) {
+      *ard[k] = reinterpret_cast<double*>(q) - (size_t)lo * P;
+      q += (size_t)g.maxpx * P * 2;
+    }
+    float** arr[kPixF] = {&a.b, &a.a, &a.C, &a.g, &a.d, &a.lbar, &a.zbar, &a.Abar, &a.zeta, &a.Dbar, &a.bp, &a.tmp};
+    for (int k = 0; k < kPixF; ++k) {
       *arr[k] = q - (size_t)lo * P;
       q += (size_t)g.maxpx * P;
     }
@@ -621,7 +855,7 @@ __device__ UArgs local_view(const UArgs& g, float* dyn) {
 template <int P>
 __global__ void __launch_bounds__(kT, 1) k_unrolled_fwd(UArgs ag) {
   __shared__ Sm S;
-  extern __shared__ float dyn[];
+  extern __shared__ __align__(16) float dyn[];
   const UArgs a = local_view(ag, dyn);
   unsigned nbar = 0;
   const int tid = threadIdx.x;
@@ -630,8 +864,8 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_fwd(UArgs ag) {
   prange(a.N, lo, hi);
   // A^0 = 1/p (eq. initA0); B^0 = softmax(0.1 u), u from SplitMix64 (eq. initB0)
   for (int e = lo * P + tid; e < hi * P; e += kT) {
-    a.z[e] = -logf((float)P);
-    a.l[e] = 0.1f * ((float)(sm64(a.seed, (uint64_t)e + 1) >> 40) * (1.0f / 16777216.0f));
+    a.z[e] = -log((double)P);
+    a.l[e] = 0.1 * ((double)(sm64(a.seed, (uint64_t)e + 1) >> 40) * (1.0 / 16777216.0));
   }
   __syncthreads();
   lse_part<P>(a, a.l, S);
@@ -650,7 +884,7 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_fwd(UArgs ag) {
   merge_dist(a, a.Ed, a.E32, a.Eout);
   for (int i = lo + tid; i < hi; i += kT)
 #pragma unroll
-    for (int j = 0; j < P; ++j) a.Aout[(size_t)j * a.N + i] = expf(a.z[(size_t)i * P + j]);
+    for (int j = 0; j < P; ++j) a.Aout[(size_t)j * a.N + i] = exp_d(a.z[(size_t)i * P + j]);
 }
 
 // ---- the reverse sweep: from d(loss)/dE_hat (dE) and d(loss)/dA_hat (dA),
@@ -658,7 +892,7 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_fwd(UArgs ag) {
 template <int P>
 __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
   __shared__ Sm S;
-  extern __shared__ float dyn[];
+  extern __shared__ __align__(16) float dyn[];
   const UArgs a = local_view(ag, dyn);
   unsigned nbar = 0;
   const int tid = threadIdx.x, L = a.L, LP = a.LP, T = a.T;
@@ -687,7 +921,7 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
     copy_px<P>(a, a.lck + (size_t)t * n, a.l, a.b);
     if (!fwd_outer<P>(a, S, t, true, nbar)) return;
     // now z = z_{t+1}, a = exp z_{t+1}, S.W = A A^T; ls[k], gs[k], Rs[k]
-    const float etaB = a.eta[T + t], etaA = a.eta[t];
+    const float etaB = (float)a.eta[T + t], etaA = (float)a.eta[t];
     for (int e = tid; e < P * P; e += kT) S.Wacc[e] = 0.f;
     // ---- reverse the B-steps
     for (int k = a.K2 - 1; k >= 0; --k) {
@@ -788,14 +1022,15 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
     if (!gbar(a)) return;
     for (int e = tid; e < LP; e += kT) S.p0[e] = a.E32[e];
     __syncthreads();
-    gram(a, S.p0, S.G);
+    gram(a, S.p0, S.G, S.Gl);
     xdot<P>(a, S.p0, 1.f, a.C);
     {
       float gacc[P * P + 1];
 #pragma unroll
       for (int e = 0; e <= P * P; ++e) gacc[e] = 0.f;
       for (int i = lo + tid; i < hi; i += kT) {
-        float z[kMaxP], c[kMaxP], zb[P], cb[P];
+        double z[kMaxP];
+        float c[kMaxP], zb[P], cb[P];
         float zs[6][kMaxP];  // K1 <= 5 recorded iterates + the result
 #pragma unroll
         for (int j = 0; j < P; ++j) {
@@ -804,7 +1039,7 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
           zb[j] = a.zbar[(size_t)i * P + j];
           cb[j] = 0.f;
         }
-        a_steps<P>(z, c, S.G, etaA, a.K1, zs);
+        a_steps<P>(z, c, S.G, S.Gl, a.eta[t], a.K1, zs);
         for (int k = a.K1 - 1; k >= 0; --k) {
           float ak[P], ap[P], zeta[P], sz = 0.f;
 #pragma unroll
@@ -915,7 +1150,7 @@ struct edaa_unrolled {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   eu::Buf buf;
   eu::UArgs a{};
-  float* eta_d = nullptr;
+  double* eta_d = nullptr;
   float *dE_d = nullptr, *dA_d = nullptr;
   bool have_forward = false;
 };
@@ -966,7 +1201,7 @@ cudaError_t grid_size(int P, size_t dyn, int* G) {
     return r;
   });
   if (e != cudaSuccess) return e;
-  *G = bps >= 1 ? sms : 0;
+  *G = bps >= 1 ? std::min(sms, kMaxG) : 0;
   return cudaSuccess;
 }
 
@@ -1014,10 +1249,15 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
     }
     const size_t maxpx = (size_t)(N + sms - 1) / sms + 1;
     const size_t room = 232448 - sizeof(Sm) - 1024;
-    const size_t st = maxpx * p * kPixArrays * 4, xs = ((maxpx * L + 3) & ~(size_t)3) * 4;
+    // resident X rows: stride a multiple of 4 floats (16-byte loads) and an
+    // odd multiple of 4 (eight rows' 16-byte words fall in distinct banks)
+    int Ls = (L + 3) & ~3;
+    if (Ls % 8 == 0) Ls += 4;
+    const size_t st = maxpx * p * (kPixF * 4 + kPixD * 8), xs = maxpx * (size_t)Ls * 4;
     u->a.maxpx = (int)maxpx;
     u->a.res_state = st <= room;
     u->a.res_x = u->a.res_state && st + xs <= room;
+    u->a.Ls = u->a.res_x ? Ls : L;
     u->dyn = (u->a.res_state ? st : 0) + (u->a.res_x ? xs : 0);
     if (grid_size(p, u->dyn, &u->G) != cudaSuccess || u->G < 1) {
       edaa_unrolled_destroy(u);
@@ -1030,20 +1270,21 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
   a.L = L; a.N = N; a.P = p; a.T = T; a.K1 = K1; a.K2 = K2; a.LP = (int)lp;  // (maxpx, res_* set above)
   a.timeout_ns = 2000000000ll;
   a.X = B.get<float>((size_t)N * L);
-  u->eta_d = B.get<float>((size_t)2 * T);
+  u->eta_d = B.get<double>((size_t)2 * T);
   a.eta = u->eta_d;
-  a.z = B.get<float>(n); a.l = B.get<float>(n); a.b = B.get<float>(n); a.a = B.get<float>(n);
+  a.z = B.get<double>(n); a.l = B.get<double>(n); a.b = B.get<float>(n); a.a = B.get<float>(n);
   a.C = B.get<float>(n); a.g = B.get<float>(n); a.d = B.get<float>(n);
   a.lbar = B.get<float>(n); a.zbar = B.get<float>(n); a.Abar = B.get<float>(n); a.zeta = B.get<float>(n);
   a.Dbar = B.get<float>(n); a.bp = B.get<float>(n); a.tmp = B.get<float>(n);
-  a.zck = B.get<float>((T + 1) * n); a.lck = B.get<float>((T + 1) * n);
-  a.ls = B.get<float>((size_t)(K2 + 1) * n); a.gs = B.get<float>((size_t)std::max(K2, 1) * n);
+  a.zck = B.get<double>((T + 1) * n); a.lck = B.get<double>((T + 1) * n);
+  a.ls = B.get<double>((size_t)(K2 + 1) * n); a.gs = B.get<float>((size_t)std::max(K2, 1) * n);
   a.Rs = B.get<float>((size_t)std::max(K2, 1) * lp);
   a.Xbar = B.get<float>((size_t)N * L);
   u->dE_d = B.get<float>(lp); u->dA_d = B.get<float>(n);
   a.dE = u->dE_d; a.dA = u->dA_d;
   a.Eout = B.get<float>(lp); a.Aout = B.get<float>(n);
   a.part = B.get<float>(G * lp); a.part2 = B.get<float>(G * kSmall); a.peta = B.get<float>(G * 2 * T);
+  a.part2d = B.get<double>(G * kSmall);
   a.E32 = B.get<float>(lp); a.R32 = B.get<float>(lp); a.P32 = B.get<float>(lp);
   a.Ed = B.get<double>(lp); a.XCd = B.get<double>(lp); a.deta = B.get<double>((size_t)2 * T);
   a.bar = B.get<unsigned>(2); a.status = B.get<int>(1);
@@ -1072,16 +1313,16 @@ edaa_status edaa_unrolled_forward(edaa_unrolled* u, const float* X, uint64_t see
                                   const double* eta_B, float* E_out, float* A_out) {
   if (!u || !X || !eta_A || !eta_B) return ufail(EDAA_ERR_ARG, "edaa_unrolled_forward: NULL argument");
   const int N = u->N, P = u->P, L = u->L, n = N * P;
-  std::vector<float> eta(2 * u->T);
+  std::vector<double> eta(2 * u->T);
   for (int t = 0; t < u->T; ++t) {
-    eta[t] = (float)eta_A[t];
-    eta[u->T + t] = (float)eta_B[t];
+    eta[t] = eta_A[t];
+    eta[u->T + t] = eta_B[t];
   }
   u->a.seed = seed;
   // our stream follows the caller's
   UCK(cudaEventRecord(u->ev_in, u->caller), "order after the caller's stream");
   UCK(cudaStreamWaitEvent(u->s, u->ev_in, 0), "order after the caller's stream");
-  UCK(cudaMemcpyAsync(u->eta_d, eta.data(), eta.size() * sizeof(float), cudaMemcpyHostToDevice, u->s), "copy eta");
+  UCK(cudaMemcpyAsync(u->eta_d, eta.data(), eta.size() * sizeof(double), cudaMemcpyHostToDevice, u->s), "copy eta");
   UCK(cudaMemcpyAsync((void*)u->a.X, X, (size_t)N * L * 4, cudaMemcpyDefault, u->s), "copy X");
   UCK(sweep(u, true), "forward sweep");
   if (E_out) UCK(cudaMemcpyAsync(E_out, u->a.Eout, (size_t)L * P * 4, cudaMemcpyDefault, u->s), "copy E");
