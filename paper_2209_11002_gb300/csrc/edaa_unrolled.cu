@@ -106,6 +106,9 @@ struct UArgs {
   double* ls;                  // backward recompute: (K2 + 1) logits (N x p)
   float *gs, *Rs;              // K2 B-gradients (N x p), K2 R (L x p)
   float* Xbar;                 // N x L
+  float* U;                    // N x RK: per-pixel coefficients of the rank-p terms of Xbar
+  float* V;                    // RK x Lv: their panel columns (Lv >= L, zero padded)
+  int RK, Lv;
   const float *dE, *dA;        // backward inputs: L x p, p x N
   float *Eout, *Aout;          // forward outputs: E_hat (L x p), A_hat (p x N)
   float* part;                 // G x LP per-CTA partials of an X contraction
@@ -492,54 +495,119 @@ __device__ void xdot(const UArgs& a, const float* panel, float scale, float* __r
   __syncthreads();
 }
 
-// ---- Xbar_i[l] += s1 sum_j L1[l,j] R1[i,j] + s2 sum_j L2[l,j] R2[i,j] over this
-// CTA's pixels (Xbar in global memory): warp per pixel, two pixels at a time,
-// every load of a row issued before its updates so that the round trips overlap
+// ---- Xbar = sum of rank-p terms s L R^T (L: an L x p panel in shared memory;
+// R: per-pixel coefficients).  A term is recorded: s R into this CTA's rows of
+// U (columns ru..ru+p), the panel's columns into rows ru.. of V (by CTA 0: the
+// panels are the same in every CTA).  dx_contract forms the sum once, after
+// the last grid barrier.
 template <int P>
-__device__ void rank_update(const UArgs& a, const float* L1, const float* R1, float s1, const float* L2,
+__device__ void rank_record(const UArgs& a, int& ru, const float* L1, const float* R1, float s1, const float* L2,
                             const float* R2, float s2) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, L = a.L;
   int lo, hi;
   prange(a.N, lo, hi);
-  for (int i0 = lo + warp; i0 < hi; i0 += 2 * kW) {
-    float v[2][kLT], r1[2][P], r2[2][P];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int i = i0 + u * kW;
-      const bool live = i < hi;
-      const float* xb = a.Xbar + (size_t)(live ? i : i0) * L;
-#pragma unroll
-      for (int k = 0; k < kLT; ++k) {
-        const int l = lane + 32 * k;
-        v[u][k] = (live && l < L) ? xb[l] : 0.f;
-      }
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        r1[u][j] = live ? s1 * R1[(size_t)i * P + j] : 0.f;
-        r2[u][j] = (live && L2) ? s2 * R2[(size_t)i * P + j] : 0.f;
-      }
+  const int nt = L2 ? 2 : 1;
+  for (int e = lo * P + (int)threadIdx.x; e < hi * P; e += kT) {
+    const int i = e / P, j = e - i * P;
+    float* u = a.U + (size_t)i * a.RK + ru;
+    u[j] = s1 * R1[e];
+    if (L2) u[P + j] = s2 * R2[e];
+  }
+  if (blockIdx.x == 0)
+    for (int e = threadIdx.x; e < nt * a.LP; e += kT) {
+      const int t = e / a.LP, f = e - t * a.LP, l = f / P, j = f - l * P;
+      a.V[(size_t)(ru + t * P + j) * a.Lv + l] = (t ? L2 : L1)[f];
     }
+  ru += nt * P;
+  __syncthreads();
+}
+
+// ---- Xbar_i = U_i V over this CTA's pixels (the nr recorded terms, FP32 FMAs
+// in the order they were recorded).  Blocks of kDxBlk pixels; a thread per
+// tile of kDxPx pixels x kDxB bands; kKC terms at a time staged in shared
+// memory, the next kKC terms' loads in flight meanwhile.
+constexpr int kDxPx = 8, kDxB = 14, kDxBlk = 96, kKC = 8, kLvMax = 322;
+constexpr int kUL = (kKC * kDxBlk + kT - 1) / kT, kVL = (kKC * kLvMax + kT - 1) / kT;
+__device__ __forceinline__ void dx_contract(const UArgs& a, int nr, Sm& S) {
+  int lo, hi;
+  prange(a.N, lo, hi);
+  const int Lv = a.Lv, tid = threadIdx.x, nbg = Lv / kDxB;
+  float* Us = S.xs;                 // [kKC][kDxBlk]
+  float* Vs = S.xs + kKC * kDxBlk;  // [kKC][Lv]
+  const int nc = (nr + kKC - 1) / kKC;
+  for (int p0 = lo; p0 < hi; p0 += kDxBlk) {
+    const int np = min(kDxBlk, hi - p0);
+    const int ntile = ((np + kDxPx - 1) / kDxPx) * nbg;
+    for (int tb = 0; tb < ntile; tb += kT) {
+      const int tau = tb + tid;
+      const bool mine = tau < ntile;
+      const int pg = mine ? tau / nbg : 0, bg = mine ? tau - pg * nbg : 0;
+      float acc[kDxPx][kDxB];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int i = i0 + u * kW;
-      if (i >= hi) continue;
-      float* xb = a.Xbar + (size_t)i * L;
+      for (int q = 0; q < kDxPx; ++q)
 #pragma unroll
-      for (int k = 0; k < kLT; ++k) {
-        const int l = lane + 32 * k;
-        if (l < L) {
-          float x = v[u][k];
+        for (int b = 0; b < kDxB; ++b) acc[q][b] = 0.f;
+      float ur[kUL], vr[kVL];
+      auto fetch = [&](int c) {
+        const int r0 = c * kKC;
 #pragma unroll
-          for (int j = 0; j < P; ++j) {
-            x = fmaf(L1[l * P + j], r1[u][j], x);
-            if (L2) x = fmaf(L2[l * P + j], r2[u][j], x);
-          }
-          xb[l] = x;
+        for (int u = 0; u < kUL; ++u) {
+          const int e = tid + u * kT, px = e / kKC, r = e - px * kKC;
+          ur[u] = (px < np && r0 + r < nr) ? a.U[(size_t)(p0 + px) * a.RK + r0 + r] : 0.f;
         }
+#pragma unroll
+        for (int u = 0; u < kVL; ++u) {
+          const int e = tid + u * kT, r = e / Lv, l = e - r * Lv;
+          vr[u] = (r < kKC && r0 + r < nr) ? a.V[(size_t)(r0 + r) * Lv + l] : 0.f;
+        }
+      };
+      fetch(0);
+      for (int c = 0; c < nc; ++c) {
+#pragma unroll
+        for (int u = 0; u < kUL; ++u) {
+          const int e = tid + u * kT, px = e / kKC, r = e - px * kKC;
+          if (px < kDxBlk) Us[r * kDxBlk + px] = ur[u];
+        }
+#pragma unroll
+        for (int u = 0; u < kVL; ++u) {
+          const int e = tid + u * kT, r = e / Lv, l = e - r * Lv;
+          if (r < kKC) Vs[r * Lv + l] = vr[u];
+        }
+        __syncthreads();
+        if (c + 1 < nc) fetch(c + 1);
+        if (mine) {
+#pragma unroll
+          for (int r = 0; r < kKC; ++r) {
+            const float4 u0 = *reinterpret_cast<const float4*>(Us + r * kDxBlk + pg * kDxPx);
+            const float4 u1 = *reinterpret_cast<const float4*>(Us + r * kDxBlk + pg * kDxPx + 4);
+            const float uv[kDxPx] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+            float vv[kDxB];
+#pragma unroll
+            for (int m = 0; m < kDxB / 2; ++m) {
+              const float2 t2 = *reinterpret_cast<const float2*>(Vs + r * Lv + bg * kDxB + 2 * m);
+              vv[2 * m] = t2.x;
+              vv[2 * m + 1] = t2.y;
+            }
+#pragma unroll
+            for (int q = 0; q < kDxPx; ++q)
+#pragma unroll
+              for (int b = 0; b < kDxB; ++b) acc[q][b] = fmaf(uv[q], vv[b], acc[q][b]);
+          }
+        }
+        __syncthreads();
       }
+      if (mine)
+#pragma unroll
+        for (int q = 0; q < kDxPx; ++q) {
+          const int i = pg * kDxPx + q;
+          if (i < np)
+#pragma unroll
+            for (int b = 0; b < kDxB; ++b) {
+              const int l = bg * kDxB + b;
+              if (l < a.L) a.Xbar[(size_t)(p0 + i) * a.L + l] = acc[q][b];
+            }
+        }
     }
   }
-  __syncthreads();
 }
 
 // ---- G = E^T E from E in shared memory: warp per entry, lanes over the bands
@@ -635,9 +703,15 @@ __device__ void lse_merge(const UArgs& a, double* lse) {
     for (int u = 0; u < kB; ++u)
       if (mb[u] != -INFINITY) ff_add(hi, lo, sb[u] * expf(mb[u] - m));
     const double sum = ff_warp_total(hi, lo);
-    // (logf: its rounding shifts the whole column of logits alike, which the
-    // next normalisation takes out again)
-    if (lane == 0) lse[j] = (double)m + (double)logf((float)sum);
+    // log sum = k ln 2 + log f, sum = f 2^k, f in [1/2, 1): logf of f's float
+    // part plus the first-order term of its remainder (about 2^-24 absolute;
+    // FP64's log is a long chain of FP64 operations)
+    if (lane == 0) {
+      int k2;
+      const double f = frexp(sum, &k2);
+      const float fh = (float)f;
+      lse[j] = (double)m + (double)k2 * 0.6931471805599453 + (double)logf(fh) + (double)((float)(f - (double)fh) / fh);
+    }
   }
   __syncthreads();
 }
@@ -836,17 +910,20 @@ __device__ UArgs local_view(const UArgs& g, float* dyn) {
     a.X = q - (size_t)lo * Ls;
     q += (size_t)g.maxpx * Ls;
   }
-  if (g.res_state) {  // the FP64 arrays first (q is 16-byte aligned here)
-    double** ard[kPixD] = {&a.z, &a.l};
-    for (int k = 0; k < kPixD; ++k) {
-      *ard[k] = reinterpret_cast<double*>(q) - (size_t)lo * P;
+  if (g.res_state) {  // the kPixD FP64 arrays first (q is 16-byte aligned here), then the kPixF float ones
+    auto nextd = [&]() {
+      double* r = reinterpret_cast<double*>(q) - (size_t)lo * P;
       q += (size_t)g.maxpx * P * 2;
-    }
-    float** arr[kPixF] = {&a.b, &a.a, &a.C, &a.g, &a.d, &a.lbar, &a.zbar, &a.Abar, &a.zeta, &a.Dbar, &a.bp, &a.tmp};
-    for (int k = 0; k < kPixF; ++k) {
-      *arr[k] = q - (size_t)lo * P;
+      return r;
+    };
+    auto nextf = [&]() {
+      float* r = q - (size_t)lo * P;
       q += (size_t)g.maxpx * P;
-    }
+      return r;
+    };
+    a.z = nextd(); a.l = nextd();
+    a.b = nextf(); a.a = nextf(); a.C = nextf(); a.g = nextf(); a.d = nextf(); a.lbar = nextf();
+    a.zbar = nextf(); a.Abar = nextf(); a.zeta = nextf(); a.Dbar = nextf(); a.bp = nextf(); a.tmp = nextf();
   }
   __syncthreads();
   return a;
@@ -901,7 +978,7 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
   prange(a.N, lo, hi);
   float* peta = a.peta + (size_t)blockIdx.x * 2 * T;  // this CTA's d eta partials
   for (int e = tid; e < 2 * T; e += kT) peta[e] = 0.f;
-  for (size_t e = (size_t)lo * L + tid; e < (size_t)hi * L; e += kT) a.Xbar[e] = 0.f;
+  int ru = 0;  // rank-p terms of Xbar recorded so far
   for (int e = lo * P + tid; e < hi * P; e += kT) {
     a.zbar[e] = 0.f;
     const int i = e / P, j = e - i * P;
@@ -911,7 +988,7 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
   copy_px<P>(a, a.lck + (size_t)T * n, a.l, a.b);
   for (int e = tid; e < LP; e += kT) S.p0[e] = a.dE[e];
   __syncthreads();
-  rank_update<P>(a, S.p0, a.b, 1.f, nullptr, nullptr, 0.f);
+  rank_record<P>(a, ru, S.p0, a.b, 1.f, nullptr, nullptr, 0.f);
   xdot<P>(a, S.p0, 1.f, a.tmp);
   for (int e = lo * P + tid; e < hi * P; e += kT) a.lbar[e] = a.b[e] * a.tmp[e];
   __syncthreads();
@@ -990,7 +1067,7 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
         }
       }
       __syncthreads();
-      rank_update<P>(a, S.p1, a.zeta, -etaB, S.p0, a.d, -etaB);
+      rank_record<P>(a, ru, S.p1, a.zeta, -etaB, S.p0, a.d, -etaB);
       block_total<P * P>(wb, S);
       for (int e = tid; e < P * P; e += kT) S.Wacc[e] += S.tmp[e];
       __syncthreads();
@@ -1089,12 +1166,12 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
       S.p1[e] = (float)s;
     }
     __syncthreads();
-    rank_update<P>(a, S.p0, a.tmp, 1.f, S.p1, a.b, 1.f);
+    rank_record<P>(a, ru, S.p0, a.tmp, 1.f, S.p1, a.b, 1.f);
     xdot<P>(a, S.p1, 1.f, a.d);
     for (int e = lo * P + tid; e < hi * P; e += kT) a.lbar[e] = fmaf(a.b[e], a.d[e], a.lbar[e]);
     __syncthreads();
   }
-  // d eta: the CTAs' partials in a fixed order
+  // d eta: the CTAs' partials in a fixed order; Xbar from the recorded terms
   if (!gbar(a)) return;
   if (blockIdx.x == 0) {
     const int lane = tid & 31, warp = tid >> 5, G = gridDim.x;
@@ -1105,6 +1182,7 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
       if (lane == 0) a.deta[e] = s;
     }
   }
+  dx_contract(a, ru, S);
 }
 
 template <class F>
@@ -1280,6 +1358,10 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
   a.ls = B.get<double>((size_t)(K2 + 1) * n); a.gs = B.get<float>((size_t)std::max(K2, 1) * n);
   a.Rs = B.get<float>((size_t)std::max(K2, 1) * lp);
   a.Xbar = B.get<float>((size_t)N * L);
+  a.RK = (p * (1 + 2 * T * (K2 + 1)) + 7) & ~7;  // the rank-p terms of Xbar: dE B^T, 2 per B-step, 2 per A-phase
+  a.Lv = (L + kDxB - 1) / kDxB * kDxB;
+  a.U = B.get<float>((size_t)N * a.RK);
+  a.V = B.get<float>((size_t)a.RK * a.Lv);
   u->dE_d = B.get<float>(lp); u->dA_d = B.get<float>(n);
   a.dE = u->dE_d; a.dA = u->dA_d;
   a.Eout = B.get<float>(lp); a.Aout = B.get<float>(n);
@@ -1292,7 +1374,8 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
     edaa_unrolled_destroy(u);
     return ufail(EDAA_ERR_OOM, "cudaMalloc failed in edaa_unrolled_create");
   }
-  if (cudaMemset(a.bar, 0, 2 * sizeof(unsigned)) != cudaSuccess || cudaMemset(a.status, 0, sizeof(int)) != cudaSuccess) {
+  if (cudaMemset(a.bar, 0, 2 * sizeof(unsigned)) != cudaSuccess || cudaMemset(a.status, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(a.V, 0, (size_t)a.RK * a.Lv * 4) != cudaSuccess) {
     edaa_unrolled_destroy(u);
     return ufail(EDAA_ERR_CUDA, "edaa_unrolled_create: memset failed");
   }
