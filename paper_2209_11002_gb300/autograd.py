@@ -11,6 +11,7 @@ per outer iteration) both run in libedaa; this module only moves pointers.
 from __future__ import annotations
 
 import ctypes
+import threading
 
 import numpy as np
 import torch
@@ -18,18 +19,47 @@ import torch
 from . import edaa
 
 
+_POOL: dict = {}  # (device, L, N, p, T, K1, K2, stream) -> idle engine handles
+_POOL_LOCK = threading.Lock()
+
+
 class _Engine:
+    """One libedaa unrolled engine (device buffers sized for one shape), held
+    by an autograd context from its forward to its backward.  Creating one
+    allocates ~100 MB and queries the device, so released engines go back to
+    a per-shape pool (the engine's own stream orders a reuse after any work
+    still queued on it); free_engines() destroys the pooled ones."""
+
     def __init__(self, L, N, p, T, K1, K2, stream):
         self.lib = edaa.load_library()
-        h = ctypes.c_void_p()
-        edaa._check(self.lib.edaa_unrolled_create(ctypes.byref(h), L, N, p, T, K1, K2, stream),
-                    "edaa_unrolled_create")
-        self.h = h
+        self.key = (torch.cuda.current_device(), L, N, p, T, K1, K2, stream.value if stream else 0)
+        with _POOL_LOCK:
+            idle = _POOL.get(self.key)
+            self.h = idle.pop() if idle else None
+        if self.h is None:
+            h = ctypes.c_void_p()
+            edaa._check(self.lib.edaa_unrolled_create(ctypes.byref(h), L, N, p, T, K1, K2, stream),
+                        "edaa_unrolled_create")
+            self.h = h
+
+    def release(self):
+        h, self.h = self.h, None
+        if h:
+            with _POOL_LOCK:
+                _POOL.setdefault(self.key, []).append(h)
 
     def __del__(self):
-        if getattr(self, "h", None):
-            self.lib.edaa_unrolled_destroy(self.h)
-            self.h = None
+        self.release()
+
+
+def free_engines():
+    """Destroy every pooled (idle) unrolled engine."""
+    lib = edaa.load_library()
+    with _POOL_LOCK:
+        handles = [h for hs in _POOL.values() for h in hs]
+        _POOL.clear()
+    for h in handles:
+        lib.edaa_unrolled_destroy(h)
 
 
 class EDAAUnrolled(torch.autograd.Function):
@@ -66,9 +96,13 @@ class EDAAUnrolled(torch.autograd.Function):
         deA = np.zeros(T)
         deB = np.zeros(T)
         dp = ctypes.POINTER(ctypes.c_double)
-        edaa._check(ctx.eng.lib.edaa_unrolled_backward(ctx.eng.h, edaa._ptr(dE), edaa._ptr(dA), edaa._ptr(dX),
+        eng, ctx.eng = ctx.eng, None
+        try:
+            edaa._check(eng.lib.edaa_unrolled_backward(eng.h, edaa._ptr(dE), edaa._ptr(dA), edaa._ptr(dX),
                                                        deA.ctypes.data_as(dp), deB.ctypes.data_as(dp)),
-                    "edaa_unrolled_backward")
+                        "edaa_unrolled_backward")
+        finally:
+            eng.release()  # (the backward synchronises with the engine's stream before it returns)
         return (dX, torch.from_numpy(deA).to(ctx.eta_dtype), torch.from_numpy(deB).to(ctx.eta_dtype),
                 None, None, None, None)
 

@@ -5,7 +5,7 @@
 // d(loss)/dX and d(loss)/d(eta) from d(loss)/dE_hat and d(loss)/dA_hat.
 //
 // State (pixel-major, N x p): z = log A (normalised per pixel), l = log B
-// (normalised per column).  One A-step (eq. update_A in softmax form):
+// (normalised per column), both FP64.  One A-step (eq. update_A in softmax form):
 //   z' = log_softmax_j(z - eta (G a - c)),  a = exp z, G = E^T E, c = E^T x_i
 // One B-step (eq. update_B):
 //   l' = log_softmax_i(l - eta g),  g_i = x_i^T R,  R = X (B W - A^T), W = A A^T
@@ -33,8 +33,15 @@
 // one barrier, a distributed merge (each CTA a few of the L x p entries),
 // a second barrier; a small reduction (W, log-sum-exp, column sums, Gbar)
 // is merged by every CTA for itself after one barrier.  That is 18 barriers
-// per outer iteration forward and 39 backward.  d(loss)/dX is accumulated
-// in place in each CTA's own rows (rank-p updates, no barrier).
+// per outer iteration forward and 39 backward.  d(loss)/dX is a sum of
+// rank-p terms: the backward records them and forms each CTA's rows once at
+// the end.
+//
+// Precision: d(loss)/dX holds the residual X - E_hat A_hat, small where the
+// model fits, so rounding that moves the trajectory shows up there
+// amplified.  Hence the FP64 logs (a float's rounding of a log was the
+// largest error), and G a - c and W b - a (which cancel near a fit) formed
+// from G and W exact for the float E and A and evaluated in float-float.
 #include <math.h>
 #include <stdint.h>
 

@@ -116,3 +116,19 @@ def test_unrolled_apex_shape_full_size():
         np.abs(E - Er).max(), np.abs(A - Ar).max(), _rel(dX, dXr), _rel(deA, deAr), _rel(deB, deBr)))
     assert np.abs(A - Ar).max() <= 1e-3 and np.abs(E - Er).max() <= 1e-3
     assert _rel(dX, dXr) <= 1e-3 and _rel(deA, deAr) <= 1e-3 and _rel(deB, deBr) <= 1e-3
+
+
+def test_unrolled_engine_reuse_is_bitwise_repeatable():
+    """A second forward+backward of the same shape reuses the pooled engine and
+    reproduces the first one bit for bit (the sweeps are deterministic)."""
+    from paper_2209_11002_gb300 import autograd as AG
+    L, N, p, T, K1, K2 = 23, 777, 3, 3, 2, 3
+    X, rs, u, etaA, etaB, WE, WA = _problem(L, N, p, T, seed=11)
+    first = _gpu(X, rs, etaA, etaB, WE, WA, p, K1, K2)
+    pooled = sum(len(v) for k, v in AG._POOL.items() if k[1:7] == (L, N, p, T, K1, K2))
+    second = _gpu(X, rs, etaA, etaB, WE, WA, p, K1, K2)
+    assert pooled >= 1
+    for a, b in zip(first, second):
+        assert np.array_equal(a, b)
+    AG.free_engines()
+    assert not AG._POOL
