@@ -33,7 +33,8 @@
 // one barrier, a distributed merge (each CTA a few of the L x p entries),
 // a second barrier; a small reduction (W, log-sum-exp, column sums, Gbar)
 // is merged by every CTA for itself after one barrier.  That is 18 barriers
-// per outer iteration forward and 39 backward.  d(loss)/dX is a sum of
+// per outer iteration forward and 35 backward (the forward keeps E_t = X B_t
+// of every iteration; the backward's recompute reads it back).  d(loss)/dX is a sum of
 // rank-p terms: the backward records them and forms each CTA's rows once at
 // the end.
 //
@@ -107,10 +108,11 @@ struct UArgs {
   uint64_t seed;
   const float* X;              // N x L
   const double* eta;           // 2T: eta_A[t], then eta_B[t]
-  double *z, *l;               // log A, log B (FP64: a float's rounding of a log is the sweep's largest error)
+  float2 *z, *l;               // log A, log B as float-float (x + y): a float's rounding of a log
+                               // is the sweep's largest error
   float *b, *a, *C, *g, *d, *lbar, *zbar, *Abar, *zeta, *Dbar, *bp, *tmp;
-  double *zck, *lck;           // (T + 1) x N x p: log A, log B at the start of every outer iteration
-  double* ls;                  // backward recompute: (K2 + 1) logits (N x p)
+  float2 *zck, *lck;           // (T + 1) x N x p: log A, log B at the start of every outer iteration
+  float2* ls;                  // backward recompute: (K2 + 1) logits (N x p)
   float *gs, *Rs;              // K2 B-gradients (N x p), K2 R (L x p)
   float* Xbar;                 // N x L
   float* U;                    // N x RK: per-pixel coefficients of the rank-p terms of Xbar
@@ -123,6 +125,8 @@ struct UArgs {
   double* part2d;              // G x kSmall per-CTA FP64 partials (W = A A^T)
   float* peta;                 // G x 2T per-CTA partials of d eta
   float *E32, *R32, *P32;      // merged L x p (float)
+  float* Es;                   // T x L x p: E_t = X B_t of every outer iteration (float) ...
+  double* Eds;                 // ... and FP64, kept by the forward for the reverse sweep
   double *Ed, *XCd;            // merged L x p (FP64)
   double* deta;                // 2T
   unsigned* bar;               // arrivals at the grid barriers of this launch (zeroed before it)
@@ -132,15 +136,35 @@ struct UArgs {
   int res_state, res_x;        // the per-pixel arrays / the CTA's X rows live in shared memory
   int Ls;                      // row stride of X as the sweeps read it (L, or padded in shared memory)
 };
-constexpr int kPixD = 2;   // per-pixel FP64 arrays: z, l
+constexpr int kPixD = 2;   // per-pixel float-float arrays: z, l
 constexpr int kPixF = 12;  // per-pixel float arrays: b, a, C, g, d, lbar, zbar, Abar, zeta, Dbar, bp, tmp
 
-// exp of an FP64 log to float accuracy: expf of the float part times
-// 1 + (the remainder), the first-order term of exp of the remainder
-__device__ __forceinline__ float exp_d(double v) {
-  const float f = (float)v;
-  const float e = expf(f);
-  return fmaf(e, (float)(v - (double)f), e);
+// Float-float logs v = v.x + v.y (|v.y| <= ulp(v.x)).
+// exp to float accuracy: expf of the high part times 1 + the low part (the
+// first-order term of exp of the low part)
+__device__ __forceinline__ float ff_exp(float2 v) {
+  const float e = expf(v.x);
+  return fmaf(e, v.y, e);
+}
+// h + l -= x (Knuth's TwoSum of h and -x, then renormalised)
+__device__ __forceinline__ void ff_sub(float& h, float& l, float x) {
+  const float s = h - x;
+  const float bp = s - h;
+  const float e = (h - (s - bp)) - (x + bp);
+  l += e;
+  h = s + l;
+  l -= h - s;
+}
+// v - w for float-float w
+__device__ __forceinline__ float2 ff_minus(float2 v, float2 w) {
+  ff_sub(v.x, v.y, w.x);
+  ff_sub(v.x, v.y, w.y);
+  return v;
+}
+// a double as float-float
+__device__ __forceinline__ float2 ff_split(double d) {
+  const float h = (float)d;
+  return make_float2(h, (float)(d - (double)h));
 }
 
 // shared memory of a CTA
@@ -151,6 +175,7 @@ struct Sm {
   float red[kW * kSmall];                     // per-warp partials of a small reduction
   float W[64], G[64], Wb[64], Wacc[64], tmp[kSmall];
   double Gb[64], lse[kMaxP], sd[kMaxP];
+  float2 lse2[kMaxP], sd2[kMaxP];  // lse and sd as float-float
   float Gl[64], Wl[64];          // low parts: G + Gl = E^T E, W + Wl = A A^T, exact for the float E, A
 };
 
@@ -337,8 +362,9 @@ __device__ void merge_small(const UArgs& a, int n, float* outf, double* outd) {
   __syncthreads();
 }
 
-// ---- W = A A^T: this CTA's share in FP64 (the products of floats are exact;
-// a warp per entry, lanes over the pixels, a fixed butterfly) into
+// ---- W = A A^T: this CTA's share, exact for the float A to about 2^-44
+// (each product split into its rounded value and fma remainder, float-float
+// sums; a warp per entry, lanes over the pixels, a fixed butterfly) into
 // a.part2d[g]; after a barrier every CTA sums the CTAs' partials in order into
 // outf + out_lo (float-float)
 template <int P>
@@ -348,11 +374,14 @@ __device__ void aat_part(const UArgs& a) {
   prange(a.N, lo, hi);
   for (int e = warp; e < P * P; e += kW) {
     const int j = e / P, k = e - j * P;
-    double s = 0.0;
-    for (int i = lo + lane; i < hi; i += 32)
-      s = fma((double)a.a[(size_t)i * P + j], (double)a.a[(size_t)i * P + k], s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    float sh = 0.f, sl = 0.f;
+    for (int i = lo + lane; i < hi; i += 32) {
+      const float x = a.a[(size_t)i * P + j], y = a.a[(size_t)i * P + k];
+      const float pr = __fmul_rn(x, y);
+      ff_add(sh, sl, pr);
+      sl += fmaf(x, y, -pr);
+    }
+    const double s = ff_warp_total(sh, sl);
     if (lane == 0) a.part2d[(size_t)blockIdx.x * kSmall + e] = s;
   }
 }
@@ -644,7 +673,7 @@ __device__ void gram(const UArgs& a, const float* E, float* G, float* Gl) {
 // (max m, sum of exp(v - m)) pairs into part2 (two passes: the column maxima
 // over the CTA, then the sums), then (after a barrier) every CTA merges
 template <int P>
-__device__ void lse_part(const UArgs& a, const double* __restrict__ v, Sm& S) {
+__device__ void lse_part(const UArgs& a, const float2* __restrict__ v, Sm& S) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int lo, hi;
   prange(a.N, lo, hi);
@@ -656,7 +685,7 @@ __device__ void lse_part(const UArgs& a, const double* __restrict__ v, Sm& S) {
   }
   for (int i = lo + (int)threadIdx.x; i < hi; i += kT)
 #pragma unroll
-    for (int j = 0; j < P; ++j) m[j] = fmaxf(m[j], (float)v[(size_t)i * P + j]);
+    for (int j = 0; j < P; ++j) m[j] = fmaxf(m[j], v[(size_t)i * P + j].x);
 #pragma unroll
   for (int j = 0; j < P; ++j) {
 #pragma unroll
@@ -672,7 +701,10 @@ __device__ void lse_part(const UArgs& a, const double* __restrict__ v, Sm& S) {
   }
   for (int i = lo + (int)threadIdx.x; i < hi; i += kT)
 #pragma unroll
-    for (int j = 0; j < P; ++j) s[j] += expf((float)(v[(size_t)i * P + j] - (double)m[j]));
+    for (int j = 0; j < P; ++j) {
+      const float2 x = v[(size_t)i * P + j];
+      s[j] += expf((x.x - m[j]) + x.y);
+    }
 #pragma unroll
   for (int j = 0; j < P; ++j) {
     s[j] = wsum(s[j]);
@@ -690,7 +722,7 @@ __device__ void lse_part(const UArgs& a, const double* __restrict__ v, Sm& S) {
 }
 // every CTA: lse_j = M + log sum_g s_g exp(m_g - M), M the largest m_g (the
 // CTAs' pairs loaded once, a warp per column)
-__device__ void lse_merge(const UArgs& a, double* lse) {
+__device__ void lse_merge(const UArgs& a, double* lse, float2* lse2) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
   constexpr int kB = kMaxG / 32;
   if (warp < a.P) {
@@ -718,23 +750,16 @@ __device__ void lse_merge(const UArgs& a, double* lse) {
       const double f = frexp(sum, &k2);
       const float fh = (float)f;
       lse[j] = (double)m + (double)k2 * 0.6931471805599453 + (double)logf(fh) + (double)((float)(f - (double)fh) / fh);
+      lse2[j] = ff_split(lse[j]);
     }
   }
   __syncthreads();
 }
 
 // one pixel's A-phase: K1 mirror steps; keeps the iterates when `zs` is given
-// z = zh + zl (float-float) through the steps, FP64 in memory; the
+// z = zh + zl (float-float) through the steps and in memory; the
 // normaliser lz is a float: its rounding is common to the pixel's p entries,
 // which the next normalisation takes out again
-__device__ __forceinline__ void ff_sub(float& h, float& l, float x) {  // h + l -= x
-  const float s = h - x;
-  const float bp = s - h;
-  const float e = (h - (s - bp)) - (x + bp);
-  l += e;
-  h = s + l;  // renormalise
-  l -= h - s;
-}
 // sum_q (h_q + l_q) v_q - c for float-float weights (h, l) and float v, c:
 // every product split exactly (its rounded value and the fma remainder), the
 // sum carried as float-float; good to about 2^-44 of the largest term
@@ -756,13 +781,13 @@ __device__ __forceinline__ float ff_dot_sub(const float* h, const float* l, cons
 // The gradient g = G a - c cancels near a fit: it is evaluated from G + Gl =
 // E^T E, exact for the float E, and the float a and c (ff_dot_sub).
 template <int P>
-__device__ __forceinline__ void a_steps(double* z, const float* c, const float* G, const float* Gl, double eta,
+__device__ __forceinline__ void a_steps(float2* z, const float* c, const float* G, const float* Gl, double eta,
                                         int K1, float (*zs)[kMaxP]) {
   float zh[P], zl[P];
 #pragma unroll
   for (int j = 0; j < P; ++j) {
-    zh[j] = (float)z[j];
-    zl[j] = (float)(z[j] - (double)zh[j]);
+    zh[j] = z[j].x;
+    zl[j] = z[j].y;
   }
   const float et = (float)eta;
   for (int k = 0; k < K1; ++k) {
@@ -792,31 +817,31 @@ __device__ __forceinline__ void a_steps(double* z, const float* c, const float* 
 #pragma unroll
     for (int j = 0; j < P; ++j) zs[K1][j] = zh[j];
 #pragma unroll
-  for (int j = 0; j < P; ++j) z[j] = (double)zh[j] + (double)zl[j];
+  for (int j = 0; j < P; ++j) z[j] = make_float2(zh[j], zl[j]);
 }
 
 // l <- l - lse (per column), b = exp(l); optionally a copy of l
 template <int P>
-__device__ void shift_exp(const UArgs& a, const double* lse, double* copy) {
+__device__ void shift_exp(const UArgs& a, const float2* lse, float2* copy) {
   int lo, hi;
   prange(a.N, lo, hi);
   for (int e = lo * P + (int)threadIdx.x; e < hi * P; e += kT) {
-    const double v = a.l[e] - lse[e % P];
+    const float2 v = ff_minus(a.l[e], lse[e % P]);
     a.l[e] = v;
-    a.b[e] = exp_d(v);
+    a.b[e] = ff_exp(v);
     if (copy) copy[e] = v;
   }
   __syncthreads();
 }
 // dst = src (logs) over this CTA's pixels (p values each); b = exp(src) when b is given
 template <int P>
-__device__ void copy_px(const UArgs& a, const double* __restrict__ src, double* __restrict__ dst, float* __restrict__ eb) {
+__device__ void copy_px(const UArgs& a, const float2* __restrict__ src, float2* __restrict__ dst, float* __restrict__ eb) {
   int lo, hi;
   prange(a.N, lo, hi);
   for (int e = lo * P + (int)threadIdx.x; e < hi * P; e += kT) {
-    const double v = src[e];
+    const float2 v = src[e];
     if (dst) dst[e] = v;
-    if (eb) eb[e] = exp_d(v);
+    if (eb) eb[e] = ff_exp(v);
   }
   __syncthreads();
 }
@@ -830,19 +855,23 @@ __device__ bool fwd_outer(const UArgs& a, Sm& S, int t, bool rec, unsigned& nbar
   const int tid = threadIdx.x, LP = a.LP;
   int lo, hi;
   prange(a.N, lo, hi);
-  // E = X B (FP64 and float), G = E^T E
-  xw_part<P>(a, a.b, S);
-  if (!gbar(a)) return false;
-  merge_dist(a, a.Ed, a.E32, nullptr);
-  if (!gbar(a)) return false;
-  for (int e = tid; e < LP; e += kT) S.p0[e] = a.E32[e];
+  // E = X B (FP64 and float; kept by the forward, read back by the
+  // recompute), G = E^T E
+  float* Et = a.Es + (size_t)t * LP;
+  if (!rec) {
+    xw_part<P>(a, a.b, S);
+    if (!gbar(a)) return false;
+    merge_dist(a, a.Eds + (size_t)t * LP, Et, nullptr);
+    if (!gbar(a)) return false;
+  }
+  for (int e = tid; e < LP; e += kT) S.p0[e] = Et[e];
   __syncthreads();
   gram(a, S.p0, S.G, S.Gl);
   // c = E^T x_i, the K1 A-steps, a = exp z, and this CTA's share of W = A A^T
   xdot<P>(a, S.p0, 1.f, a.C);
   const double etaA = a.eta[t];
   for (int i = lo + tid; i < hi; i += kT) {
-    double z[kMaxP];
+    float2 z[kMaxP];
     float c[kMaxP];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
@@ -853,7 +882,7 @@ __device__ bool fwd_outer(const UArgs& a, Sm& S, int t, bool rec, unsigned& nbar
 #pragma unroll
     for (int j = 0; j < P; ++j) {
       a.z[(size_t)i * P + j] = z[j];
-      a.a[(size_t)i * P + j] = exp_d(z[j]);
+      a.a[(size_t)i * P + j] = ff_exp(z[j]);
     }
   }
   __syncthreads();
@@ -861,7 +890,7 @@ __device__ bool fwd_outer(const UArgs& a, Sm& S, int t, bool rec, unsigned& nbar
   if (rec) copy_px<P>(a, a.l, a.ls, nullptr);
   if (!gbar(a)) return false;
   merge_small_d(a, P * P, S.Wl, S.W);
-  const double etaB = a.eta[a.T + t];
+  const float etaB = (float)a.eta[a.T + t];
   for (int k = 0; k < a.K2; ++k) {
     // d_i = W b_i - a_i (cancels near a fit: from the exact W + Wl by
     // ff_dot_sub); R = X D (FP64 and float; kept for the reverse sweep)
@@ -884,14 +913,16 @@ __device__ bool fwd_outer(const UArgs& a, Sm& S, int t, bool rec, unsigned& nbar
     xdot<P>(a, S.p0, 1.f, a.g);
     for (int e = lo * P + tid; e < hi * P; e += kT) {
       const float gv = a.g[e];
-      a.l[e] = fma(-etaB, (double)gv, a.l[e]);
+      float2 v = a.l[e];
+      ff_sub(v.x, v.y, __fmul_rn(etaB, gv));  // (a rounded product: not contracted into the sum)
+      a.l[e] = v;
       if (rec) a.gs[(size_t)k * a.N * P + e] = gv;
     }
     __syncthreads();
     lse_part<P>(a, a.l, S);
     if (!gbar(a)) return false;
-    lse_merge(a, S.lse);
-    shift_exp<P>(a, S.lse, rec ? a.ls + (size_t)(k + 1) * a.N * P : nullptr);
+    lse_merge(a, S.lse, S.lse2);
+    shift_exp<P>(a, S.lse2, rec ? a.ls + (size_t)(k + 1) * a.N * P : nullptr);
   }
   return true;
 }
@@ -919,7 +950,7 @@ __device__ UArgs local_view(const UArgs& g, float* dyn) {
   }
   if (g.res_state) {  // the kPixD FP64 arrays first (q is 16-byte aligned here), then the kPixF float ones
     auto nextd = [&]() {
-      double* r = reinterpret_cast<double*>(q) - (size_t)lo * P;
+      float2* r = reinterpret_cast<float2*>(q) - (size_t)lo * P;
       q += (size_t)g.maxpx * P * 2;
       return r;
     };
@@ -947,15 +978,16 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_fwd(UArgs ag) {
   int lo, hi;
   prange(a.N, lo, hi);
   // A^0 = 1/p (eq. initA0); B^0 = softmax(0.1 u), u from SplitMix64 (eq. initB0)
+  const float2 z0 = ff_split(-log((double)P));
   for (int e = lo * P + tid; e < hi * P; e += kT) {
-    a.z[e] = -log((double)P);
-    a.l[e] = 0.1 * ((double)(sm64(a.seed, (uint64_t)e + 1) >> 40) * (1.0 / 16777216.0));
+    a.z[e] = z0;
+    a.l[e] = ff_split(0.1 * ((double)(sm64(a.seed, (uint64_t)e + 1) >> 40) * (1.0 / 16777216.0)));
   }
   __syncthreads();
   lse_part<P>(a, a.l, S);
   if (!gbar(a)) return;
-  lse_merge(a, S.lse);
-  shift_exp<P>(a, S.lse, nullptr);
+  lse_merge(a, S.lse, S.lse2);
+  shift_exp<P>(a, S.lse2, nullptr);
   for (int t = 0; t < a.T; ++t) {
     copy_px<P>(a, a.z, a.zck + (size_t)t * n, nullptr);
     copy_px<P>(a, a.l, a.lck + (size_t)t * n, nullptr);
@@ -968,7 +1000,7 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_fwd(UArgs ag) {
   merge_dist(a, a.Ed, a.E32, a.Eout);
   for (int i = lo + tid; i < hi; i += kT)
 #pragma unroll
-    for (int j = 0; j < P; ++j) a.Aout[(size_t)j * a.N + i] = exp_d(a.z[(size_t)i * P + j]);
+    for (int j = 0; j < P; ++j) a.Aout[(size_t)j * a.N + i] = ff_exp(a.z[(size_t)i * P + j]);
 }
 
 // ---- the reverse sweep: from d(loss)/dE_hat (dE) and d(loss)/dA_hat (dA),
@@ -979,7 +1011,7 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
   extern __shared__ __align__(16) float dyn[];
   const UArgs a = local_view(ag, dyn);
   unsigned nbar = 0;
-  const int tid = threadIdx.x, L = a.L, LP = a.LP, T = a.T;
+  const int tid = threadIdx.x, LP = a.LP, T = a.T;
   const size_t n = (size_t)a.N * P;
   int lo, hi;
   prange(a.N, lo, hi);
@@ -1023,12 +1055,18 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
       }
       if (!gbar(a)) return;
       merge_small(a, P, nullptr, S.sd);
+      if (tid < P) S.sd2[tid] = ff_split(S.sd[tid]);
+      __syncthreads();
       // zeta; d eta_B += -<zeta, g_k>
       {
         float de[1] = {0.f};
         const float* gk = a.gs + (size_t)k * n;
         for (int e = lo * P + tid; e < hi * P; e += kT) {
-          const float zt = (float)((double)a.lbar[e] - (double)a.bp[e] * S.sd[e % P]);
+          // lbar - bp sd with sd float-float: the product split exactly
+          const float2 sd = S.sd2[e % P];
+          const float bpv = a.bp[e], pr = __fmul_rn(bpv, sd.x);
+          const float pe = fmaf(bpv, sd.x, -pr) + bpv * sd.y;
+          const float zt = (a.lbar[e] - pr) - pe;
           a.zeta[e] = zt;
           de[0] = fmaf(-zt, gk[e], de[0]);
         }
@@ -1099,21 +1137,17 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
     }
     __syncthreads();
     // ---- reverse the A-steps from z_t with E_t = X B_t, its Gram, and c = E_t^T x
+    // (G and c are still those the recompute of iteration t formed)
     copy_px<P>(a, a.lck + (size_t)t * n, a.l, a.b);
-    xw_part<P>(a, a.b, S);
-    if (!gbar(a)) return;
-    merge_dist(a, a.Ed, a.E32, nullptr);
-    if (!gbar(a)) return;
-    for (int e = tid; e < LP; e += kT) S.p0[e] = a.E32[e];
+    const double* Edt = a.Eds + (size_t)t * LP;
+    for (int e = tid; e < LP; e += kT) S.p0[e] = a.Es[(size_t)t * LP + e];
     __syncthreads();
-    gram(a, S.p0, S.G, S.Gl);
-    xdot<P>(a, S.p0, 1.f, a.C);
     {
       float gacc[P * P + 1];
 #pragma unroll
       for (int e = 0; e <= P * P; ++e) gacc[e] = 0.f;
       for (int i = lo + tid; i < hi; i += kT) {
-        double z[kMaxP];
+        float2 z[kMaxP];
         float c[kMaxP], zb[P], cb[P];
         float zs[6][kMaxP];  // K1 <= 5 recorded iterates + the result
 #pragma unroll
@@ -1169,7 +1203,7 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
       const int l = e / P, j = e - l * P;
       double s = a.XCd[e];
 #pragma unroll
-      for (int k = 0; k < P; ++k) s += a.Ed[l * P + k] * (S.Gb[k * P + j] + S.Gb[j * P + k]);
+      for (int k = 0; k < P; ++k) s += Edt[l * P + k] * (S.Gb[k * P + j] + S.Gb[j * P + k]);
       S.p1[e] = (float)s;
     }
     __syncthreads();
@@ -1357,12 +1391,12 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
   a.X = B.get<float>((size_t)N * L);
   u->eta_d = B.get<double>((size_t)2 * T);
   a.eta = u->eta_d;
-  a.z = B.get<double>(n); a.l = B.get<double>(n); a.b = B.get<float>(n); a.a = B.get<float>(n);
+  a.z = B.get<float2>(n); a.l = B.get<float2>(n); a.b = B.get<float>(n); a.a = B.get<float>(n);
   a.C = B.get<float>(n); a.g = B.get<float>(n); a.d = B.get<float>(n);
   a.lbar = B.get<float>(n); a.zbar = B.get<float>(n); a.Abar = B.get<float>(n); a.zeta = B.get<float>(n);
   a.Dbar = B.get<float>(n); a.bp = B.get<float>(n); a.tmp = B.get<float>(n);
-  a.zck = B.get<double>((T + 1) * n); a.lck = B.get<double>((T + 1) * n);
-  a.ls = B.get<double>((size_t)(K2 + 1) * n); a.gs = B.get<float>((size_t)std::max(K2, 1) * n);
+  a.zck = B.get<float2>((T + 1) * n); a.lck = B.get<float2>((T + 1) * n);
+  a.ls = B.get<float2>((size_t)(K2 + 1) * n); a.gs = B.get<float>((size_t)std::max(K2, 1) * n);
   a.Rs = B.get<float>((size_t)std::max(K2, 1) * lp);
   a.Xbar = B.get<float>((size_t)N * L);
   a.RK = (p * (1 + 2 * T * (K2 + 1)) + 7) & ~7;  // the rank-p terms of Xbar: dE B^T, 2 per B-step, 2 per A-phase
@@ -1375,6 +1409,7 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
   a.part = B.get<float>(G * lp); a.part2 = B.get<float>(G * kSmall); a.peta = B.get<float>(G * 2 * T);
   a.part2d = B.get<double>(G * kSmall);
   a.E32 = B.get<float>(lp); a.R32 = B.get<float>(lp); a.P32 = B.get<float>(lp);
+  a.Es = B.get<float>((size_t)T * lp); a.Eds = B.get<double>((size_t)T * lp);
   a.Ed = B.get<double>(lp); a.XCd = B.get<double>(lp); a.deta = B.get<double>((size_t)2 * T);
   a.bar = B.get<unsigned>(2); a.status = B.get<int>(1);
   if (B.err != cudaSuccess) {
