@@ -33,8 +33,10 @@
 // one barrier, a distributed merge (each CTA a few of the L x p entries),
 // a second barrier; a small reduction (W, log-sum-exp, column sums, Gbar)
 // is merged by every CTA for itself after one barrier.  That is 18 barriers
-// per outer iteration forward and 35 backward (the forward keeps E_t = X B_t
-// of every iteration; the backward's recompute reads it back).  d(loss)/dX is a sum of
+// per outer iteration forward and 19 backward: the forward keeps the
+// iteration's grid-level reductions (E_t, W, every R_k and column
+// normaliser; O(T K2 L p) floats), so that the backward's recompute of an
+// iteration from its checkpoint needs none.  d(loss)/dX is a sum of
 // rank-p terms: the backward records them and forms each CTA's rows once at
 // the end.
 //
@@ -113,7 +115,10 @@ struct UArgs {
   float *b, *a, *C, *g, *d, *lbar, *zbar, *Abar, *zeta, *Dbar, *bp, *tmp;
   float2 *zck, *lck;           // (T + 1) x N x p: log A, log B at the start of every outer iteration
   float2* ls;                  // backward recompute: (K2 + 1) logits (N x p)
-  float *gs, *Rs;              // K2 B-gradients (N x p), K2 R (L x p)
+  float* gs;                   // K2 B-gradients (N x p) of the iteration being reversed
+  float* Rs;                   // T x K2 x L x p: R of every B-step (kept by the forward)
+  float* Ws;                   // T x 2p^2: W = A A^T of every outer iteration (high, low parts)
+  float2* lses;                // T x K2 x p: the column normalisers of every B-step
   float* Xbar;                 // N x L
   float* U;                    // N x RK: per-pixel coefficients of the rank-p terms of Xbar
   float* V;                    // RK x Lv: their panel columns (Lv >= L, zero padded)
@@ -124,7 +129,7 @@ struct UArgs {
   float* part2;                // G x kSmall per-CTA partials of a small reduction
   double* part2d;              // G x kSmall per-CTA FP64 partials (W = A A^T)
   float* peta;                 // G x 2T per-CTA partials of d eta
-  float *E32, *R32, *P32;      // merged L x p (float)
+  float *E32, *P32;            // merged L x p (float)
   float* Es;                   // T x L x p: E_t = X B_t of every outer iteration (float) ...
   double* Eds;                 // ... and FP64, kept by the forward for the reverse sweep
   double *Ed, *XCd;            // merged L x p (FP64)
@@ -847,9 +852,13 @@ __device__ void copy_px(const UArgs& a, const float2* __restrict__ src, float2* 
 }
 
 // ---- one outer iteration forward from (z, l normalised, b = exp l): the
-// A-phase, then K2 B-steps.  With `rec`, keeps the logits ls[k], B-gradients
-// gs[k] and R_k (Rs[k]) for the reverse sweep.  Ends with z = z_{t+1}, a =
-// exp z, W = A A^T in S.W.
+// A-phase, then K2 B-steps.  The forward (rec false) forms the grid-level
+// reductions of the iteration and keeps them: E_t (Es, Eds), W (Ws), every
+// R_k (Rs) and every column normaliser (lses).  The reverse sweep's
+// recompute (rec true) reads them back, so it needs no grid barrier and
+// reproduces the forward's per-pixel values bit for bit; it keeps the
+// logits ls[k] and B-gradients gs[k] for the reverse B-steps.  Ends with
+// z = z_{t+1}, a = exp z, W in S.W + S.Wl.
 template <int P>
 __device__ bool fwd_outer(const UArgs& a, Sm& S, int t, bool rec, unsigned& nbar) {
   const int tid = threadIdx.x, LP = a.LP;
@@ -886,28 +895,46 @@ __device__ bool fwd_outer(const UArgs& a, Sm& S, int t, bool rec, unsigned& nbar
     }
   }
   __syncthreads();
-  aat_part<P>(a);
-  if (rec) copy_px<P>(a, a.l, a.ls, nullptr);
-  if (!gbar(a)) return false;
-  merge_small_d(a, P * P, S.Wl, S.W);
-  const float etaB = (float)a.eta[a.T + t];
-  for (int k = 0; k < a.K2; ++k) {
-    // d_i = W b_i - a_i (cancels near a fit: from the exact W + Wl by
-    // ff_dot_sub); R = X D (FP64 and float; kept for the reverse sweep)
-    for (int i = lo + tid; i < hi; i += kT) {
-      float bv[P];
-#pragma unroll
-      for (int q = 0; q < P; ++q) bv[q] = a.b[(size_t)i * P + q];
-#pragma unroll
-      for (int j = 0; j < P; ++j)
-        a.d[(size_t)i * P + j] = ff_dot_sub<P>(S.W + j * P, S.Wl + j * P, bv, a.a[(size_t)i * P + j]);
+  float* Wt = a.Ws + (size_t)t * 2 * P * P;
+  if (!rec) {
+    aat_part<P>(a);
+    if (!gbar(a)) return false;
+    merge_small_d(a, P * P, S.Wl, S.W);
+    if (blockIdx.x == 0)
+      for (int e = tid; e < P * P; e += kT) {
+        Wt[e] = S.W[e];
+        Wt[P * P + e] = S.Wl[e];
+      }
+  } else {
+    copy_px<P>(a, a.l, a.ls, nullptr);
+    for (int e = tid; e < P * P; e += kT) {
+      S.W[e] = Wt[e];
+      S.Wl[e] = Wt[P * P + e];
     }
     __syncthreads();
-    xw_part<P>(a, a.d, S);
-    if (!gbar(a)) return false;
-    merge_dist(a, nullptr, a.R32, rec ? a.Rs + (size_t)k * LP : nullptr);
-    if (!gbar(a)) return false;
-    for (int e = tid; e < LP; e += kT) S.p0[e] = a.R32[e];
+  }
+  const float etaB = (float)a.eta[a.T + t];
+  for (int k = 0; k < a.K2; ++k) {
+    float* Rk = a.Rs + ((size_t)t * a.K2 + k) * LP;
+    float2* lk = a.lses + ((size_t)t * a.K2 + k) * P;
+    if (!rec) {
+      // d_i = W b_i - a_i (cancels near a fit: from the exact W + Wl by
+      // ff_dot_sub); R = X D, kept
+      for (int i = lo + tid; i < hi; i += kT) {
+        float bv[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) bv[q] = a.b[(size_t)i * P + q];
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+          a.d[(size_t)i * P + j] = ff_dot_sub<P>(S.W + j * P, S.Wl + j * P, bv, a.a[(size_t)i * P + j]);
+      }
+      __syncthreads();
+      xw_part<P>(a, a.d, S);
+      if (!gbar(a)) return false;
+      merge_dist(a, nullptr, Rk, nullptr);
+      if (!gbar(a)) return false;
+    }
+    for (int e = tid; e < LP; e += kT) S.p0[e] = Rk[e];
     __syncthreads();
     // g_i = x_i^T R; l' = l - eta g, normalised per column
     xdot<P>(a, S.p0, 1.f, a.g);
@@ -919,9 +946,15 @@ __device__ bool fwd_outer(const UArgs& a, Sm& S, int t, bool rec, unsigned& nbar
       if (rec) a.gs[(size_t)k * a.N * P + e] = gv;
     }
     __syncthreads();
-    lse_part<P>(a, a.l, S);
-    if (!gbar(a)) return false;
-    lse_merge(a, S.lse, S.lse2);
+    if (!rec) {
+      lse_part<P>(a, a.l, S);
+      if (!gbar(a)) return false;
+      lse_merge(a, S.lse, S.lse2);
+      if (blockIdx.x == 0 && tid < P) lk[tid] = S.lse2[tid];
+    } else {
+      if (tid < P) S.lse2[tid] = lk[tid];
+      __syncthreads();
+    }
     shift_exp<P>(a, S.lse2, rec ? a.ls + (size_t)(k + 1) * a.N * P : nullptr);
   }
   return true;
@@ -1080,7 +1113,7 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
       if (!gbar(a)) return;
       for (int e = tid; e < LP; e += kT) {
         S.p0[e] = a.P32[e];
-        S.p1[e] = a.Rs[(size_t)k * LP + e];
+        S.p1[e] = a.Rs[((size_t)t * a.K2 + k) * LP + e];
       }
       __syncthreads();
       xdot<P>(a, S.p0, -etaB, a.Dbar);
@@ -1397,7 +1430,9 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
   a.Dbar = B.get<float>(n); a.bp = B.get<float>(n); a.tmp = B.get<float>(n);
   a.zck = B.get<float2>((T + 1) * n); a.lck = B.get<float2>((T + 1) * n);
   a.ls = B.get<float2>((size_t)(K2 + 1) * n); a.gs = B.get<float>((size_t)std::max(K2, 1) * n);
-  a.Rs = B.get<float>((size_t)std::max(K2, 1) * lp);
+  a.Rs = B.get<float>((size_t)T * std::max(K2, 1) * lp);
+  a.Ws = B.get<float>((size_t)T * 2 * p * p);
+  a.lses = B.get<float2>((size_t)T * std::max(K2, 1) * p);
   a.Xbar = B.get<float>((size_t)N * L);
   a.RK = (p * (1 + 2 * T * (K2 + 1)) + 7) & ~7;  // the rank-p terms of Xbar: dE B^T, 2 per B-step, 2 per A-phase
   a.Lv = (L + kDxB - 1) / kDxB * kDxB;
@@ -1408,7 +1443,7 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
   a.Eout = B.get<float>(lp); a.Aout = B.get<float>(n);
   a.part = B.get<float>(G * lp); a.part2 = B.get<float>(G * kSmall); a.peta = B.get<float>(G * 2 * T);
   a.part2d = B.get<double>(G * kSmall);
-  a.E32 = B.get<float>(lp); a.R32 = B.get<float>(lp); a.P32 = B.get<float>(lp);
+  a.E32 = B.get<float>(lp); a.P32 = B.get<float>(lp);
   a.Es = B.get<float>((size_t)T * lp); a.Eds = B.get<double>((size_t)T * lp);
   a.Ed = B.get<double>(lp); a.XCd = B.get<double>(lp); a.deta = B.get<double>((size_t)2 * T);
   a.bar = B.get<unsigned>(2); a.status = B.get<int>(1);
