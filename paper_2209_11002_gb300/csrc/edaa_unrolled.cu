@@ -33,7 +33,7 @@
 // one barrier, a distributed merge (each CTA a few of the L x p entries),
 // a second barrier; a small reduction (W, log-sum-exp, column sums, Gbar)
 // is merged by every CTA for itself after one barrier.  That is 18 barriers
-// per outer iteration forward and 19 backward: the forward keeps the
+// per outer iteration forward and 18 backward: the forward keeps the
 // iteration's grid-level reductions (E_t, W, every R_k and column
 // normaliser; O(T K2 L p) floats), so that the backward's recompute of an
 // iteration from its checkpoint needs none.  d(loss)/dX is a sum of
@@ -1225,11 +1225,11 @@ __global__ void __launch_bounds__(kT, 1) k_unrolled_bwd(UArgs ag) {
       block_part<P * P + 1>(a, gacc, S);
       if (tid == 0) peta[t] += a.part2[(size_t)blockIdx.x * kSmall + P * P];
     }
-    if (!gbar(a)) return;
-    merge_small(a, P * P, nullptr, S.Gb);
     // Ebar = E (Gbar + Gbar^T) + X Cbar^T ; Xbar += E Cbar + Ebar B^T ; lbar += B o (X^T Ebar)
+    // (the Gbar partials and the X Cbar^T partials share one barrier)
     xw_part<P>(a, a.tmp, S);
     if (!gbar(a)) return;
+    merge_small(a, P * P, nullptr, S.Gb);
     merge_dist(a, a.XCd, nullptr, nullptr);
     if (!gbar(a)) return;
     for (int e = tid; e < LP; e += kT) {
