@@ -538,9 +538,9 @@ __device__ void xdot(const UArgs& a, const float* panel, float scale, float* __r
 
 // ---- Xbar = sum of rank-p terms s L R^T (L: an L x p panel in shared memory;
 // R: per-pixel coefficients).  A term is recorded: s R into this CTA's rows of
-// U (columns ru..ru+p), the panel's columns into rows ru.. of V (by CTA 0: the
-// panels are the same in every CTA).  dx_contract forms the sum once, after
-// the last grid barrier.
+// U (columns ru..ru+p), the panel's columns into rows ru.. of V (shared out
+// among the CTAs: the panels are the same in every CTA).  dx_contract forms
+// the sum once, after the last grid barrier.
 template <int P>
 __device__ void rank_record(const UArgs& a, int& ru, const float* L1, const float* R1, float s1, const float* L2,
                             const float* R2, float s2) {
@@ -553,11 +553,12 @@ __device__ void rank_record(const UArgs& a, int& ru, const float* L1, const floa
     u[j] = s1 * R1[e];
     if (L2) u[P + j] = s2 * R2[e];
   }
-  if (blockIdx.x == 0)
-    for (int e = threadIdx.x; e < nt * a.LP; e += kT) {
-      const int t = e / a.LP, f = e - t * a.LP, l = f / P, j = f - l * P;
-      a.V[(size_t)(ru + t * P + j) * a.Lv + l] = (t ? L2 : L1)[f];
-    }
+  // the panels' columns: spread over the CTAs (each holds the same panels),
+  // bands fastest so that consecutive threads write consecutive floats of V
+  for (int e = blockIdx.x * kT + threadIdx.x; e < nt * a.LP; e += gridDim.x * kT) {
+    const int r = e / a.L, l = e - r * a.L, t = r / P, j = r - t * P;
+    a.V[(size_t)(ru + r) * a.Lv + l] = (t ? L2 : L1)[l * P + j];
+  }
   ru += nt * P;
   __syncthreads();
 }
