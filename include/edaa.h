@@ -255,12 +255,17 @@ edaa_status edaa_measure_fma_peak(double* tflops, void* stream);
  * (eq. update_B) of outer iteration t; A^0 = 1/p (eq. initA0), B^0 =
  * softmax(0.1 u) with u from SplitMix64(seed) exactly as in edaa_init (eq.
  * initB0).  X is used as given (no normalisation inside).  The forward keeps
- * one checkpoint (log A, log B) per outer iteration; the backward recomputes
- * each outer iteration from its checkpoint and runs hand-written adjoint
- * kernels, returning d loss / d X and d loss / d eta from d loss / d E_hat
- * and d loss / d A_hat, where E_hat = X B_hat and A_hat are the outputs.
+ * one checkpoint (log A, log B) per outer iteration and the iteration's
+ * grid-level reductions (E = X B, W = A A^T, and per B-step R and the column
+ * normaliser: O(T K2 L p) floats); the backward recomputes each outer
+ * iteration from its checkpoint and those reductions and runs hand-written
+ * adjoint kernels, returning d loss / d X and d loss / d eta from
+ * d loss / d E_hat and d loss / d A_hat, where E_hat = X B_hat and A_hat are
+ * the outputs.  Results are deterministic (fixed-order reductions).
  * Limits: 1 <= p <= 8, p <= N, L <= 320, K1 <= 5.  All device buffers are
- * allocated by edaa_unrolled_create; `stream` is a cudaStream_t. */
+ * allocated by edaa_unrolled_create: about 8 N L + 8 N p T (K2 + 3) + 100 N p
+ * bytes (106 MB at L=285, N=13542, p=4, T=20, K2=5); `stream` is a
+ * cudaStream_t. */
 typedef struct edaa_unrolled edaa_unrolled;
 
 edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T, int K1, int K2, void* stream);
