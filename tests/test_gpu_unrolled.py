@@ -132,3 +132,31 @@ def test_unrolled_engine_reuse_is_bitwise_repeatable():
         assert np.array_equal(a, b)
     AG.free_engines()
     assert not AG._POOL
+
+
+def test_unrolled_two_live_contexts():
+    """Two forwards alive at once (their backwards in reverse order) give the
+    same results as two separate forward+backward steps."""
+    L, N, p, T, K1, K2 = 23, 777, 3, 3, 2, 3
+    X1, rs, u, etaA, etaB, WE, WA = _problem(L, N, p, T, seed=12)
+    X2 = X1[:, ::-1].copy()
+    ref1 = _gpu(X1, rs, etaA, etaB, WE, WA, p, K1, K2)
+    ref2 = _gpu(X2, rs, etaA, etaB, WE, WA, p, K1, K2)
+    from paper_2209_11002_gb300.autograd import EDAAUnrolled
+    outs, grads = [], []
+    for Xh in (X1, X2):
+        Xg = torch.tensor(Xh.T.astype(np.float32), device="cuda", requires_grad=True)
+        eA = torch.tensor(etaA, dtype=torch.float64, requires_grad=True)
+        eB = torch.tensor(etaB, dtype=torch.float64, requires_grad=True)
+        E, A = EDAAUnrolled.apply(Xg, eA, eB, p, rs, K1, K2)
+        R = Xg.t() - E @ A
+        loss = 0.5 * (R * R).sum() + (torch.tensor(WE, dtype=torch.float32, device="cuda") * E).sum() \
+            + (torch.tensor(WA, dtype=torch.float32, device="cuda") * A).sum()
+        outs.append((E, A, loss))
+        grads.append((Xg, eA, eB))
+    for (E, A, loss), (Xg, eA, eB), ref in reversed(list(zip(outs, grads, (ref1, ref2)))):
+        loss.backward()
+        got = (E.detach().cpu().numpy(), A.detach().cpu().numpy(), Xg.grad.cpu().numpy().T, eA.grad.numpy(),
+               eB.grad.numpy())
+        for a_, b_ in zip(got, ref):
+            assert np.array_equal(a_, b_)
