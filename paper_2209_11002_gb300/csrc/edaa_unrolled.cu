@@ -140,6 +140,7 @@ struct UArgs {
   int maxpx;                   // the most pixels a CTA owns
   int res_state, res_x;        // the per-pixel arrays / the CTA's X rows live in shared memory
   int Ls;                      // row stride of X as the sweeps read it (L, or padded in shared memory)
+  int Qx;                      // quad stride of xw_part's chunk sums in shared memory (>= ceil(L/4))
 };
 constexpr int kPixD = 2;   // per-pixel float-float arrays: z, l
 constexpr int kPixF = 12;  // per-pixel float arrays: b, a, C, g, d, lbar, zbar, Abar, zeta, Dbar, bp, tmp
@@ -284,7 +285,7 @@ __device__ void xw_part(const UArgs& a, const float* __restrict__ w, Sm& S) {
     }
     return;
   }
-  const int Ls = a.Ls, Q = (L + 3) >> 2, C = min(8, max(1, kT / Q)), npx = hi - lo;
+  const int Ls = a.Ls, Q = (L + 3) >> 2, C = min(8, max(1, kT / Q)), npx = hi - lo, Qs = a.Qx;
   if (tid < Q * C) {
     const int c = tid / Q, q = tid - c * Q;
     const int k0 = lo + npx * c / C, k1 = lo + npx * (c + 1) / C;
@@ -321,17 +322,17 @@ __device__ void xw_part(const UArgs& a, const float* __restrict__ w, Sm& S) {
           s[r][j] = 0.f;
         }
     }
-    float* xs = S.xs + (size_t)c * 4 * P * Q;
+    float* xs = S.xs + (size_t)c * 4 * P * Qs;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-      for (int j = 0; j < P; ++j) xs[(r * P + j) * Q + q] = sh[r][j] + sl[r][j];
+      for (int j = 0; j < P; ++j) xs[(r * P + j) * Qs + q] = sh[r][j] + sl[r][j];
   }
   __syncthreads();
   for (int e = tid; e < LP; e += kT) {
     const int l = e / P, j = e - l * P, q = l >> 2, r = l & 3;
     float h = 0.f, lw = 0.f;
-    for (int c = 0; c < C; ++c) ff_add(h, lw, S.xs[((size_t)c * 4 * P + r * P + j) * Q + q]);
+    for (int c = 0; c < C; ++c) ff_add(h, lw, S.xs[((size_t)c * 4 * P + r * P + j) * Qs + q]);
     dst[e] = h + lw;
   }
 }
@@ -1338,6 +1339,31 @@ cudaError_t set_dyn(size_t dyn) {
 cudaError_t sweep(edaa_unrolled* u, bool forward) {
   return by_p(u->P, [&](auto pc) { return launch_sweep<decltype(pc)::value>(u, forward); });
 }
+// xw_part's chunk sums sit in shared memory at [c][r][j][q] with quad stride
+// Qx: the smallest Qx >= ceil(L/4) (up to 32 more) whose reads in the
+// combine loop (thread e takes entry (l, j) = (e / p, e % p)) fall in the
+// fewest banks at once; writes (consecutive q) are conflict-free for any Qx
+int xs_stride(int L, int P) {
+  const int Q = (L + 3) >> 2, C = std::min(8, std::max(1, kT / Q)), LP = L * P;
+  int best = Q, bestw = 1 << 30;
+  for (int Qp = Q; Qp <= Q + 32 && C * 4 * P * Qp <= 4 * kMaxP * kT; ++Qp) {
+    int w = 1;
+    for (int c = 0; c < C; ++c)
+      for (int e0 = 0; e0 < LP; e0 += 32) {
+        int cnt[32] = {0};
+        for (int lane = 0; lane < 32 && e0 + lane < LP; ++lane) {
+          const int e = e0 + lane, l = e / P, j = e - l * P, q = l >> 2, r = l & 3;
+          w = std::max(w, ++cnt[(((c * 4 + r) * P + j) * Qp + q) & 31]);
+        }
+      }
+    if (w < bestw) {
+      bestw = w;
+      best = Qp;
+    }
+    if (bestw == 1) break;
+  }
+  return best;
+}
 // the largest grid a cooperative launch of the sweeps can take: every SM, one CTA each
 cudaError_t grid_size(int P, size_t dyn, int* G) {
   int dev = 0, sms = 0, bps = 0;
@@ -1411,6 +1437,7 @@ edaa_status edaa_unrolled_create(edaa_unrolled** out, int L, int N, int p, int T
     u->a.res_state = st <= room;
     u->a.res_x = u->a.res_state && st + xs <= room;
     u->a.Ls = u->a.res_x ? Ls : L;
+    u->a.Qx = xs_stride(L, p);
     u->dyn = (u->a.res_state ? st : 0) + (u->a.res_x ? xs : 0);
     if (grid_size(p, u->dyn, &u->G) != cudaSuccess || u->G < 1) {
       edaa_unrolled_destroy(u);
