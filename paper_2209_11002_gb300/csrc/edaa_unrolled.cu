@@ -5,7 +5,7 @@
 // d(loss)/dX and d(loss)/d(eta) from d(loss)/dE_hat and d(loss)/dA_hat.
 //
 // State (pixel-major, N x p): z = log A (normalised per pixel), l = log B
-// (normalised per column), both FP64.  One A-step (eq. update_A in softmax form):
+// (normalised per column), both float-float (hi + lo).  One A-step (eq. update_A in softmax form):
 //   z' = log_softmax_j(z - eta (G a - c)),  a = exp z, G = E^T E, c = E^T x_i
 // One B-step (eq. update_B):
 //   l' = log_softmax_i(l - eta g),  g_i = x_i^T R,  R = X (B W - A^T), W = A A^T
@@ -42,7 +42,7 @@
 //
 // Precision: d(loss)/dX holds the residual X - E_hat A_hat, small where the
 // model fits, so rounding that moves the trajectory shows up there
-// amplified.  Hence the FP64 logs (a float's rounding of a log was the
+// amplified.  Hence the float-float logs (a float's rounding of a log was the
 // largest error), and G a - c and W b - a (which cancel near a fit) formed
 // from G and W exact for the float E and A and evaluated in float-float.
 #include <math.h>
@@ -983,7 +983,7 @@ __device__ UArgs local_view(const UArgs& g, float* dyn) {
     a.X = q - (size_t)lo * Ls;
     q += (size_t)g.maxpx * Ls;
   }
-  if (g.res_state) {  // the kPixD FP64 arrays first (q is 16-byte aligned here), then the kPixF float ones
+  if (g.res_state) {  // the kPixD float-float arrays first (q is 16-byte aligned here), then the kPixF float ones
     auto nextd = [&]() {
       float2* r = reinterpret_cast<float2*>(q) - (size_t)lo * P;
       q += (size_t)g.maxpx * P * 2;
