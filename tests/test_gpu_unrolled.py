@@ -160,3 +160,26 @@ def test_unrolled_two_live_contexts():
                eB.grad.numpy())
         for a_, b_ in zip(got, ref):
             assert np.array_equal(a_, b_)
+
+
+@pytest.mark.parametrize("shape", [(200, 50000, 3, 2, 2, 2), (30, 150000, 8, 2, 2, 2)])
+def test_unrolled_global_memory_paths(shape):
+    """Cubes whose X rows (L=200, N=50000) or X rows and per-pixel state (L=30,
+    N=150000, p=8) do not fit in a CTA's shared memory: E, A and d(loss)/dX
+    against the FP64 reference.  d(loss)/d eta at these shapes is a small sum
+    of large per-pixel terms that cancel: the FP64 restatement itself, run in
+    float32, misses its FP64 result by 4e-3 and 0.6 (d eta_A) here, so d eta
+    is held only to the order of magnitude (its accuracy is pinned at the APEX
+    shape and by central differences above)."""
+    L, N, p, T, K1, K2 = shape
+    X, rs, u, etaA, etaB, WE, WA = _problem(L, N, p, T, seed=L + p)
+    E, A, dX, deA, deB = _gpu(X, rs, etaA, etaB, WE, WA, p, K1, K2)
+    Er, Ar, dXr, deAr, deBr = _reference(X, u, etaA, etaB, WE, WA, K1, K2)
+    print("global-memory paths %s: E %.2e A %.2e dX %.2e d eta_A %.2e d eta_B %.2e" % (
+        shape, np.abs(E - Er).max(), np.abs(A - Ar).max(), _rel(dX, dXr), _rel(deA, deAr), _rel(deB, deBr)))
+    assert np.abs(A - Ar).max() <= 1e-3 and np.abs(E - Er).max() <= 1e-3
+    assert _rel(dX, dXr) <= 1e-3
+    assert np.all(np.isfinite(deA)) and np.all(np.isfinite(deB))
+    for got, ref in ((deA, deAr), (deB, deBr)):
+        ratio = np.linalg.norm(got) / np.linalg.norm(ref)
+        assert 0.1 <= ratio <= 10.0
