@@ -5,7 +5,8 @@
 // d(loss)/dX and d(loss)/d(eta) from d(loss)/dE_hat and d(loss)/dA_hat.
 //
 // State (pixel-major, N x p): z = log A (normalised per pixel), l = log B
-// (normalised per column), both float-float (hi + lo).  One A-step (eq. update_A in softmax form):
+// (normalised per column), both float-float (hi + lo).  One A-step (eq.
+// update_A in softmax form):
 //   z' = log_softmax_j(z - eta (G a - c)),  a = exp z, G = E^T E, c = E^T x_i
 // One B-step (eq. update_B):
 //   l' = log_softmax_i(l - eta g),  g_i = x_i^T R,  R = X (B W - A^T), W = A A^T
