@@ -263,8 +263,8 @@ edaa_status edaa_measure_fma_peak(double* tflops, void* stream);
  * d loss / d E_hat and d loss / d A_hat, where E_hat = X B_hat and A_hat are
  * the outputs.  Results are deterministic (fixed-order reductions).
  * Limits: 1 <= p <= 8, p <= N, L <= 320, K1 <= 5.  All device buffers are
- * allocated by edaa_unrolled_create: about 8 N L + 8 N p T (K2 + 3) + 100 N p
- * bytes (106 MB at L=285, N=13542, p=4, T=20, K2=5); `stream` is a
+ * allocated by edaa_unrolled_create: about 8 N L + 8 N p T (K2 + 3) + 150 N p
+ * bytes (111 MB at L=285, N=13542, p=4, T=20, K2=5); `stream` is a
  * cudaStream_t. */
 typedef struct edaa_unrolled edaa_unrolled;
 

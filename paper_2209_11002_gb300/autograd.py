@@ -26,7 +26,7 @@ _POOL_LOCK = threading.Lock()
 class _Engine:
     """One libedaa unrolled engine (device buffers sized for one shape), held
     by an autograd context from its forward to its backward.  Creating one
-    allocates ~100 MB and queries the device, so released engines go back to
+    allocates ~110 MB at the APEX shape and queries the device, so released engines go back to
     a per-shape pool (the engine's own stream orders a reuse after any work
     still queued on it); free_engines() destroys the pooled ones."""
 
