@@ -26,9 +26,10 @@ _POOL_LOCK = threading.Lock()
 class _Engine:
     """One libedaa unrolled engine (device buffers sized for one shape), held
     by an autograd context from its forward to its backward.  Creating one
-    allocates ~110 MB at the APEX shape and queries the device, so released engines go back to
-    a per-shape pool (the engine's own stream orders a reuse after any work
-    still queued on it); free_engines() destroys the pooled ones."""
+    allocates device memory (~110 MB for L=285, N=13542, p=4, T=20) and
+    queries the device, so released engines go back to a per-shape pool (the
+    engine's own stream orders a reuse after any work still queued on it);
+    free_engines() destroys the pooled ones."""
 
     def __init__(self, L, N, p, T, K1, K2, stream):
         self.lib = edaa.load_library()
