@@ -45,7 +45,7 @@ class _Engine:
 
     def release(self):
         h, self.h = self.h, None
-        if h:
+        if h and _POOL_LOCK is not None:  # (module globals may be gone at interpreter exit)
             with _POOL_LOCK:
                 _POOL.setdefault(self.key, []).append(h)
 
